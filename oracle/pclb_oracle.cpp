@@ -1,0 +1,511 @@
+// ============================================================================
+// Oracle for the polar-coordinate finite-difference lattice Boltzmann step
+// (Lin, Xu, Zhang, Li & Succi, "Polar coordinate lattice Boltzmann modeling
+// of compressible flows").
+//
+// TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, FP64 restatement of
+// the paper's method, written to be checked against the paper by eye.  Only
+// the test suite, the smoke check and the benchmark's CPU-baseline leg may
+// load it; the product (the CUDA library) never does, and the two share no
+// code, headers or tables.
+//
+// What it computes, in the paper's order and notation:
+//   * the discrete velocity model, Eq. (2), with N_k = 4 shells;
+//   * the macroscopic moments rho, u, E, Eqs. (3)-(5);
+//   * the weights F_k, Eqs. (11a), (11b), (12), and the equilibrium, Eq. (10);
+//   * one time step of the combined scheme, Eq. (38): analytic relaxation,
+//     Eq. (19), minus the Modified Warming-Beam terms, Eq. (28) with the switch
+//     function S(eta) of Eq. (37), in r and in theta;
+//   * the radial ghost nodes of Sec. II C 1 (Eq. 39, ghost f = f^eq) and the
+//     azimuthal ghost nodes of Sec. II C 2 (Eq. 40, index rotation).
+//   * the vector-Jacobian product of that step (the adjoint step), by its
+//     plain definition: forward-mode derivatives column by column, each
+//     dotted with the cotangent.
+//
+// Readings where the paper is silent (each is also listed in the design notes):
+//   * velocity labels are fixed in Cartesian space: v_r = v.e_r(theta),
+//     v_theta = v.e_theta(theta) at the node being updated;
+//   * delta == 0 in Eq. (28): eta is undefined, the bracket times delta is
+//     replaced by its limit C*delta (= 0); |eta| overflowing to infinity is
+//     replaced by its limit;
+//   * the derivative of |x| at x = 0 is taken as 0 (active-branch convention);
+//   * ghost nodes: rho and T extrapolated by Eq. (39), applied twice for the
+//     outer ghost layer; u extrapolated the same way (BC kind 0), prescribed
+//     (kind 1), or everything prescribed (kind 2).
+//
+// Parity pins for every function here live in tests/test_oracle_*.py.
+// Build: g++ -O2 -std=c++17 -ffp-contract=off -fopenmp -shared -fPIC.
+// ============================================================================
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Forward-mode dual number (value, derivative), used only by the adjoint.
+// ---------------------------------------------------------------------------
+struct Dual {
+  double v, d;
+  Dual() : v(0), d(0) {}
+  Dual(double x) : v(x), d(0) {}
+  Dual(double x, double dx) : v(x), d(dx) {}
+};
+inline Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+inline Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+inline Dual operator-(Dual a) { return {-a.v, -a.d}; }
+inline Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+inline Dual operator/(Dual a, Dual b) {
+  double q = a.v / b.v;
+  return {q, (a.d - q * b.d) / b.v};
+}
+inline Dual operator+(Dual a, double b) { return {a.v + b, a.d}; }
+inline Dual operator+(double a, Dual b) { return {a + b.v, b.d}; }
+inline Dual operator-(Dual a, double b) { return {a.v - b, a.d}; }
+inline Dual operator-(double a, Dual b) { return {a - b.v, -b.d}; }
+inline Dual operator*(Dual a, double b) { return {a.v * b, a.d * b}; }
+inline Dual operator*(double a, Dual b) { return {a * b.v, a * b.d}; }
+inline Dual operator/(Dual a, double b) { return {a.v / b, a.d / b}; }
+inline Dual operator/(double a, Dual b) { return Dual(a) / b; }
+inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+
+inline double val(double x) { return x; }
+inline double val(const Dual& x) { return x.v; }
+inline double sgn(double x) { return (x > 0) - (x < 0); }
+inline double absval(double x) { return std::fabs(x); }
+// |x| with d|x|/dx = sign(x), sign(0) = 0.
+inline Dual absval(const Dual& x) { return {std::fabs(x.v), sgn(x.v) * x.d}; }
+
+// ---------------------------------------------------------------------------
+// Discrete velocity model, Eq. (2): v_ki = v_k (cos(2 pi (i-1)/N_i),
+// sin(2 pi (i-1)/N_i)), k = 1..4, i = 1..N_i, plus the rest velocity v_0 = 0
+// counted once.  Index q = 0 is the rest velocity, q = 1 + (k-1) N_i + (i-1).
+// ---------------------------------------------------------------------------
+struct Dvm {
+  int n_dirs, Q;
+  double speed[5];
+  double B[5];
+  std::vector<double> vx, vy;
+  std::vector<int> shell, dir;  // shell k (0..4) and direction i (1..N_i; 0 for rest)
+};
+
+Dvm make_dvm(int n_dirs, const double* speeds, const double* B) {
+  Dvm d;
+  d.n_dirs = n_dirs;
+  d.Q = 1 + 4 * n_dirs;
+  for (int k = 0; k < 5; ++k) { d.speed[k] = speeds[k]; d.B[k] = B[k]; }
+  d.vx.assign(d.Q, 0.0); d.vy.assign(d.Q, 0.0);
+  d.shell.assign(d.Q, 0); d.dir.assign(d.Q, 0);
+  for (int k = 1; k <= 4; ++k)
+    for (int i = 1; i <= n_dirs; ++i) {
+      int q = 1 + (k - 1) * n_dirs + (i - 1);
+      double phi = 2.0 * M_PI * (i - 1) / n_dirs;
+      d.vx[q] = speeds[k] * std::cos(phi);
+      d.vy[q] = speeds[k] * std::sin(phi);
+      d.shell[q] = k;
+      d.dir[q] = i;
+    }
+  return d;
+}
+
+// mod{a, b} of Eq. (12).
+int paper_mod(int a, int b) { return a <= b ? a : a - b; }
+
+// Weights F_k(E), Eq. (11a) for k = 1..4 and Eq. (11b) for F_0.
+template <class T>
+void weights(const Dvm& d, T E, T F[5]) {
+  for (int k = 1; k <= 4; ++k) {
+    double vk2 = d.speed[k] * d.speed[k];
+    double a = d.speed[paper_mod(k + 1, 4)] * d.speed[paper_mod(k + 1, 4)];
+    double b = d.speed[paper_mod(k + 2, 4)] * d.speed[paper_mod(k + 2, 4)];
+    double c = d.speed[paper_mod(k + 3, 4)] * d.speed[paper_mod(k + 3, 4)];
+    T E2 = E * E, E3 = E2 * E, E4 = E3 * E;
+    T num = d.B[4] * E4 + d.B[3] * (a + b + c) * E3 + d.B[2] * (a * b + b * c + c * a) * E2 +
+            d.B[1] * (a * b * c) * E;
+    double den = vk2 * (vk2 - a) * (vk2 - b) * (vk2 - c);
+    F[k] = num / den;
+  }
+  F[0] = 1.0 - d.B[0] * (F[1] + F[2] + F[3] + F[4]);
+}
+
+// Equilibrium distribution, Eq. (10), for one node.
+template <class T>
+void feq_node(const Dvm& d, T rho, T ux, T uy, T E, T* feq) {
+  T F[5];
+  weights(d, E, F);
+  T u2 = ux * ux + uy * uy;
+  T a = 1.0 - u2 / (2.0 * E);
+  for (int q = 0; q < d.Q; ++q) {
+    T vu = d.vx[q] * ux + d.vy[q] * uy;  // v_{ki eps} u_eps
+    T bracket = (1.0 - u2 / (2.0 * E) + u2 * u2 / (8.0 * E * E)) + (vu / E) * a +
+                (vu * vu / (2.0 * E * E)) * a + vu * vu * vu / (6.0 * E * E * E) +
+                vu * vu * vu * vu / (24.0 * E * E * E * E);
+    feq[q] = rho * F[d.shell[q]] * bracket;
+  }
+}
+
+// Macroscopic moments of one node, Eqs. (3)-(5): rho = sum f,
+// rho u = sum f v, rho E = sum f |v - u|^2 / 2.  f[q * stride].
+template <class T>
+void moments_node(const Dvm& d, const T* f, long stride, T& rho, T& ux, T& uy, T& E) {
+  T s0 = 0.0, sx = 0.0, sy = 0.0;
+  for (int q = 0; q < d.Q; ++q) {
+    T fq = f[q * stride];
+    s0 += fq;
+    sx += fq * d.vx[q];
+    sy += fq * d.vy[q];
+  }
+  rho = s0;
+  ux = sx / rho;
+  uy = sy / rho;
+  T se = 0.0;
+  for (int q = 0; q < d.Q; ++q) {
+    T cx = d.vx[q] - ux, cy = d.vy[q] - uy;
+    se += 0.5 * f[q * stride] * (cx * cx + cy * cy);
+  }
+  E = se / rho;
+}
+
+// The Modified Warming-Beam increment of Eq. (28) for one node, i.e.
+//   [C + C (1 - |C|) (1 - S(eta)) (1 - eta) / 2] * delta
+// with delta and eta taken on the upwind side chosen by the sign of C
+// (Eq. 27 / the definitions under Eq. 38) and S(eta) = (|eta| - 1)/(|eta| + 1)
+// (Eq. 37).  Arguments are psi_{j-2} .. psi_{j+2}.
+template <class T>
+T mwb_increment(double C, T pm2, T pm1, T p0, T pp1, T pp2) {
+  T delta, upstream;
+  if (C >= 0) {
+    delta = p0 - pm1;
+    upstream = pm1 - pm2;
+  } else {
+    delta = pp1 - p0;
+    upstream = pp2 - pp1;
+  }
+  if (val(delta) == 0.0) return C * delta;  // limit of the bracket times delta
+  T eta = upstream / delta;
+  if (!std::isfinite(val(eta)))  // |eta| -> infinity: (1-S)(1-eta) delta -> -2|delta| sign(upstream)
+    return C * delta - C * (1.0 - std::fabs(C)) * absval(delta) * sgn(val(upstream));
+  T S = (absval(eta) - 1.0) / (absval(eta) + 1.0);
+  return (C + 0.5 * C * (1.0 - std::fabs(C)) * (1.0 - S) * (1.0 - eta)) * delta;
+}
+
+}  // namespace
+
+// ============================================================================
+// C interface (ctypes).
+// ============================================================================
+extern "C" {
+
+typedef struct {
+  int32_t n_r, n_theta;     // interior nodes in r and theta
+  int32_t n_dirs, n_f;      // N_i directions; N_f sector periods (n_f == n_dirs: full circle)
+  double r_in, r_out;       // R1, R2
+  double speeds[5];         // v_0 .. v_4
+  double B[5];              // B[n] = B_n of Table I (B[0] is the F_0 factor)
+  double tau, dt;
+  int32_t bc_kind[2];       // inner, outer: 0 extrapolate, 1 wall (u given), 2 all given
+  const double* bc_values[2];  // [2 layers][4 fields rho,u_r,u_theta,T][n_theta]
+} orc_problem;
+
+enum { ORC_OK = 0, ORC_NONPHYS = 1, ORC_NONFINITE = 2, ORC_EINVAL = 4 };
+
+}  // extern "C"
+
+namespace {
+
+// One time step of Eq. (38) with the boundary nodes of Sec. II C.
+// f_in, f_out: [Q][n_theta][n_r].  Returns a status bitmask.
+template <class T>
+int step_impl(const orc_problem& P, const Dvm& d, const T* f_in, T* f_out, bool parallel) {
+  const int NR = P.n_r, NT = P.n_theta, Q = d.Q;
+  const double dr = (P.r_out - P.r_in) / (NR - 1);                       // Sec. II C 1
+  const double dth = 2.0 * M_PI * P.n_f / (double(P.n_dirs) * NT);       // Sec. II C 2
+  const double decay = std::exp(-P.dt / P.tau);                          // Eq. (19)
+
+  // Extended array with two ghost layers on every side; corner ghosts are
+  // never read by the axis-aligned stencils and stay NaN.
+  const int ER = NR + 4, ET = NT + 4;
+  std::vector<T> g((size_t)Q * ET * ER, T(std::numeric_limits<double>::quiet_NaN()));
+  auto G = [&](int q, int it, int ir) -> T& {  // it, ir: 0-based interior index, ghosts -2,-1,N,N+1
+    return g[((size_t)q * ET + (it + 2)) * ER + (ir + 2)];
+  };
+  for (int q = 0; q < Q; ++q)
+    for (int it = 0; it < NT; ++it)
+      for (int ir = 0; ir < NR; ++ir) G(q, it, ir) = f_in[((size_t)q * NT + it) * NR + ir];
+
+  int status = 0;
+
+  // (1) Radial ghost nodes, Sec. II C 1: macroscopic quantities from Eq. (39)
+  //     (or prescribed), f = f^eq there.
+  for (int it = 0; it < NT; ++it) {
+    const double theta = (it + 1) * dth;
+    const double c = std::cos(theta), s = std::sin(theta);
+    for (int side = 0; side < 2; ++side) {
+      const int ia = side == 0 ? 0 : NR - 1;       // wall node i_r = 1 or N_r
+      const int ib = side == 0 ? 1 : NR - 2;       // next node inward
+      const int g1 = side == 0 ? -1 : NR;          // adjacent ghost (i_r = 0 or N_r + 1)
+      const int g2 = side == 0 ? -2 : NR + 1;      // outer ghost (i_r = -1 or N_r + 2)
+      const long stride = (long)ET * ER;
+      T ra, uxa, uya, Ea, rb, uxb, uyb, Eb;
+      moments_node(d, &G(0, it, ia), stride, ra, uxa, uya, Ea);
+      moments_node(d, &G(0, it, ib), stride, rb, uxb, uyb, Eb);
+      T rho1 = 2.0 * ra - rb, rho2 = 2.0 * rho1 - ra;   // Eq. (39), applied twice
+      T E1 = 2.0 * Ea - Eb, E2 = 2.0 * E1 - Ea;         // "temperature in a similar way"
+      T ux1 = 2.0 * uxa - uxb, ux2 = 2.0 * ux1 - uxa;
+      T uy1 = 2.0 * uya - uyb, uy2 = 2.0 * uy1 - uya;
+      const int kind = P.bc_kind[side];
+      const double* V = P.bc_values[side];
+      auto given = [&](int layer, int field) { return V[((size_t)layer * 4 + field) * NT + it]; };
+      if (kind == 1 || kind == 2) {  // prescribed polar velocity at the ghost nodes
+        ux1 = T(given(0, 1) * c - given(0, 2) * s);
+        uy1 = T(given(0, 1) * s + given(0, 2) * c);
+        ux2 = T(given(1, 1) * c - given(1, 2) * s);
+        uy2 = T(given(1, 1) * s + given(1, 2) * c);
+      }
+      if (kind == 2) {
+        rho1 = T(given(0, 0)); E1 = T(given(0, 3));
+        rho2 = T(given(1, 0)); E2 = T(given(1, 3));
+      }
+      if (!(val(rho1) > 0 && val(rho2) > 0 && val(E1) > 0 && val(E2) > 0)) status |= ORC_NONPHYS;
+      std::vector<T> fe(Q);
+      feq_node(d, rho1, ux1, uy1, E1, fe.data());
+      for (int q = 0; q < Q; ++q) G(q, it, g1) = fe[q];
+      feq_node(d, rho2, ux2, uy2, E2, fe.data());
+      for (int q = 0; q < Q; ++q) G(q, it, g2) = fe[q];
+    }
+  }
+
+  // (2) Azimuthal ghost nodes, Eq. (40): copies of the rows at the other end
+  //     of the period with the direction label rotated by N_f.
+  for (int q = 0; q < Q; ++q) {
+    int q_lo = q, q_hi = q;  // source labels for i_theta <= 0 and i_theta > N_theta
+    if (d.shell[q] > 0) {
+      int k = d.shell[q], i = d.dir[q];
+      int i_lo = paper_mod(i + P.n_f, P.n_dirs);
+      int i_hi = paper_mod(i - P.n_f + P.n_dirs, P.n_dirs);
+      q_lo = 1 + (k - 1) * P.n_dirs + (i_lo - 1);
+      q_hi = 1 + (k - 1) * P.n_dirs + (i_hi - 1);
+    }
+    for (int ir = 0; ir < NR; ++ir) {
+      G(q, -2, ir) = G(q_lo, NT - 2, ir);
+      G(q, -1, ir) = G(q_lo, NT - 1, ir);
+      G(q, NT, ir) = G(q_hi, 0, ir);
+      G(q, NT + 1, ir) = G(q_hi, 1, ir);
+    }
+  }
+
+  // (3) Combined scheme, Eq. (38), at every node.
+#pragma omp parallel for schedule(static) reduction(| : status) if (parallel)
+  for (int it = 0; it < NT; ++it) {
+    const double theta = (it + 1) * dth;
+    const double c = std::cos(theta), s = std::sin(theta);
+    std::vector<T> fe(Q);
+    for (int ir = 0; ir < NR; ++ir) {
+      const double r = P.r_in + ir * dr;
+      T rho, ux, uy, E;
+      moments_node(d, &G(0, it, ir), (long)ET * ER, rho, ux, uy, E);
+      if (!(val(rho) > 0 && val(E) > 0)) status |= ORC_NONPHYS;
+      feq_node(d, rho, ux, uy, E, fe.data());
+      for (int q = 0; q < Q; ++q) {
+        const double v_r = d.vx[q] * c + d.vy[q] * s;
+        const double v_t = -d.vx[q] * s + d.vy[q] * c;
+        const double C_r = v_r * P.dt / dr;
+        const double C_t = v_t * P.dt / (r * dth);
+        T f = G(q, it, ir);
+        T relax = fe[q] + (f - fe[q]) * decay;
+        T term_r = mwb_increment(C_r, G(q, it, ir - 2), G(q, it, ir - 1), f, G(q, it, ir + 1),
+                                 G(q, it, ir + 2));
+        T term_t = mwb_increment(C_t, G(q, it - 2, ir), G(q, it - 1, ir), f, G(q, it + 1, ir),
+                                 G(q, it + 2, ir));
+        T out = relax - term_r - term_t;
+        if (!std::isfinite(val(out))) status |= ORC_NONFINITE;
+        f_out[((size_t)q * NT + it) * NR + ir] = out;
+      }
+    }
+  }
+  return status;
+}
+
+bool valid(const orc_problem* P) {
+  if (!P) return false;
+  if (P->n_r < 3 || P->n_theta < 2) return false;
+  if (P->n_dirs < 1 || P->n_f < 1 || P->n_f > P->n_dirs) return false;
+  if (!(P->r_out > P->r_in) || !(P->r_in > 0) || !(P->tau > 0) || !(P->dt > 0)) return false;
+  for (int s = 0; s < 2; ++s)
+    if (P->bc_kind[s] != 0 && P->bc_values[s] == nullptr) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int orc_q(int n_dirs) { return 1 + 4 * n_dirs; }
+
+void orc_dvm(int n_dirs, const double* speeds, double* vx, double* vy, int32_t* shell) {
+  const double B[5] = {0, 0, 0, 0, 0};
+  Dvm d = make_dvm(n_dirs, speeds, B);
+  for (int q = 0; q < d.Q; ++q) { vx[q] = d.vx[q]; vy[q] = d.vy[q]; shell[q] = d.shell[q]; }
+}
+
+void orc_weights(int n_dirs, const double* speeds, const double* B, double E, double* F) {
+  Dvm d = make_dvm(n_dirs, speeds, B);
+  weights(d, E, F);
+}
+
+void orc_feq(int n_dirs, const double* speeds, const double* B, double rho, double ux, double uy,
+             double E, double* feq) {
+  Dvm d = make_dvm(n_dirs, speeds, B);
+  feq_node(d, rho, ux, uy, E, feq);
+}
+
+// out = (rho, u_x, u_y, E)
+void orc_moments(int n_dirs, const double* speeds, const double* f, double* out) {
+  const double B[5] = {0, 0, 0, 0, 0};
+  Dvm d = make_dvm(n_dirs, speeds, B);
+  moments_node(d, f, 1, out[0], out[1], out[2], out[3]);
+}
+
+double orc_mwb_increment(double C, double pm2, double pm1, double p0, double pp1, double pp2) {
+  return mwb_increment(C, pm2, pm1, p0, pp1, pp2);
+}
+
+// The bare MWB scheme, Eq. (28), on a periodic 1-D array with constant C.
+void orc_mwb_1d(int n, const double* psi, double C, double* out) {
+  for (int j = 0; j < n; ++j) {
+    auto at = [&](int k) { return psi[((k % n) + n) % n]; };
+    out[j] = psi[j] - mwb_increment(C, at(j - 2), at(j - 1), at(j), at(j + 1), at(j + 2));
+  }
+}
+
+// f = f^eq of the given fields (initially in equilibrium).  Fields
+// [n_theta][n_r], polar velocity components; f: [Q][n_theta][n_r].
+int orc_set_state(const orc_problem* P, const double* rho, const double* u_r, const double* u_t,
+                  const double* T, double* f) {
+  if (!valid(P)) return ORC_EINVAL;
+  Dvm d = make_dvm(P->n_dirs, P->speeds, P->B);
+  const int NR = P->n_r, NT = P->n_theta;
+  const double dth = 2.0 * M_PI * P->n_f / (double(P->n_dirs) * NT);
+  std::vector<double> fe(d.Q);
+  int status = 0;
+  for (int it = 0; it < NT; ++it) {
+    const double th = (it + 1) * dth, c = std::cos(th), s = std::sin(th);
+    for (int ir = 0; ir < NR; ++ir) {
+      size_t n = (size_t)it * NR + ir;
+      if (!(rho[n] > 0 && T[n] > 0)) status |= ORC_NONPHYS;
+      double ux = u_r[n] * c - u_t[n] * s, uy = u_r[n] * s + u_t[n] * c;
+      feq_node(d, rho[n], ux, uy, T[n], fe.data());  // E = T / (gamma - 1), gamma = 2
+      for (int q = 0; q < d.Q; ++q) f[((size_t)q * NT + it) * NR + ir] = fe[q];
+    }
+  }
+  return status;
+}
+
+// rho, u_r, u_theta, T of every node from f (any output may be NULL).
+int orc_fields(const orc_problem* P, const double* f, double* rho, double* u_r, double* u_t,
+               double* T) {
+  if (!valid(P)) return ORC_EINVAL;
+  Dvm d = make_dvm(P->n_dirs, P->speeds, P->B);
+  const int NR = P->n_r, NT = P->n_theta;
+  const double dth = 2.0 * M_PI * P->n_f / (double(P->n_dirs) * NT);
+  for (int it = 0; it < NT; ++it) {
+    const double th = (it + 1) * dth, c = std::cos(th), s = std::sin(th);
+    for (int ir = 0; ir < NR; ++ir) {
+      size_t n = (size_t)it * NR + ir;
+      double r_, ux, uy, E;
+      moments_node(d, f + n, (long)NT * NR, r_, ux, uy, E);
+      if (rho) rho[n] = r_;
+      if (u_r) u_r[n] = ux * c + uy * s;
+      if (u_t) u_t[n] = -ux * s + uy * c;
+      if (T) T[n] = E;
+    }
+  }
+  return 0;
+}
+
+// Global integrals with the polar area element r dr dtheta:
+// out = (mass, x-momentum, y-momentum, total energy, min rho, min T).
+int orc_diagnostics(const orc_problem* P, const double* f, double* out) {
+  if (!valid(P)) return ORC_EINVAL;
+  Dvm d = make_dvm(P->n_dirs, P->speeds, P->B);
+  const int NR = P->n_r, NT = P->n_theta;
+  const double dr = (P->r_out - P->r_in) / (NR - 1);
+  const double dth = 2.0 * M_PI * P->n_f / (double(P->n_dirs) * NT);
+  double m = 0, jx = 0, jy = 0, e = 0, rmin = INFINITY, tmin = INFINITY;
+  for (int it = 0; it < NT; ++it)
+    for (int ir = 0; ir < NR; ++ir) {
+      size_t n = (size_t)it * NR + ir;
+      double rho, ux, uy, E;
+      moments_node(d, f + n, (long)NT * NR, rho, ux, uy, E);
+      double w = (P->r_in + ir * dr) * dr * dth;
+      m += w * rho;
+      jx += w * rho * ux;
+      jy += w * rho * uy;
+      e += w * rho * (E + 0.5 * (ux * ux + uy * uy));
+      rmin = std::fmin(rmin, rho);
+      tmin = std::fmin(tmin, E);
+    }
+  out[0] = m; out[1] = jx; out[2] = jy; out[3] = e; out[4] = rmin; out[5] = tmin;
+  return 0;
+}
+
+// One step of Eq. (38).  f_in, f_out: [Q][n_theta][n_r].
+int orc_step(const orc_problem* P, const double* f_in, double* f_out, int parallel) {
+  if (!valid(P)) return ORC_EINVAL;
+  Dvm d = make_dvm(P->n_dirs, P->speeds, P->B);
+  return step_impl<double>(*P, d, f_in, f_out, parallel != 0);
+}
+
+// n steps; f is updated in place.
+int orc_run(const orc_problem* P, double* f, int n, int parallel) {
+  if (!valid(P)) return ORC_EINVAL;
+  Dvm d = make_dvm(P->n_dirs, P->speeds, P->B);
+  size_t N = (size_t)d.Q * P->n_theta * P->n_r;
+  std::vector<double> tmp(N);
+  int status = 0;
+  for (int s = 0; s < n; ++s) {
+    status |= step_impl<double>(*P, d, f, tmp.data(), parallel != 0);
+    std::memcpy(f, tmp.data(), N * sizeof(double));
+  }
+  return status;
+}
+
+// Directional derivative of one step: df_out = J(f) df.
+int orc_step_jvp(const orc_problem* P, const double* f, const double* df, double* df_out) {
+  if (!valid(P)) return ORC_EINVAL;
+  Dvm d = make_dvm(P->n_dirs, P->speeds, P->B);
+  size_t N = (size_t)d.Q * P->n_theta * P->n_r;
+  std::vector<Dual> x(N), y(N);
+  for (size_t i = 0; i < N; ++i) x[i] = Dual(f[i], df[i]);
+  int st = step_impl<Dual>(*P, d, x.data(), y.data(), false);
+  for (size_t i = 0; i < N; ++i) df_out[i] = y[i].d;
+  return st;
+}
+
+// Adjoint (vector-Jacobian product) of one step: lam_n = J(f_n)^T lam_np1,
+// computed by its definition, one forward-mode column per input entry:
+// lam_n[j] = < lam_np1, J e_j >.  Cost O(N^2): small grids only.
+int orc_adjoint_step(const orc_problem* P, const double* f_n, const double* lam_np1,
+                     double* lam_n) {
+  if (!valid(P)) return ORC_EINVAL;
+  Dvm d = make_dvm(P->n_dirs, P->speeds, P->B);
+  const long N = (long)d.Q * P->n_theta * P->n_r;
+  int status = 0;
+#pragma omp parallel reduction(| : status)
+  {
+    std::vector<Dual> x(N), y(N);
+#pragma omp for schedule(dynamic, 16)
+    for (long j = 0; j < N; ++j) {
+      for (long i = 0; i < N; ++i) x[i] = Dual(f_n[i], i == j ? 1.0 : 0.0);
+      status |= step_impl<Dual>(*P, d, x.data(), y.data(), false);
+      double acc = 0.0;
+      for (long i = 0; i < N; ++i) acc += lam_np1[i] * y[i].d;
+      lam_n[j] = acc;
+    }
+  }
+  return status;
+}
+
+}  // extern "C"
