@@ -1,0 +1,341 @@
+"""Throughput benchmark of the polar-coordinate FDLB step on GB300.
+
+Default workload: the Kelvin-Helmholtz annulus, N_r x N_theta = 4096 x 4096,
+33 velocities, FP32 with double-precision temperature recovery.  One "step"
+is one time step of the combined scheme over the whole grid (one fused kernel
+launch).  The distribution (2 x 2.2 GB) is far larger than L2, so no flush is
+needed between steps.
+
+Prints ONE JSON line.  Keys beyond the base contract:
+  roofline      dominant kernel (the fused step) against measured HBM bandwidth
+  cpu_baseline  the FP64 CPU oracle timed on this host on a bounded sample
+  fp64          the same workload through the FP64 path (value + roofline)
+  e2e           the metric through pclb_run_host with page-locked host buffers
+  clocks        SM clocks / throttle reasons sampled during the timed region
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload kh|rm|rm_adj|shock|rot] [--no-cpu-baseline]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell·velocity updates/s + %HBM roofline: FP32 vs FP64 step; adjoint/forward"
+UNIT = "cell·velocity updates/s"
+Q = 33
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def _workload(name: str):
+    from paper_1302_7104_gb300 import inputs as I
+    return {
+        "kh": lambda: I.kh(),
+        "rm": lambda: I.rm(),
+        "rm_adj": lambda: I.rm_adj(),
+        "shock": lambda: I.shock(),
+        "rot": lambda: I.rot(),
+    }[name]()
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _kernel_hash() -> str:
+    h = hashlib.sha256()
+    for rel in ("paper_1302_7104_gb300/csrc/step_kernel.cu", "paper_1302_7104_gb300/csrc/device_common.cuh",
+                "paper_1302_7104_gb300/csrc/pclb_internal.h"):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(kernel_tag: str, cells: int):
+    """DRAM bytes per launch from the committed ncu summary for this kernel,
+    scaled to `cells`, or None if the kernel changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        line = line.strip()
+        if line.startswith("#") or ":" not in line:
+            continue
+        k, v = line.split(":", 1)
+        rec[k.strip()] = v.strip()
+    if rec.get("source_hash") != _kernel_hash():
+        return None
+    key = f"{kernel_tag}_bytes_per_cell"
+    if key not in rec:
+        return None
+    return float(rec[key]) * cells
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons in the background."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, p in zip(names, parts[3:7]):
+                if p.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def time_steps(g, steps: int, warmup: int, torch):
+    """Warm up, then time exactly `steps` steps with CUDA events on the
+    context's stream.  Returns seconds."""
+    g.step(warmup)
+    g.sync()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(g.stream)
+    for _ in range(steps):
+        g.step(1)
+    end.record(g.stream)
+    end.synchronize()
+    return start.elapsed_time(end) / 1e3
+
+
+def cpu_baseline(wname: str, n_theta: int = 256, steps: int = 2):
+    """The FP64 oracle as it stands, on a radial band of the workload: the full
+    radial resolution with `n_theta` azimuthal nodes, `steps` steps."""
+    import oracle as O
+    from paper_1302_7104_gb300 import inputs as I
+    full = {"kh": I.kh, "rm": I.rm, "rm_adj": I.rm_adj, "shock": I.shock, "rot": I.rot}[wname]
+    w = full(n_theta=min(n_theta, full().n_theta)) if wname != "rot" else full()
+    f = O.set_state(w)
+    t0 = time.perf_counter()
+    O.run(w, f, steps)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    ups = w.n_r * w.n_theta * Q * steps / dt
+    return {"value": ups, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{wname} radial band {w.n_r}x{w.n_theta} (full radial resolution), {steps} steps, "
+                      f"FP64, OpenMP over theta rows, {dt:.1f} s"}
+
+
+def run_ours(args):
+    import torch
+    from paper_1302_7104_gb300 import pclb as P
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = _workload(args.workload)
+    cells = w.n_r * w.n_theta
+    updates = cells * Q
+    hbm, peak_src = _peaks()
+
+    g = P.PCLB(w, precision="fp32", device=f"cuda:{local}")
+    g.set_state()
+    g.sync()
+    clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    secs = time_steps(g, args.steps, args.warmup, torch)
+    clk = clocks.stop()
+    flags = g.status_flags()
+    if ws > 1:
+        t = torch.tensor([secs], device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        secs = float(t.item())
+    value = updates * args.steps * ws / secs
+    per_launch = secs / args.steps
+    alg_bytes = updates * 8.0
+    achieved = alg_bytes / per_launch / 1e9
+    traffic = _profiled_traffic("fp32", cells)
+
+    # e2e: the same metric through the host-buffer C ABI call, copies included
+    pinned = [torch.as_tensor(x, dtype=torch.float32).pin_memory() for x in w.fields()]
+    outs = [torch.empty((w.n_theta, w.n_r), dtype=torch.float32).pin_memory() for _ in range(4)]
+    for _ in range(max(1, min(args.warmup, 2))):
+        g.run_host(*pinned, 1, outs)
+    e2e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.run_host(*pinned, 1, outs)
+    e2e_secs = time.perf_counter() - t0
+    e2e_value = updates * e2e_steps * ws / e2e_secs
+    io_bytes = 4 * cells * 4
+    g.close()
+    del pinned, outs
+
+    # FP64 step on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        g64 = P.PCLB(w, precision="fp64", device=f"cuda:{local}")
+        g64.set_state()
+        g64.sync()
+        k64 = max(3, min(args.steps, 10))
+        s64 = time_steps(g64, k64, 2, torch)
+        g64.close()
+        fp64 = {"value": updates * k64 / s64, "unit": UNIT, "steps": k64, "ms_per_step": s64 / k64 * 1e3,
+                "roofline": {"bound": "hbm", "achieved": updates * 16.0 / (s64 / k64) / 1e9, "peak": hbm,
+                             "unit": "GB/s", "frac": updates * 16.0 / (s64 / k64) / 1e9 / hbm,
+                             "traffic": _profiled_traffic("fp64", cells)}}
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_launch * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}_{w.n_r}x{w.n_theta}_q33_fp32", "n_r": w.n_r,
+                   "n_theta": w.n_theta, "velocities": Q, "cells": cells, "tau": w.tau, "dt": w.dt,
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                   "l2": "state 2 x %.2f GB > 129 MB L2, no flush needed" % (updates * 4 / 1e9),
+                   "T_recovery": "fp64"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src,
+                     "kernel": "pclb::step_kernel<float>", "alg_bytes_per_launch": alg_bytes},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+                "d2h_bytes_per_step": io_bytes, "steps": e2e_steps},
+        "gpu_launches": args.steps,
+        "status_flags": flags,
+    }
+    if fp64 is not None:
+        line["fp64"] = fp64
+    if clk is not None:
+        line["clocks"] = clk
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_1302_7104_gb300 import inputs as I
+    full = _workload(args.workload)
+    w = {"kh": I.kh, "rm": I.rm, "rm_adj": I.rm_adj, "shock": I.shock, "rot": I.rot}[args.workload](
+        n_theta=min(128, full.n_theta)) if args.workload != "rot" else full
+    f = O.set_state(w)
+    prob = O.Problem(w)
+    f = O.run(w, f, args.warmup, prob=prob)
+    t0 = time.perf_counter()
+    O.run(w, f, args.steps, prob=prob)
+    secs = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = w.n_r * w.n_theta * Q * args.steps / secs
+    sample = (f"{args.workload} radial band {w.n_r}x{w.n_theta} (full radial resolution), FP64 oracle, "
+              f"OpenMP over theta rows")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}_{full.n_r}x{full.n_theta}_q33_fp32",
+                       "sample_n_theta": w.n_theta},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="kh", choices=["kh", "rm", "rm_adj", "shock", "rot"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

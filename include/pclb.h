@@ -1,0 +1,201 @@
+/*
+ * pclb.h -- C ABI of the GB300 polar-coordinate lattice Boltzmann library.
+ *
+ * The library advances the discrete distribution f of the polar-coordinate
+ * finite-difference lattice Boltzmann model (Lin, Xu, Zhang, Li & Succi,
+ * "Polar coordinate lattice Boltzmann modeling of compressible flows") on an
+ * annulus R1 <= r <= R2, 0 < theta <= 2 pi N_f / N_i, one GPU, one stream.
+ *
+ * One time step is the combined scheme of Eq. (38): at every node and for
+ * every discrete velocity, the analytic BGK relaxation of Eq. (19) towards
+ * the equilibrium of Eq. (10) (weights Eqs. 11a-12, Table I), minus the
+ * Modified Warming-Beam increments of Eq. (28) (switch function Eq. 37) in r
+ * and in theta, all evaluated from the distribution at time t.  Boundary
+ * nodes follow Sec. II C: two radial ghost layers per wall in equilibrium
+ * with extrapolated (Eq. 39) or prescribed macroscopic values, and periodic
+ * azimuthal ghosts with the direction label rotated by N_f (Eq. 40).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Velocity index q: q = 0 is the rest velocity; q = 1 + (k-1) N_i + (i-1)
+ *    for shell k = 1..4 and direction i = 1..N_i, v_ki = v_k (cos phi_i,
+ *    sin phi_i), phi_i = 2 pi (i-1)/N_i (Eq. 2).  Q = 1 + 4 N_i.  Labels are
+ *    fixed in Cartesian space.
+ *  * Nodes: r = R1 + i_r dr, i_r = 0..n_r-1, dr = (R2-R1)/(n_r-1) (both walls
+ *    are nodes); theta = (i_t + 1) dtheta, i_t = 0..n_theta-1,
+ *    dtheta = 2 pi n_f / (n_dirs n_theta).
+ *  * Field arrays are [n_theta][n_r], r fastest, contiguous.  Distribution
+ *    arrays are [Q][n_theta][n_r], contiguous.  The element type is float for
+ *    PCLB_FP32 and double for PCLB_FP64.  Velocities are polar (u_r,
+ *    u_theta) at the node's theta.  T is the temperature, equal to the
+ *    internal energy E for the paper's gamma = 2.
+ *  * Pointers marked "device" must be CUDA device memory (or managed memory)
+ *    of the context's device; "host" pointers are ordinary host memory.
+ *    Caller pointers are borrowed for the duration of the call (device
+ *    pointers until the work queued on the context's stream has run).
+ *  * All device work is queued on the context's CUDA stream and is
+ *    asynchronous unless stated otherwise.  Calls on one context must not be
+ *    made from two host threads at once.
+ *  * Every call returns a pclb_status; PCLB_OK is 0.  On failure nothing has
+ *    been queued unless stated, and pclb_last_error() describes the cause.
+ *    No C++ exception crosses this interface.
+ *
+ * Precision: PCLB_FP32 stores f in float and computes the step in float,
+ * except that the velocity moments are summed with a compensated (two-sum)
+ * accumulation across shells and the temperature recovery
+ * T = (e - |j|^2 / (2 rho)) / rho is done in double.  PCLB_FP64 computes
+ * everything in double.
+ */
+#ifndef PCLB_H
+#define PCLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PCLB_VERSION_MAJOR 0
+#define PCLB_VERSION_MINOR 1
+
+typedef enum {
+  PCLB_OK = 0,
+  PCLB_EINVAL = 1,       /* invalid argument: NULL pointer, size, parameter out of range */
+  PCLB_ENOMEM = 2,       /* the workspace given is smaller than pclb_workspace_size() */
+  PCLB_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  PCLB_ENONPHYS = 4,     /* a node or ghost node had rho <= 0, T <= 0 or a non-finite value */
+  PCLB_ETIMEOUT = 5,     /* a bounded wait for the stream (or a device-side wait) ran out */
+  PCLB_ECFL = 6,         /* max over velocities and nodes of |C_r| + |C_theta| exceeds 1 */
+  PCLB_ESTATE = 7,       /* call out of order, e.g. pclb_step before any state was set */
+  PCLB_EUNSUPPORTED = 8  /* configuration this build does not implement (e.g. n_dirs != 8) */
+} pclb_status;
+
+typedef enum { PCLB_FP32 = 0, PCLB_FP64 = 1 } pclb_precision;
+
+typedef enum {
+  PCLB_BC_EXTRAP = 0,    /* rho, u, T of both ghost layers by linear extrapolation, Eq. (39) */
+  PCLB_BC_WALL = 1,      /* rho, T extrapolated; u_r, u_theta prescribed at the ghost nodes */
+  PCLB_BC_DIRICHLET = 2  /* rho, u_r, u_theta, T prescribed at the ghost nodes */
+} pclb_bc_kind;
+
+/* Device status bits accumulated by the kernels (pclb_status_flags). */
+#define PCLB_FLAG_NONPHYS 1u   /* rho <= 0 or T <= 0 at a node or ghost node */
+#define PCLB_FLAG_NONFINITE 2u /* a non-finite moment or distribution value */
+#define PCLB_FLAG_TIMEOUT 4u   /* a kernel gave up waiting for its own asynchronous copies */
+
+/* Annulus and its grid (Sec. II C). */
+typedef struct {
+  int32_t n_r;      /* radial nodes, >= 3 */
+  int32_t n_theta;  /* azimuthal nodes, >= 2 */
+  double r_in;      /* R1 > 0 */
+  double r_out;     /* R2 > R1 */
+  int32_t n_f;      /* 1 <= n_f <= n_dirs; n_f == n_dirs is the full circle */
+} pclb_grid;
+
+/* Discrete velocity model (Sec. II A): N_k = 4 shells of n_dirs directions
+ * plus the rest velocity. */
+typedef struct {
+  int32_t n_dirs;    /* N_i; this build implements 8 */
+  double speeds[5];  /* v_0 .. v_4; the paper uses 0, 1, 2.92, 2.99, 4.49 */
+  double B[5];       /* B[n] = B_n of Table I (octagon: 8, -1/4, 1, -6, 48) */
+} pclb_dvm;
+
+/* Radial boundary conditions (Sec. II C 1).  values[s] (host, copied by
+ * pclb_create) holds double [2][4][n_theta]: ghost layer (0 = next to the
+ * wall, 1 = outer), field (rho, u_r, u_theta, T), theta node.  It may be
+ * NULL for PCLB_BC_EXTRAP.  Side 0 is the inner wall, side 1 the outer. */
+typedef struct {
+  int32_t kind[2];
+  const double* values[2];
+} pclb_bc;
+
+typedef struct pclb_ctx pclb_ctx;
+
+/* Library version as major * 100 + minor. */
+int32_t pclb_version(void);
+
+/* Text of the last error on ctx, or of the last failed pclb_create /
+ * pclb_workspace_size on this host thread when ctx is NULL.  Never NULL;
+ * valid until the next call on the same context or thread. */
+const char* pclb_last_error(const pclb_ctx* ctx);
+
+/* Bytes of device workspace pclb_create needs for this problem: two
+ * ping-pong copies of f with two azimuthal ghost rows on each side and rows
+ * padded to 32 elements, small tables, the status word and reduction
+ * scratch.  Host-only; queues nothing. */
+pclb_status pclb_workspace_size(const pclb_grid* grid, const pclb_dvm* dvm, pclb_precision prec,
+                                size_t* bytes);
+
+/* Create a context.  tau > 0 is the relaxation time and dt > 0 the time step
+ * of Eq. (38).  workspace (device, 256-byte aligned, at least
+ * pclb_workspace_size() bytes) is owned by the caller and must outlive the
+ * context; the library allocates no device memory of its own.  stream is a
+ * cudaStream_t (NULL = the legacy default stream).  Validates every argument
+ * and the Courant numbers before queuing anything; then uploads the tables
+ * on the stream.  The state is undefined until pclb_set_state or
+ * pclb_set_f. */
+pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, double dt,
+                        pclb_precision prec, const pclb_bc* bc, void* workspace,
+                        size_t workspace_bytes, void* stream, pclb_ctx** out);
+
+/* Release the host-side context (the workspace stays the caller's).
+ * Synchronizes the context's stream first (bounded wait). */
+pclb_status pclb_destroy(pclb_ctx* ctx);
+
+/* Queue later work of ctx on another stream (cudaStream_t). */
+pclb_status pclb_set_stream(pclb_ctx* ctx, void* stream);
+
+/* f = f^eq(rho, u, T) at every node (the initial equilibrium of Sec. III).
+ * rho, u_r, u_theta, T: device, [n_theta][n_r], context precision.
+ * Non-physical inputs set PCLB_FLAG_NONPHYS in the status word. */
+pclb_status pclb_set_state(pclb_ctx* ctx, const void* rho, const void* u_r, const void* u_theta,
+                           const void* T);
+
+/* Copy a distribution in / out: device, [Q][n_theta][n_r], context
+ * precision.  Bitwise; used for checkpoints. */
+pclb_status pclb_set_f(pclb_ctx* ctx, const void* f);
+pclb_status pclb_get_f(pclb_ctx* ctx, void* f);
+
+/* Advance n >= 0 time steps of Eq. (38).  One fused kernel launch per step
+ * (ghost nodes are computed inside it).  Asynchronous; errors found on the
+ * device are reported by pclb_status_flags. */
+pclb_status pclb_step(pclb_ctx* ctx, int32_t n);
+
+/* Macroscopic fields of the current state (Eqs. 3-5): device,
+ * [n_theta][n_r], context precision; any pointer may be NULL. */
+pclb_status pclb_moments(pclb_ctx* ctx, void* rho, void* u_r, void* u_theta, void* T);
+
+/* Global integrals of the current state with the area element r dr dtheta,
+ * summed in double: out[0] mass, out[1] x-momentum, out[2] y-momentum,
+ * out[3] total energy (rho (E + u^2/2)), out[4] min rho, out[5] min T,
+ * out[6] number of nodes, out[7] reserved (0).  out: host, 8 doubles.
+ * Synchronizes the stream (bounded wait). */
+pclb_status pclb_diagnostics(pclb_ctx* ctx, double* out);
+
+/* Read (and if clear != 0, reset) the device status word that the kernels
+ * set (PCLB_FLAG_*).  flags: host.  Synchronizes the stream (bounded wait).
+ * Returns PCLB_ENONPHYS when any flag other than the timeout flag is set,
+ * PCLB_ETIMEOUT when the timeout flag is set, else PCLB_OK. */
+pclb_status pclb_status_flags(pclb_ctx* ctx, uint32_t* flags, int32_t clear);
+
+/* Wait for all work queued on the context's stream, polling for at most
+ * timeout_ms milliseconds (PCLB_ETIMEOUT when it runs out). */
+pclb_status pclb_sync(pclb_ctx* ctx, int32_t timeout_ms);
+
+/* End-to-end call with host buffers: copy rho, u_r, u_theta, T (host,
+ * [n_theta][n_r], context precision) to the device, set f = f^eq, advance n
+ * steps, compute the moments and copy them back to the host arrays
+ * out_rho .. out_T (any may be NULL).  Staging lives in the workspace tail
+ * (pclb_workspace_size reserves it).  For page-locked host memory the copies
+ * are asynchronous DMA; the call returns after the results are on the host
+ * (bounded wait). */
+pclb_status pclb_run_host(pclb_ctx* ctx, const void* rho, const void* u_r, const void* u_theta,
+                          const void* T, int32_t n, void* out_rho, void* out_u_r,
+                          void* out_u_theta, void* out_T);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCLB_H */

@@ -1,0 +1,196 @@
+// Per-node kernels around the step: equilibrium initialisation (f = f^eq of
+// given fields, Eq. 10), macroscopic fields out (Eqs. 3-5), copies between
+// the packed [Q][n_theta][n_r] layout and the stored layout (with azimuthal
+// ghost rows and padded rows), and the global diagnostics reduction.
+#include <cuda_runtime.h>
+#include <float.h>
+
+#include "device_common.cuh"
+#include "pclb_internal.h"
+
+namespace pclb {
+
+// Write value v of label q at interior row t, column r of the stored layout,
+// together with its copies in the azimuthal ghost rows (Eq. 40).
+template <class T>
+__device__ __forceinline__ void store_with_ghosts(T* f, const StepParams& p, const DvmConst<T>& d,
+                                                  int q, int t, int r, T v) {
+  const size_t plane = (size_t)p.rows * p.pitch;
+  f[(size_t)q * plane + (size_t)(t + kGhostRows) * p.pitch + r] = v;
+  if (t >= p.n_theta - 2)
+    f[(size_t)d.recv_lo[q] * plane + (size_t)(t - (p.n_theta - 2)) * p.pitch + r] = v;
+  if (t < 2) f[(size_t)d.recv_hi[q] * plane + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r] = v;
+}
+
+template <class T>
+__global__ void set_state_kernel(T* __restrict__ f, const T* __restrict__ rho, const T* __restrict__ u_r,
+                                 const T* __restrict__ u_t, const T* __restrict__ temp,
+                                 const StepParams p, const DvmConst<T> d) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  if (r >= p.n_r || t >= p.n_theta) return;
+  const size_t n = (size_t)t * p.n_r + r;
+  const T c = (T)p.cos_t[t], s = (T)p.sin_t[t];
+  const T R = rho[n], ur = u_r[n], ut = u_t[n], E = temp[n];  // E = T for gamma = 2
+  if (!(R > T(0) && E > T(0))) atomicOr(p.status, PCLB_FLAG_NONPHYS);
+  const T ux = ur * c - ut * s, uy = ur * s + ut * c;
+  const EqParams<T> e = eq_params<T>((double)R, ux, uy, (double)E, d);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int q_begin = k == 0 ? 0 : 1 + (k - 1) * kNDirs;
+    const int q_end = k == 0 ? 1 : q_begin + kNDirs;
+    for (int q = q_begin; q < q_end; ++q)
+      store_with_ghosts<T>(f, p, d, q, t, r, feq_q<T>(e, d.vx[q], d.vy[q], k));
+  }
+}
+
+template <class T>
+__global__ void moments_kernel(const T* __restrict__ f, T* rho, T* u_r, T* u_t, T* temp,
+                               const StepParams p, const DvmConst<T> d) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  if (r >= p.n_r || t >= p.n_theta) return;
+  const size_t plane = (size_t)p.rows * p.pitch;
+  const NodeState<T> m = node_moments(f + (size_t)(t + kGhostRows) * p.pitch + r, plane, d);
+  const size_t n = (size_t)t * p.n_r + r;
+  const T c = (T)p.cos_t[t], s = (T)p.sin_t[t];
+  if (rho) rho[n] = m.rho;
+  if (u_r) u_r[n] = m.ux * c + m.uy * s;
+  if (u_t) u_t[n] = m.uy * c - m.ux * s;
+  if (temp) temp[n] = m.E;
+}
+
+template <class T>
+__global__ void pack_kernel(const T* __restrict__ f, T* __restrict__ out, const StepParams p) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y, q = blockIdx.z;
+  if (r >= p.n_r) return;
+  out[((size_t)q * p.n_theta + t) * p.n_r + r] =
+      f[(size_t)q * p.rows * p.pitch + (size_t)(t + kGhostRows) * p.pitch + r];
+}
+
+template <class T>
+__global__ void unpack_kernel(const T* __restrict__ in, T* __restrict__ f, const StepParams p,
+                              const DvmConst<T> d) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y, q = blockIdx.z;
+  if (r >= p.n_r) return;
+  store_with_ghosts<T>(f, p, d, q, t, r, in[((size_t)q * p.n_theta + t) * p.n_r + r]);
+}
+
+// Global integrals with weight r dr dtheta, in double.  Each block reduces a
+// fixed grid-stride subset in a fixed order, so results are reproducible.
+template <class T>
+__global__ void diag_partial_kernel(const T* __restrict__ f, double* partials, const StepParams p,
+                                    const DvmConst<T> d, double dr, double dth, double r_in) {
+  const size_t plane = (size_t)p.rows * p.pitch;
+  const size_t n_nodes = (size_t)p.n_r * p.n_theta;
+  double acc[4] = {0, 0, 0, 0};
+  double mn[2] = {DBL_MAX, DBL_MAX};
+  for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes;
+       n += (size_t)gridDim.x * blockDim.x) {
+    const int t = (int)(n / p.n_r), r = (int)(n % p.n_r);
+    const NodeState<T> m = node_moments(f + (size_t)(t + kGhostRows) * p.pitch + r, plane, d);
+    const double w = (r_in + r * dr) * dr * dth;
+    const double rho = (double)m.rho, ux = (double)m.ux, uy = (double)m.uy, E = (double)m.E;
+    acc[0] += w * rho;
+    acc[1] += w * rho * ux;
+    acc[2] += w * rho * uy;
+    acc[3] += w * rho * (E + 0.5 * (ux * ux + uy * uy));
+    mn[0] = fmin(mn[0], rho);
+    mn[1] = fmin(mn[1], E);
+  }
+  __shared__ double red[6][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double v[6] = {acc[0], acc[1], acc[2], acc[3], mn[0], mn[1]};
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    for (int off = 16; off > 0; off >>= 1) {
+      const double o = __shfl_down_sync(0xffffffffu, v[i], off);
+      v[i] = i < 4 ? v[i] + o : fmin(v[i], o);
+    }
+    if (lane == 0) red[i][warp] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x / 32;
+    for (int i = 0; i < 6; ++i) {
+      double s = red[i][0];
+      for (int w = 1; w < nw; ++w) s = i < 4 ? s + red[i][w] : fmin(s, red[i][w]);
+      partials[(size_t)blockIdx.x * 8 + i] = s;
+    }
+  }
+}
+
+__global__ void diag_final_kernel(const double* partials, int n_blocks, double* out, double n_nodes) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s[6] = {0, 0, 0, 0, DBL_MAX, DBL_MAX};
+  for (int b = 0; b < n_blocks; ++b)
+    for (int i = 0; i < 6; ++i)
+      s[i] = i < 4 ? s[i] + partials[(size_t)b * 8 + i] : fmin(s[i], partials[(size_t)b * 8 + i]);
+  for (int i = 0; i < 6; ++i) out[i] = s[i];
+  out[6] = n_nodes;
+  out[7] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+constexpr int kRowThreads = 128;
+
+template <class T>
+cudaError_t launch_set_state(T* f, const T* rho, const T* ur, const T* ut, const T* temp,
+                             const StepParams& p, const DvmConst<T>& d, cudaStream_t s) {
+  dim3 grid((p.n_r + kRowThreads - 1) / kRowThreads, p.n_theta);
+  set_state_kernel<T><<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_moments(const T* f, T* rho, T* ur, T* ut, T* temp, const StepParams& p,
+                           const DvmConst<T>& d, cudaStream_t s) {
+  dim3 grid((p.n_r + kRowThreads - 1) / kRowThreads, p.n_theta);
+  moments_kernel<T><<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_pack(const T* f, T* out, const StepParams& p, cudaStream_t s) {
+  dim3 grid((p.n_r + kRowThreads - 1) / kRowThreads, p.n_theta, kQ);
+  pack_kernel<T><<<grid, kRowThreads, 0, s>>>(f, out, p);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_unpack(const T* in, T* f, const StepParams& p, const DvmConst<T>& d, cudaStream_t s) {
+  dim3 grid((p.n_r + kRowThreads - 1) / kRowThreads, p.n_theta, kQ);
+  unpack_kernel<T><<<grid, kRowThreads, 0, s>>>(in, f, p, d);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_diagnostics(const T* f, double* partials, double* out, const StepParams& p,
+                               const DvmConst<T>& d, double dr, double dth, double r_in,
+                               cudaStream_t s) {
+  diag_partial_kernel<T><<<kDiagBlocks, 256, 0, s>>>(f, partials, p, d, dr, dth, r_in);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_final_kernel<<<1, 32, 0, s>>>(partials, kDiagBlocks, out, (double)p.n_r * p.n_theta);
+  return cudaGetLastError();
+}
+
+#define PCLB_INSTANTIATE(T)                                                                         \
+  template cudaError_t launch_set_state<T>(T*, const T*, const T*, const T*, const T*,             \
+                                           const StepParams&, const DvmConst<T>&, cudaStream_t);   \
+  template cudaError_t launch_moments<T>(const T*, T*, T*, T*, T*, const StepParams&,              \
+                                         const DvmConst<T>&, cudaStream_t);                        \
+  template cudaError_t launch_pack<T>(const T*, T*, const StepParams&, cudaStream_t);              \
+  template cudaError_t launch_unpack<T>(const T*, T*, const StepParams&, const DvmConst<T>&,       \
+                                        cudaStream_t);                                             \
+  template cudaError_t launch_diagnostics<T>(const T*, double*, double*, const StepParams&,        \
+                                             const DvmConst<T>&, double, double, double,           \
+                                             cudaStream_t);
+PCLB_INSTANTIATE(float)
+PCLB_INSTANTIATE(double)
+
+}  // namespace pclb

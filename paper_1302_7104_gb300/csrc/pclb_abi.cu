@@ -1,0 +1,524 @@
+// Host side of the C ABI declared in include/pclb.h: argument validation,
+// workspace layout, host-computed tables, TMA descriptors, launches, bounded
+// waits and error reporting.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "pclb_internal.h"
+
+namespace pclb {
+template <class T>
+cudaError_t launch_step(const CUtensorMap*, T*, const StepParams&, const DvmConst<T>&, cudaStream_t);
+template <class T>
+cudaError_t launch_set_state(T*, const T*, const T*, const T*, const T*, const StepParams&,
+                             const DvmConst<T>&, cudaStream_t);
+template <class T>
+cudaError_t launch_moments(const T*, T*, T*, T*, T*, const StepParams&, const DvmConst<T>&, cudaStream_t);
+template <class T>
+cudaError_t launch_pack(const T*, T*, const StepParams&, cudaStream_t);
+template <class T>
+cudaError_t launch_unpack(const T*, T*, const StepParams&, const DvmConst<T>&, cudaStream_t);
+template <class T>
+cudaError_t launch_diagnostics(const T*, double*, double*, const StepParams&, const DvmConst<T>&,
+                               double, double, double, cudaStream_t);
+}  // namespace pclb
+
+using namespace pclb;
+
+namespace {
+
+thread_local char g_err[512] = "";
+constexpr int kDefaultTimeoutMs = 120000;
+
+struct HostCtx : pclb_ctx {
+  std::vector<double> cos_t, sin_t, inv_r, bc_vals;
+};
+
+pclb_status fail(pclb_ctx* ctx, pclb_status st, const char* fmt, ...) {
+  char* buf = ctx ? ctx->err : g_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+pclb_status cuda_fail(pclb_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, PCLB_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+pclb_status validate(const pclb_grid* g, const pclb_dvm* d, pclb_precision prec) {
+  if (!g || !d) return fail(nullptr, PCLB_EINVAL, "grid and dvm must not be NULL");
+  if (prec != PCLB_FP32 && prec != PCLB_FP64) return fail(nullptr, PCLB_EINVAL, "unknown precision %d", (int)prec);
+  if (g->n_r < 3) return fail(nullptr, PCLB_EINVAL, "n_r = %d; need at least 3 radial nodes", g->n_r);
+  if (g->n_theta < 2) return fail(nullptr, PCLB_EINVAL, "n_theta = %d; need at least 2", g->n_theta);
+  if (g->n_r > (1 << 20) || g->n_theta > (1 << 20))
+    return fail(nullptr, PCLB_EINVAL, "grid %d x %d beyond the supported 2^20 per direction", g->n_r, g->n_theta);
+  if (!(g->r_in > 0.0) || !(g->r_out > g->r_in) || !std::isfinite(g->r_out))
+    return fail(nullptr, PCLB_EINVAL, "need 0 < r_in < r_out (got %g, %g)", g->r_in, g->r_out);
+  if (d->n_dirs != kNDirs)
+    return fail(nullptr, PCLB_EUNSUPPORTED, "n_dirs = %d; this build implements %d directions", d->n_dirs, kNDirs);
+  if (g->n_f < 1 || g->n_f > d->n_dirs)
+    return fail(nullptr, PCLB_EINVAL, "n_f = %d must be in [1, n_dirs]", g->n_f);
+  if (d->speeds[0] != 0.0) return fail(nullptr, PCLB_EINVAL, "speeds[0] must be 0 (rest velocity)");
+  for (int k = 1; k <= 4; ++k) {
+    if (!(d->speeds[k] > 0.0) || !std::isfinite(d->speeds[k]))
+      return fail(nullptr, PCLB_EINVAL, "speeds[%d] must be positive and finite", k);
+    for (int j = 1; j < k; ++j)
+      if (d->speeds[j] == d->speeds[k]) return fail(nullptr, PCLB_EINVAL, "shell speeds must differ");
+  }
+  for (int n = 0; n < 5; ++n)
+    if (!std::isfinite(d->B[n])) return fail(nullptr, PCLB_EINVAL, "B[%d] is not finite", n);
+  return PCLB_OK;
+}
+
+Layout make_layout(const pclb_grid* g, pclb_precision prec) {
+  Layout L{};
+  const size_t es = elem_size(prec);
+  const size_t pitch = align_up((size_t)g->n_r, kPitchAlign);
+  const size_t rows = (size_t)g->n_theta + 2 * kGhostRows;
+  L.f_bytes = align_up((size_t)kQ * rows * pitch * es, 256);
+  size_t off = 0;
+  L.f[0] = off; off += L.f_bytes;
+  L.f[1] = off; off += L.f_bytes;
+  L.cos_t = off; off = align_up(off + (size_t)g->n_theta * 8, 256);
+  L.sin_t = off; off = align_up(off + (size_t)g->n_theta * 8, 256);
+  L.inv_r = off; off = align_up(off + (size_t)g->n_r * 8, 256);
+  L.bc_vals = off; off = align_up(off + (size_t)2 * 2 * 4 * g->n_theta * 8, 256);
+  L.status = off; off = align_up(off + 256, 256);
+  L.partials = off; off = align_up(off + (size_t)kDiagBlocks * 8 * 8, 256);
+  L.diag_out = off; off = align_up(off + 8 * 8, 256);
+  L.stage = off; off = align_up(off + (size_t)8 * g->n_r * g->n_theta * es, 256);
+  L.total = off;
+  return L;
+}
+
+// Weights of Eq. (11a) as polynomials in E: the numerator is
+// sum_n B_n e_{4-n} E^n over the elementary symmetric polynomials e_j of the
+// other three shells' squared speeds (e_0 = 1), the denominator
+// v_k^2 prod_{l != k} (v_k^2 - v_l^2).
+template <class T>
+void fill_dvm(DvmConst<T>& c, const pclb_dvm& d, const pclb_grid& g) {
+  std::memset(&c, 0, sizeof(c));
+  for (int k = 0; k < 5; ++k) {
+    c.speed[k] = (T)d.speeds[k];
+    c.half_v2[k] = (T)(0.5 * d.speeds[k] * d.speeds[k]);
+  }
+  c.B0 = (T)d.B[0];
+  for (int k = 1; k <= 4; ++k) {
+    const double vk2 = d.speeds[k] * d.speeds[k];
+    double o[3];
+    int m = 0;
+    for (int l = 1; l <= 4; ++l)
+      if (l != k) o[m++] = d.speeds[l] * d.speeds[l];
+    const double e1 = o[0] + o[1] + o[2];
+    const double e2 = o[0] * o[1] + o[1] * o[2] + o[2] * o[0];
+    const double e3 = o[0] * o[1] * o[2];
+    const double den = vk2 * (vk2 - o[0]) * (vk2 - o[1]) * (vk2 - o[2]);
+    const double coef[4] = {d.B[1] * e3 / den, d.B[2] * e2 / den, d.B[3] * e1 / den, d.B[4] / den};
+    for (int n = 0; n < 4; ++n) {
+      c.Fc[k][n] = (T)coef[n];
+      c.Fc_lo[k][n] = (T)(coef[n] - (double)c.Fc[k][n]);
+    }
+  }
+  const int nd = d.n_dirs;
+  c.shell[0] = 0;
+  c.recv_lo[0] = 0;
+  c.recv_hi[0] = 0;
+  for (int k = 1; k <= 4; ++k)
+    for (int i = 0; i < nd; ++i) {
+      const int q = 1 + (k - 1) * nd + i;
+      const double phi = 2.0 * M_PI * i / nd;
+      const double cx = std::cos(phi), cy = std::sin(phi);
+      c.cx[q] = (T)cx;
+      c.cy[q] = (T)cy;
+      c.vx[q] = (T)(d.speeds[k] * cx);
+      c.vy[q] = (T)(d.speeds[k] * cy);
+      c.shell[q] = (int8_t)k;
+      // Low ghosts of label (k, j) copy rows of label (k, j + n_f); so rows of
+      // label (k, i) are received by (k, i - n_f); high ghosts the reverse.
+      c.recv_lo[q] = (int8_t)(1 + (k - 1) * nd + ((i - g.n_f) % nd + nd) % nd);
+      c.recv_hi[q] = (int8_t)(1 + (k - 1) * nd + (i + g.n_f) % nd);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+pclb_status make_tmap(pclb_ctx* ctx, int which) {
+  auto enc = get_encode_fn();
+  if (!enc) return fail(ctx, PCLB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const size_t es = elem_size(ctx->prec);
+  cuuint64_t dims[3] = {(cuuint64_t)ctx->grid.n_r, (cuuint64_t)ctx->sp.rows, (cuuint64_t)kQ};
+  cuuint64_t strides[2] = {(cuuint64_t)ctx->sp.pitch * es, (cuuint64_t)ctx->sp.pitch * ctx->sp.rows * es};
+  cuuint32_t box[3] = {(cuuint32_t)kWinR, (cuuint32_t)kWinT, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(&ctx->tmap[which],
+                   ctx->prec == PCLB_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                   3, ctx->ws + ctx->lay.f[which], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, PCLB_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+  return PCLB_OK;
+}
+
+pclb_status bounded_sync(pclb_ctx* ctx, int timeout_ms) {
+  cudaEvent_t ev;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventCreate");
+  e = cudaEventRecord(ev, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(ev);
+    return cuda_fail(ctx, e, "cudaEventRecord");
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  pclb_status st = PCLB_OK;
+  int sleep_us = 1;
+  while (true) {
+    e = cudaEventQuery(ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) {
+      st = cuda_fail(ctx, e, "stream work failed");
+      break;
+    }
+    const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (ms > timeout_ms) {
+      st = fail(ctx, PCLB_ETIMEOUT, "stream did not finish within %d ms", timeout_ms);
+      break;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(sleep_us));
+    if (sleep_us < 200) sleep_us *= 2;
+  }
+  cudaEventDestroy(ev);
+  return st;
+}
+
+template <class T>
+const DvmConst<T>& dvm_of(const pclb_ctx* c);
+template <>
+const DvmConst<float>& dvm_of<float>(const pclb_ctx* c) { return c->dvm32; }
+template <>
+const DvmConst<double>& dvm_of<double>(const pclb_ctx* c) { return c->dvm64; }
+
+template <class T>
+T* fbuf(pclb_ctx* c, int which) { return reinterpret_cast<T*>(c->ws + c->lay.f[which]); }
+
+pclb_status check_launch(pclb_ctx* ctx, cudaError_t e, const char* what) {
+  return e == cudaSuccess ? PCLB_OK : cuda_fail(ctx, e, what);
+}
+
+template <class T>
+pclb_status do_step(pclb_ctx* ctx, int n) {
+  for (int i = 0; i < n; ++i) {
+    const int src = ctx->cur, dst = 1 - ctx->cur;
+    cudaError_t e = launch_step<T>(&ctx->tmap[src], fbuf<T>(ctx, dst), ctx->sp, dvm_of<T>(ctx), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "step kernel launch");
+    ctx->cur = dst;
+  }
+  return PCLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t pclb_version(void) { return PCLB_VERSION_MAJOR * 100 + PCLB_VERSION_MINOR; }
+
+const char* pclb_last_error(const pclb_ctx* ctx) { return ctx ? ctx->err : g_err; }
+
+pclb_status pclb_workspace_size(const pclb_grid* grid, const pclb_dvm* dvm, pclb_precision prec,
+                                size_t* bytes) {
+  if (!bytes) return fail(nullptr, PCLB_EINVAL, "bytes must not be NULL");
+  pclb_status st = validate(grid, dvm, prec);
+  if (st != PCLB_OK) return st;
+  *bytes = make_layout(grid, prec).total;
+  return PCLB_OK;
+}
+
+pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, double dt,
+                        pclb_precision prec, const pclb_bc* bc, void* workspace,
+                        size_t workspace_bytes, void* stream, pclb_ctx** out) {
+  if (!out) return fail(nullptr, PCLB_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  pclb_status st = validate(grid, dvm, prec);
+  if (st != PCLB_OK) return st;
+  if (!(tau > 0.0) || !std::isfinite(tau)) return fail(nullptr, PCLB_EINVAL, "tau must be positive (got %g)", tau);
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, PCLB_EINVAL, "dt must be positive (got %g)", dt);
+  if (!bc) return fail(nullptr, PCLB_EINVAL, "bc must not be NULL");
+  for (int s = 0; s < 2; ++s) {
+    if (bc->kind[s] < PCLB_BC_EXTRAP || bc->kind[s] > PCLB_BC_DIRICHLET)
+      return fail(nullptr, PCLB_EINVAL, "bc kind[%d] = %d is unknown", s, bc->kind[s]);
+    if (bc->kind[s] != PCLB_BC_EXTRAP && !bc->values[s])
+      return fail(nullptr, PCLB_EINVAL, "bc values[%d] must be given for kind %d", s, bc->kind[s]);
+  }
+  if (!workspace) return fail(nullptr, PCLB_EINVAL, "workspace must not be NULL");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
+    return fail(nullptr, PCLB_EINVAL, "workspace must be 256-byte aligned");
+  const Layout lay = make_layout(grid, prec);
+  if (workspace_bytes < lay.total)
+    return fail(nullptr, PCLB_ENOMEM, "workspace has %zu bytes, %zu needed", workspace_bytes, lay.total);
+
+  const int NR = grid->n_r, NT = grid->n_theta;
+  const double dr = (grid->r_out - grid->r_in) / (NR - 1);
+  const double dth = 2.0 * M_PI * grid->n_f / ((double)dvm->n_dirs * NT);
+
+  // Courant numbers: the largest |C_r| + |C_theta| over labels and nodes
+  // (C_theta is largest at the inner wall).
+  double cmax = 0.0;
+  for (int t = 0; t < NT; ++t) {
+    const double th = (t + 1) * dth, c = std::cos(th), s = std::sin(th);
+    for (int k = 1; k <= 4; ++k)
+      for (int i = 0; i < dvm->n_dirs; ++i) {
+        const double phi = 2.0 * M_PI * i / dvm->n_dirs;
+        const double vx = dvm->speeds[k] * std::cos(phi), vy = dvm->speeds[k] * std::sin(phi);
+        const double cr = std::fabs(vx * c + vy * s) * dt / dr;
+        const double ct = std::fabs(-vx * s + vy * c) * dt / (grid->r_in * dth);
+        cmax = std::fmax(cmax, cr + ct);
+      }
+  }
+  if (cmax > 1.0)
+    return fail(nullptr, PCLB_ECFL, "max |C_r| + |C_theta| = %g exceeds 1 (dt too large)", cmax);
+
+  HostCtx* ctx = new (std::nothrow) HostCtx();
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "out of host memory");
+  ctx->grid = *grid;
+  ctx->dvm = *dvm;
+  ctx->prec = prec;
+  ctx->tau = tau;
+  ctx->dt = dt;
+  ctx->bc_kind[0] = (pclb_bc_kind)bc->kind[0];
+  ctx->bc_kind[1] = (pclb_bc_kind)bc->kind[1];
+  ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+  ctx->ws = reinterpret_cast<unsigned char*>(workspace);
+  ctx->lay = lay;
+  ctx->cur = 0;
+  ctx->has_state = false;
+  ctx->err[0] = 0;
+
+  ctx->cos_t.resize(NT);
+  ctx->sin_t.resize(NT);
+  for (int t = 0; t < NT; ++t) {
+    const double th = (t + 1) * dth;
+    ctx->cos_t[t] = std::cos(th);
+    ctx->sin_t[t] = std::sin(th);
+  }
+  ctx->inv_r.resize(NR);
+  for (int r = 0; r < NR; ++r) ctx->inv_r[r] = 1.0 / (grid->r_in + r * dr);
+  ctx->bc_vals.assign((size_t)2 * 2 * 4 * NT, 0.0);
+  for (int s = 0; s < 2; ++s)
+    if (bc->kind[s] != PCLB_BC_EXTRAP)
+      std::memcpy(ctx->bc_vals.data() + (size_t)s * 2 * 4 * NT, bc->values[s], sizeof(double) * 2 * 4 * NT);
+
+  StepParams& sp = ctx->sp;
+  sp.n_r = NR;
+  sp.n_theta = NT;
+  sp.pitch = (int)align_up((size_t)NR, kPitchAlign);
+  sp.rows = NT + 2 * kGhostRows;
+  sp.dt_dr = dt / dr;
+  sp.dt_dth = dt / dth;
+  sp.decay = std::exp(-dt / tau);
+  sp.bc_kind[0] = bc->kind[0];
+  sp.bc_kind[1] = bc->kind[1];
+  sp.cos_t = reinterpret_cast<const double*>(ctx->ws + lay.cos_t);
+  sp.sin_t = reinterpret_cast<const double*>(ctx->ws + lay.sin_t);
+  sp.inv_r = reinterpret_cast<const double*>(ctx->ws + lay.inv_r);
+  sp.bc_vals = reinterpret_cast<const double*>(ctx->ws + lay.bc_vals);
+  sp.status = reinterpret_cast<uint32_t*>(ctx->ws + lay.status);
+  fill_dvm(ctx->dvm32, *dvm, *grid);
+  fill_dvm(ctx->dvm64, *dvm, *grid);
+
+  struct Up { size_t off; const void* src; size_t n; } ups[] = {
+      {lay.cos_t, ctx->cos_t.data(), NT * 8ul}, {lay.sin_t, ctx->sin_t.data(), NT * 8ul},
+      {lay.inv_r, ctx->inv_r.data(), NR * 8ul}, {lay.bc_vals, ctx->bc_vals.data(), ctx->bc_vals.size() * 8}};
+  for (const Up& u : ups) {
+    cudaError_t e = cudaMemcpyAsync(ctx->ws + u.off, u.src, u.n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) {
+      pclb_status s2 = cuda_fail(nullptr, e, "table upload");
+      delete ctx;
+      return s2;
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(ctx->ws + lay.status, 0, 256, ctx->stream);
+  if (e != cudaSuccess) {
+    pclb_status s2 = cuda_fail(nullptr, e, "status reset");
+    delete ctx;
+    return s2;
+  }
+  for (int w = 0; w < 2; ++w) {
+    pclb_status s2 = make_tmap(ctx, w);
+    if (s2 != PCLB_OK) {
+      std::snprintf(g_err, sizeof(g_err), "%s", ctx->err);
+      delete ctx;
+      return s2;
+    }
+  }
+  *out = ctx;
+  return PCLB_OK;
+}
+
+pclb_status pclb_destroy(pclb_ctx* ctx) {
+  if (!ctx) return PCLB_OK;
+  pclb_status st = bounded_sync(ctx, kDefaultTimeoutMs);
+  if (st != PCLB_OK) std::snprintf(g_err, sizeof(g_err), "%s", ctx->err);
+  delete static_cast<HostCtx*>(ctx);
+  return st;
+}
+
+pclb_status pclb_set_stream(pclb_ctx* ctx, void* stream) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+  return PCLB_OK;
+}
+
+pclb_status pclb_set_state(pclb_ctx* ctx, const void* rho, const void* u_r, const void* u_theta,
+                           const void* T) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!rho || !u_r || !u_theta || !T) return fail(ctx, PCLB_EINVAL, "field pointers must not be NULL");
+  cudaError_t e;
+  if (ctx->prec == PCLB_FP32)
+    e = launch_set_state<float>(fbuf<float>(ctx, ctx->cur), (const float*)rho, (const float*)u_r,
+                                (const float*)u_theta, (const float*)T, ctx->sp, ctx->dvm32, ctx->stream);
+  else
+    e = launch_set_state<double>(fbuf<double>(ctx, ctx->cur), (const double*)rho, (const double*)u_r,
+                                 (const double*)u_theta, (const double*)T, ctx->sp, ctx->dvm64, ctx->stream);
+  pclb_status st = check_launch(ctx, e, "set_state kernel launch");
+  if (st == PCLB_OK) ctx->has_state = true;
+  return st;
+}
+
+pclb_status pclb_set_f(pclb_ctx* ctx, const void* f) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!f) return fail(ctx, PCLB_EINVAL, "f must not be NULL");
+  cudaError_t e = ctx->prec == PCLB_FP32
+                      ? launch_unpack<float>((const float*)f, fbuf<float>(ctx, ctx->cur), ctx->sp, ctx->dvm32, ctx->stream)
+                      : launch_unpack<double>((const double*)f, fbuf<double>(ctx, ctx->cur), ctx->sp, ctx->dvm64, ctx->stream);
+  pclb_status st = check_launch(ctx, e, "set_f kernel launch");
+  if (st == PCLB_OK) ctx->has_state = true;
+  return st;
+}
+
+pclb_status pclb_get_f(pclb_ctx* ctx, void* f) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!f) return fail(ctx, PCLB_EINVAL, "f must not be NULL");
+  if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
+  cudaError_t e = ctx->prec == PCLB_FP32
+                      ? launch_pack<float>(fbuf<float>(ctx, ctx->cur), (float*)f, ctx->sp, ctx->stream)
+                      : launch_pack<double>(fbuf<double>(ctx, ctx->cur), (double*)f, ctx->sp, ctx->stream);
+  return check_launch(ctx, e, "get_f kernel launch");
+}
+
+pclb_status pclb_step(pclb_ctx* ctx, int32_t n) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (n < 0) return fail(ctx, PCLB_EINVAL, "n = %d must be >= 0", n);
+  if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
+  return ctx->prec == PCLB_FP32 ? do_step<float>(ctx, n) : do_step<double>(ctx, n);
+}
+
+pclb_status pclb_moments(pclb_ctx* ctx, void* rho, void* u_r, void* u_theta, void* T) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
+  if (!rho && !u_r && !u_theta && !T) return PCLB_OK;
+  cudaError_t e;
+  if (ctx->prec == PCLB_FP32)
+    e = launch_moments<float>(fbuf<float>(ctx, ctx->cur), (float*)rho, (float*)u_r, (float*)u_theta,
+                              (float*)T, ctx->sp, ctx->dvm32, ctx->stream);
+  else
+    e = launch_moments<double>(fbuf<double>(ctx, ctx->cur), (double*)rho, (double*)u_r, (double*)u_theta,
+                               (double*)T, ctx->sp, ctx->dvm64, ctx->stream);
+  return check_launch(ctx, e, "moments kernel launch");
+}
+
+pclb_status pclb_diagnostics(pclb_ctx* ctx, double* out) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!out) return fail(ctx, PCLB_EINVAL, "out must not be NULL");
+  if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
+  const double dr = (ctx->grid.r_out - ctx->grid.r_in) / (ctx->grid.n_r - 1);
+  const double dth = 2.0 * M_PI * ctx->grid.n_f / ((double)ctx->dvm.n_dirs * ctx->grid.n_theta);
+  double* partials = reinterpret_cast<double*>(ctx->ws + ctx->lay.partials);
+  double* dout = reinterpret_cast<double*>(ctx->ws + ctx->lay.diag_out);
+  cudaError_t e = ctx->prec == PCLB_FP32
+                      ? launch_diagnostics<float>(fbuf<float>(ctx, ctx->cur), partials, dout, ctx->sp,
+                                                  ctx->dvm32, dr, dth, ctx->grid.r_in, ctx->stream)
+                      : launch_diagnostics<double>(fbuf<double>(ctx, ctx->cur), partials, dout, ctx->sp,
+                                                   ctx->dvm64, dr, dth, ctx->grid.r_in, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "diagnostics kernel launch");
+  pclb_status st = bounded_sync(ctx, kDefaultTimeoutMs);
+  if (st != PCLB_OK) return st;
+  e = cudaMemcpy(out, dout, 8 * sizeof(double), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? PCLB_OK : cuda_fail(ctx, e, "diagnostics copy");
+}
+
+pclb_status pclb_status_flags(pclb_ctx* ctx, uint32_t* flags, int32_t clear) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!flags) return fail(ctx, PCLB_EINVAL, "flags must not be NULL");
+  pclb_status st = bounded_sync(ctx, kDefaultTimeoutMs);
+  if (st != PCLB_OK) return st;
+  cudaError_t e = cudaMemcpy(flags, ctx->ws + ctx->lay.status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "status copy");
+  if (clear) {
+    e = cudaMemset(ctx->ws + ctx->lay.status, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status reset");
+  }
+  if (*flags & PCLB_FLAG_TIMEOUT) return fail(ctx, PCLB_ETIMEOUT, "a kernel timed out waiting for its copies");
+  if (*flags) return fail(ctx, PCLB_ENONPHYS, "non-physical state (flags 0x%x)", *flags);
+  return PCLB_OK;
+}
+
+pclb_status pclb_sync(pclb_ctx* ctx, int32_t timeout_ms) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (timeout_ms <= 0) return fail(ctx, PCLB_EINVAL, "timeout_ms must be positive");
+  return bounded_sync(ctx, timeout_ms);
+}
+
+pclb_status pclb_run_host(pclb_ctx* ctx, const void* rho, const void* u_r, const void* u_theta,
+                          const void* T, int32_t n, void* out_rho, void* out_u_r, void* out_u_theta,
+                          void* out_T) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!rho || !u_r || !u_theta || !T) return fail(ctx, PCLB_EINVAL, "input pointers must not be NULL");
+  if (n < 0) return fail(ctx, PCLB_EINVAL, "n = %d must be >= 0", n);
+  const size_t bytes = (size_t)ctx->grid.n_r * ctx->grid.n_theta * elem_size(ctx->prec);
+  unsigned char* stage = ctx->ws + ctx->lay.stage;
+  const void* in[4] = {rho, u_r, u_theta, T};
+  for (int i = 0; i < 4; ++i) {
+    cudaError_t e = cudaMemcpyAsync(stage + i * bytes, in[i], bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "input copy");
+  }
+  pclb_status st = pclb_set_state(ctx, stage, stage + bytes, stage + 2 * bytes, stage + 3 * bytes);
+  if (st != PCLB_OK) return st;
+  if ((st = pclb_step(ctx, n)) != PCLB_OK) return st;
+  void* outs[4] = {out_rho, out_u_r, out_u_theta, out_T};
+  void* dev[4];
+  for (int i = 0; i < 4; ++i) dev[i] = outs[i] ? stage + (4 + i) * bytes : nullptr;
+  if ((st = pclb_moments(ctx, dev[0], dev[1], dev[2], dev[3])) != PCLB_OK) return st;
+  if ((st = bounded_sync(ctx, kDefaultTimeoutMs)) != PCLB_OK) return st;
+  for (int i = 0; i < 4; ++i) {
+    if (!outs[i]) continue;
+    cudaError_t e = cudaMemcpyAsync(outs[i], dev[i], bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "output copy");
+  }
+  return bounded_sync(ctx, kDefaultTimeoutMs);
+}
+
+}  // extern "C"

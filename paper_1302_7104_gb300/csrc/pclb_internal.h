@@ -1,0 +1,99 @@
+// Internal types shared by the host side of the C ABI and the kernels.
+// Not part of the public interface (include/pclb.h).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pclb.h"
+
+namespace pclb {
+
+// The discrete velocity model built here: N_k = 4 shells of kNDirs directions
+// plus the rest velocity (Eq. 2), Q = 33 for the octagon.
+constexpr int kNDirs = 8;
+constexpr int kQ = 1 + 4 * kNDirs;
+
+// Tiling of the fused step kernel.  A tile is kTileR x kTileT interior nodes;
+// its shared-memory window holds every velocity plane over
+// [r0 - 4, r0 + kTileR + 4) x [t0 - 2, t0 + kTileT + 2): the +-2 stencil halo
+// in both directions, with the radial start rounded down to a 16-byte
+// boundary so the TMA box starts aligned.
+constexpr int kTileR = 32;
+constexpr int kTileT = 16;
+constexpr int kWinR = kTileR + 8;   // 40 columns
+constexpr int kWinT = kTileT + 4;   // 20 rows
+constexpr int kLeft = 4;            // column of interior r0 inside the window
+constexpr int kStepThreads = 256;   // 8 warps; each thread owns 2 nodes (rows w and w + 8)
+constexpr int kPitchAlign = 32;     // row pitch in elements (128 B for float)
+constexpr int kGhostRows = 2;       // azimuthal ghost rows stored on each side
+
+// Per-velocity constants, in the arithmetic type T of the kernel, plus the
+// double-precision ones the moment / temperature recovery uses.
+template <class T>
+struct DvmConst {
+  T vx[kQ], vy[kQ];           // Cartesian components v_qx, v_qy
+  T cx[kQ], cy[kQ];           // unit direction (cos phi_i, sin phi_i); 0 for q = 0
+  T speed[5];                 // v_k
+  T half_v2[5];               // v_k^2 / 2
+  T Fc[5][4];                 // F_k(E) = sum_{n=1..4} Fc[k][n-1] E^n, k = 1..4 (Eq. 11a)
+  T Fc_lo[5][4];              // Fc - (double)Fc rounded to T: the low part of a float-float pair
+  T B0;                       // F_0 = 1 - B0 (F_1 + .. + F_4) (Eq. 11b)
+  int8_t shell[kQ];           // k of label q
+  int8_t recv_lo[kQ];         // label whose low ghost rows copy rows n_theta-2.. of label q
+  int8_t recv_hi[kQ];         // label whose high ghost rows copy rows 0, 1 of label q
+};
+
+struct StepParams {
+  int n_r, n_theta;           // interior nodes
+  int pitch;                  // elements per stored row (multiple of kPitchAlign)
+  int rows;                   // stored rows per plane: n_theta + 4
+  double dt_dr;               // dt / dr
+  double dt_dth;              // dt / dtheta
+  double decay;               // exp(-dt / tau), Eq. (19)
+  int bc_kind[2];
+  const double* cos_t;        // [n_theta] cos(theta_i), host-computed in double
+  const double* sin_t;        // [n_theta]
+  const double* inv_r;        // [n_r] 1 / r_i
+  const double* bc_vals;      // [2 sides][2 layers][4 fields][n_theta] or unused
+  uint32_t* status;           // device status word (PCLB_FLAG_*)
+};
+
+// Workspace layout (byte offsets from the caller's base pointer).
+struct Layout {
+  size_t f[2];                // two ping-pong distributions [Q][rows][pitch]
+  size_t f_bytes;
+  size_t cos_t, sin_t, inv_r, bc_vals;
+  size_t status;              // uint32 status word (+ padding)
+  size_t partials;            // double [kDiagBlocks][8] reduction partials
+  size_t diag_out;            // double [8]
+  size_t stage;               // host-I/O staging: 8 fields [n_theta][n_r]
+  size_t total;
+};
+
+constexpr int kDiagBlocks = 304;    // 2 x 152 SMs
+
+// Element size of a precision.
+inline size_t elem_size(pclb_precision p) { return p == PCLB_FP64 ? 8 : 4; }
+
+}  // namespace pclb
+
+// Host context behind the opaque pclb_ctx handle.
+struct pclb_ctx {
+  pclb_grid grid;
+  pclb_dvm dvm;
+  pclb_precision prec;
+  double tau, dt;
+  pclb_bc_kind bc_kind[2];
+  cudaStream_t stream;
+  unsigned char* ws;
+  pclb::Layout lay;
+  int cur;                    // which of the two f buffers holds the state
+  bool has_state;
+  CUtensorMap tmap[2];        // TMA descriptors of the two f buffers
+  pclb::StepParams sp;
+  pclb::DvmConst<float> dvm32;
+  pclb::DvmConst<double> dvm64;
+  char err[512];
+};

@@ -315,7 +315,7 @@ def uniform(n_r: int, n_theta: int, rho: float = 1.3, ux: float = 0.31, uy: floa
                     n_dirs=n_dirs, n_f=n_f, B=TABLE1_B[n_dirs])
 
 
-def random_smooth(n_r: int, n_theta: int, seed: int = 1, tau: float = 2e-3, cfl: float = 0.6,
+def random_smooth(n_r: int, n_theta: int, seed: int = 1, tau: float = 2e-3, cfl: float = STABLE_CFL,
                   r_in: float = 1.0, r_out: float = 2.0, amp: float = 0.2,
                   bc_kind=(BC_EXTRAP, BC_EXTRAP), n_dirs: int = 8, n_f: int = 8) -> Workload:
     """Smooth random fields: a few low Fourier modes in theta times smooth
