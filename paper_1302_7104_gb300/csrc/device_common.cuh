@@ -218,10 +218,13 @@ __device__ __forceinline__ ff ff_mul_add(ff a, ff b, ff c) {
   return r;
 }
 __device__ __forceinline__ ff ff_mul(ff a, ff b) {
-  ff z;
-  z.hi = 0.f;
-  z.lo = 0.f;
-  return ff_mul_add(a, b, z);
+  float p, e;
+  two_prod(a.hi, b.hi, p, e);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  ff r;
+  r.hi = __fadd_rn(p, e);
+  r.lo = __fsub_rn(e, __fsub_rn(r.hi, p));
+  return r;
 }
 __device__ __forceinline__ ff ff_add(ff a, ff b) {
   float s, se;
@@ -230,6 +233,21 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
   ff r;
   r.hi = __fadd_rn(s, lo);
   r.lo = __fsub_rn(lo, __fsub_rn(r.hi, s));
+  return r;
+}
+
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_scale(ff a, float s) { return ff{a.hi * s, a.lo * s}; }  // s a power of 2
+// 1 / a: single-precision seed refined by one Newton step on the float-float value.
+__device__ __forceinline__ ff ff_recip(ff a) {
+  const float r0 = __frcp_rn(a.hi);
+  const float e = fmaf(-a.hi, r0, 1.0f) - a.lo * r0;   // 1 - a r0
+  ff r;
+  r.hi = r0;
+  r.lo = r0 * e;
+  const float s = __fadd_rn(r.hi, r.lo);
+  r.lo = __fsub_rn(r.lo, __fsub_rn(s, r.hi));
+  r.hi = s;
   return r;
 }
 

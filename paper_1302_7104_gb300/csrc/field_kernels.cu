@@ -6,6 +6,7 @@
 #include <float.h>
 
 #include "device_common.cuh"
+#include "f32_state.cuh"
 #include "pclb_internal.h"
 
 namespace pclb {
@@ -44,6 +45,52 @@ __global__ void set_state_kernel(T* __restrict__ f, const T* __restrict__ rho, c
   }
 }
 
+
+// FP32 path: the same float-float node state and equilibrium as the step.
+__global__ void set_state_f32_kernel(float* __restrict__ f, const float* __restrict__ rho,
+                                     const float* __restrict__ u_r, const float* __restrict__ u_t,
+                                     const float* __restrict__ temp, const StepParams p,
+                                     const DvmConst<float> d) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  if (r >= p.n_r || t >= p.n_theta) return;
+  const size_t n = (size_t)t * p.n_r + r;
+  const double c = p.cos_t[t], s = p.sin_t[t];
+  const double ur = u_r[n], ut = u_t[n];
+  State32 st;
+  st.rho = ff_of(rho[n]);
+  st.E = ff_of(temp[n]);                      // E = T for gamma = 2
+  st.ux = ff_from(ur * c - ut * s);
+  st.uy = ff_from(ur * s + ut * c);
+  if (!(rho[n] > 0.f && temp[n] > 0.f)) atomicOr(p.status, PCLB_FLAG_NONPHYS);
+  const Eq32 e = eq32(st, d);
+  store_with_ghosts<float>(f, p, d, 0, t, r, feq32(e, d, 0, 0, 1.f));
+#pragma unroll
+  for (int k = 1; k <= 4; ++k)
+#pragma unroll
+    for (int i = 0; i < kHalf; ++i) {
+      const int q = 1 + (k - 1) * kNDirs + i;
+      store_with_ghosts<float>(f, p, d, q, t, r, feq32(e, d, k, i, 1.f));
+      store_with_ghosts<float>(f, p, d, q + kHalf, t, r, feq32(e, d, k, i, -1.f));
+    }
+}
+
+__global__ void moments_f32_kernel(const float* __restrict__ f, float* rho, float* u_r, float* u_t,
+                                   float* temp, const StepParams p, const DvmConst<float> d) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  if (r >= p.n_r || t >= p.n_theta) return;
+  const size_t plane = (size_t)p.rows * p.pitch;
+  const State32 m = state32(f + (size_t)(t + kGhostRows) * p.pitch + r, plane, d);
+  const size_t n = (size_t)t * p.n_r + r;
+  const double c = p.cos_t[t], s = p.sin_t[t];
+  const double ux = (double)m.ux.hi + (double)m.ux.lo, uy = (double)m.uy.hi + (double)m.uy.lo;
+  if (rho) rho[n] = m.rho.hi + m.rho.lo;
+  if (u_r) u_r[n] = (float)(ux * c + uy * s);
+  if (u_t) u_t[n] = (float)(uy * c - ux * s);
+  if (temp) temp[n] = m.E.hi + m.E.lo;
+}
+
 template <class T>
 __global__ void moments_kernel(const T* __restrict__ f, T* rho, T* u_r, T* u_t, T* temp,
                                const StepParams p, const DvmConst<T> d) {
@@ -78,6 +125,20 @@ __global__ void unpack_kernel(const T* __restrict__ in, T* __restrict__ f, const
   store_with_ghosts<T>(f, p, d, q, t, r, in[((size_t)q * p.n_theta + t) * p.n_r + r]);
 }
 
+__device__ __forceinline__ void node_state_double(const float* f, size_t plane, const DvmConst<float>& d,
+                                                  double& rho, double& ux, double& uy, double& E) {
+  const State32 m = state32(f, plane, d);
+  rho = (double)m.rho.hi + m.rho.lo;
+  ux = (double)m.ux.hi + m.ux.lo;
+  uy = (double)m.uy.hi + m.uy.lo;
+  E = (double)m.E.hi + m.E.lo;
+}
+__device__ __forceinline__ void node_state_double(const double* f, size_t plane, const DvmConst<double>& d,
+                                                  double& rho, double& ux, double& uy, double& E) {
+  const NodeState<double> m = node_moments(f, plane, d);
+  rho = m.rho; ux = m.ux; uy = m.uy; E = m.E;
+}
+
 // Global integrals with weight r dr dtheta, in double.  Each block reduces a
 // fixed grid-stride subset in a fixed order, so results are reproducible.
 template <class T>
@@ -90,9 +151,9 @@ __global__ void diag_partial_kernel(const T* __restrict__ f, double* partials, c
   for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes;
        n += (size_t)gridDim.x * blockDim.x) {
     const int t = (int)(n / p.n_r), r = (int)(n % p.n_r);
-    const NodeState<T> m = node_moments(f + (size_t)(t + kGhostRows) * p.pitch + r, plane, d);
+    double rho, ux, uy, E;
+    node_state_double(f + (size_t)(t + kGhostRows) * p.pitch + r, plane, d, rho, ux, uy, E);
     const double w = (r_in + r * dr) * dr * dth;
-    const double rho = (double)m.rho, ux = (double)m.ux, uy = (double)m.uy, E = (double)m.E;
     acc[0] += w * rho;
     acc[1] += w * rho * ux;
     acc[2] += w * rho * uy;
@@ -142,7 +203,10 @@ template <class T>
 cudaError_t launch_set_state(T* f, const T* rho, const T* ur, const T* ut, const T* temp,
                              const StepParams& p, const DvmConst<T>& d, cudaStream_t s) {
   dim3 grid((p.n_r + kRowThreads - 1) / kRowThreads, p.n_theta);
-  set_state_kernel<T><<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d);
+  if constexpr (sizeof(T) == 4)
+    set_state_f32_kernel<<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d);
+  else
+    set_state_kernel<T><<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d);
   return cudaGetLastError();
 }
 
@@ -150,7 +214,10 @@ template <class T>
 cudaError_t launch_moments(const T* f, T* rho, T* ur, T* ut, T* temp, const StepParams& p,
                            const DvmConst<T>& d, cudaStream_t s) {
   dim3 grid((p.n_r + kRowThreads - 1) / kRowThreads, p.n_theta);
-  moments_kernel<T><<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d);
+  if constexpr (sizeof(T) == 4)
+    moments_f32_kernel<<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d);
+  else
+    moments_kernel<T><<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d);
   return cudaGetLastError();
 }
 

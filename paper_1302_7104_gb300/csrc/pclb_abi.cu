@@ -17,6 +17,8 @@
 #include "pclb_internal.h"
 
 namespace pclb {
+cudaError_t launch_step_f32(const CUtensorMap*, float*, const StepParams&, const DvmConst<float>&,
+                            cudaStream_t);
 template <class T>
 cudaError_t launch_step(const CUtensorMap*, T*, const StepParams&, const DvmConst<T>&, cudaStream_t);
 template <class T>
@@ -113,8 +115,11 @@ template <class T>
 void fill_dvm(DvmConst<T>& c, const pclb_dvm& d, const pclb_grid& g) {
   std::memset(&c, 0, sizeof(c));
   for (int k = 0; k < 5; ++k) {
+    const double hv2 = 0.5 * d.speeds[k] * d.speeds[k];
     c.speed[k] = (T)d.speeds[k];
-    c.half_v2[k] = (T)(0.5 * d.speeds[k] * d.speeds[k]);
+    c.speed_lo[k] = (T)(d.speeds[k] - (double)c.speed[k]);
+    c.half_v2[k] = (T)hv2;
+    c.half_v2_lo[k] = (T)(hv2 - (double)c.half_v2[k]);
   }
   c.B0 = (T)d.B[0];
   for (int k = 1; k <= 4; ++k) {
@@ -140,12 +145,21 @@ void fill_dvm(DvmConst<T>& c, const pclb_dvm& d, const pclb_grid& g) {
   for (int k = 1; k <= 4; ++k)
     for (int i = 0; i < nd; ++i) {
       const int q = 1 + (k - 1) * nd + i;
-      const double phi = 2.0 * M_PI * i / nd;
-      const double cx = std::cos(phi), cy = std::sin(phi);
+      // Unit directions of Eq. (2), taken exactly antisymmetric for opposite
+      // directions (i and i + n_dirs/2) as the velocity set is.
+      const int ib = i % (nd / 2);
+      const double phi = 2.0 * M_PI * ib / nd;
+      const double sgn = i < nd / 2 ? 1.0 : -1.0;
+      const double cx = sgn * std::cos(phi), cy = sgn * std::sin(phi);
+      const double vx = d.speeds[k] * cx, vy = d.speeds[k] * cy;
       c.cx[q] = (T)cx;
       c.cy[q] = (T)cy;
-      c.vx[q] = (T)(d.speeds[k] * cx);
-      c.vy[q] = (T)(d.speeds[k] * cy);
+      c.cx_lo[q] = (T)(cx - (double)c.cx[q]);
+      c.cy_lo[q] = (T)(cy - (double)c.cy[q]);
+      c.vx[q] = (T)vx;
+      c.vy[q] = (T)vy;
+      c.vx_lo[q] = (T)(vx - (double)c.vx[q]);
+      c.vy_lo[q] = (T)(vy - (double)c.vy[q]);
       c.shell[q] = (int8_t)k;
       // Low ghosts of label (k, j) copy rows of label (k, j + n_f); so rows of
       // label (k, i) are received by (k, i - n_f); high ghosts the reverse.
@@ -233,7 +247,11 @@ template <class T>
 pclb_status do_step(pclb_ctx* ctx, int n) {
   for (int i = 0; i < n; ++i) {
     const int src = ctx->cur, dst = 1 - ctx->cur;
-    cudaError_t e = launch_step<T>(&ctx->tmap[src], fbuf<T>(ctx, dst), ctx->sp, dvm_of<T>(ctx), ctx->stream);
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4)
+      e = launch_step_f32(&ctx->tmap[src], fbuf<float>(ctx, dst), ctx->sp, ctx->dvm32, ctx->stream);
+    else
+      e = launch_step<T>(&ctx->tmap[src], fbuf<T>(ctx, dst), ctx->sp, dvm_of<T>(ctx), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "step kernel launch");
     ctx->cur = dst;
   }

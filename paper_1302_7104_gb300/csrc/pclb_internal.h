@@ -39,6 +39,10 @@ struct DvmConst {
   T half_v2[5];               // v_k^2 / 2
   T Fc[5][4];                 // F_k(E) = sum_{n=1..4} Fc[k][n-1] E^n, k = 1..4 (Eq. 11a)
   T Fc_lo[5][4];              // Fc - (double)Fc rounded to T: the low part of a float-float pair
+  // Low parts (value - (double)hi, rounded to T) of the velocity constants, so
+  // that the FP32 path can use them as float-float pairs; zero for double.
+  T vx_lo[kQ], vy_lo[kQ], cx_lo[kQ], cy_lo[kQ];
+  T speed_lo[5], half_v2_lo[5];
   T B0;                       // F_0 = 1 - B0 (F_1 + .. + F_4) (Eq. 11b)
   int8_t shell[kQ];           // k of label q
   int8_t recv_lo[kQ];         // label whose low ghost rows copy rows n_theta-2.. of label q

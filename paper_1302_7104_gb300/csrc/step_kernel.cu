@@ -209,8 +209,6 @@ cudaError_t launch_step(const CUtensorMap* tmap_in, T* f_out, const StepParams& 
   return cudaGetLastError();
 }
 
-template cudaError_t launch_step<float>(const CUtensorMap*, float*, const StepParams&,
-                                        const DvmConst<float>&, cudaStream_t);
 template cudaError_t launch_step<double>(const CUtensorMap*, double*, const StepParams&,
                                          const DvmConst<double>&, cudaStream_t);
 

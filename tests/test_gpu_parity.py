@@ -135,10 +135,12 @@ def test_set_state_and_moments_match_oracle(prec, tol_f, tol_m):
 def test_diagnostics_match_oracle(prec):
     w = I.random_smooth(40, 24, seed=13)
     f = O.set_state(w)
+    if prec == "fp32":   # the oracle sees exactly the values the FP32 state holds
+        f = f.astype(np.float32).astype(np.float64)
     want = O.diagnostics(w, f)
     with P.PCLB(w, precision=prec) as g:
         got = g.set_f(_to_dev(f, g.dtype)).diagnostics()
-    tol = 1e-13 if prec == "fp64" else 2e-7
+    tol = 1e-13 if prec == "fp64" else 1e-11
     assert got[:6] == pytest.approx(want, rel=tol)
     assert got[6] == w.n_r * w.n_theta
 
@@ -147,7 +149,7 @@ def test_diagnostics_match_oracle(prec):
 def test_get_set_f_round_trip_is_bitwise(prec):
     w = I.random_smooth(35, 18, seed=14)
     with P.PCLB(w, precision=prec) as g:
-        f = torch.randn((33, 18, 35), dtype=g.dtype, device="cuda")
+        f = _to_dev(_noisy_state(w), g.dtype)
         back = g.set_f(f).get_f()
         assert torch.equal(back, f)
         # the state survives a step and restore bitwise
