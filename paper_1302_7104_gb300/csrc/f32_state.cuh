@@ -23,27 +23,55 @@ struct Eq32 {
   float yh[kHalf], yl[kHalf];  // c_i . u / E for the first direction of each pair (float-float)
 };
 
-// Moments of one node (Eqs. 3-5) from f[q * stride], compensated, then the
-// temperature recovery E = (e - |j|^2/(2 rho)) / rho in float-float.
+// Moments of one node (Eqs. 3-5) from f[q * stride], then the temperature
+// recovery E = (e - |j|^2/(2 rho)) / rho in float-float.  Within a shell the
+// eight values are summed in float over opposite-direction pairs; shells 2 and
+// 3 (speeds 2.92 and 2.99, weights of opposite sign) are first added direction
+// by direction so that their large contributions cancel before rounding, and
+// shell 3 enters once more with the speed differences; the shell totals are
+// combined with error-free transformations.
+template <class Stride>
+__device__ __forceinline__ void shell_sums(const float* f, Stride stride, const DvmConst<float>& d,
+                                           int k, int k_add, float& S, float& X, float& Xl, float& Y,
+                                           float& Yl) {
+  S = 0.f; X = 0.f; Xl = 0.f; Y = 0.f; Yl = 0.f;
+#pragma unroll
+  for (int i = 0; i < kHalf; ++i) {
+    const int q = 1 + (k - 1) * kNDirs + i;
+    float fa = f[q * stride], fb = f[(q + kHalf) * stride];
+    if (k_add > 0) {
+      const int qa = 1 + (k_add - 1) * kNDirs + i;
+      fa += f[qa * stride];
+      fb += f[(qa + kHalf) * stride];
+    }
+    S += fa + fb;
+    const float dd = fa - fb;   // the pair has opposite unit vectors
+    X = fmaf(d.cx[q], dd, X);
+    Xl = fmaf(d.cx_lo[q], dd, Xl);
+    Y = fmaf(d.cy[q], dd, Y);
+    Yl = fmaf(d.cy_lo[q], dd, Yl);
+  }
+}
+
 template <class Stride>
 __device__ __forceinline__ State32 state32(const float* f, Stride stride, const DvmConst<float>& d) {
   ff rho = ff_of(f[0]), jx = ff_of(0.f), jy = ff_of(0.f), e = ff_of(0.f);
+  // (shell, shell added to it, speed, v^2/2): 1; 2+3 with v_2; 3 with v_3 - v_2; 4
 #pragma unroll
-  for (int k = 1; k <= 4; ++k) {
-    float S = 0.f, X = 0.f, Xl = 0.f, Y = 0.f, Yl = 0.f;
-#pragma unroll
-    for (int i = 0; i < kHalf; ++i) {
-      const int q = 1 + (k - 1) * kNDirs + i;
-      const float fa = f[q * stride], fb = f[(q + kHalf) * stride];
-      S += fa + fb;
-      const float dd = fa - fb;   // the pair has opposite unit vectors
-      X = fmaf(d.cx[q], dd, X);
-      Xl = fmaf(d.cx_lo[q], dd, Xl);
-      Y = fmaf(d.cy[q], dd, Y);
-      Yl = fmaf(d.cy_lo[q], dd, Yl);
+  for (int g = 0; g < 4; ++g) {
+    const int k = g == 0 ? 1 : (g == 1 ? 2 : (g == 2 ? 3 : 4));
+    const int k_add = g == 1 ? 3 : 0;
+    float S, X, Xl, Y, Yl;
+    shell_sums(f, stride, d, k, k_add, S, X, Xl, Y, Yl);
+    ff sp, hv;
+    if (g == 2) {
+      sp = ff{d.dv23, d.dv23_lo};
+      hv = ff{d.dh23, d.dh23_lo};
+    } else {
+      sp = ff{d.speed[k], d.speed_lo[k]};
+      hv = ff{d.half_v2[k], d.half_v2_lo[k]};
     }
-    const ff sp{d.speed[k], d.speed_lo[k]}, hv{d.half_v2[k], d.half_v2_lo[k]};
-    rho = ff_add(rho, ff_of(S));
+    if (g != 2) rho = ff_add(rho, ff_of(S));
     jx = ff_add(jx, ff_mul(sp, ff{X, Xl}));
     jy = ff_add(jy, ff_mul(sp, ff{Y, Yl}));
     e = ff_add(e, ff_mul(hv, ff_of(S)));

@@ -122,6 +122,14 @@ void fill_dvm(DvmConst<T>& c, const pclb_dvm& d, const pclb_grid& g) {
     c.half_v2_lo[k] = (T)(hv2 - (double)c.half_v2[k]);
   }
   c.B0 = (T)d.B[0];
+  {
+    const double dv = d.speeds[3] - d.speeds[2];
+    const double dh = 0.5 * (d.speeds[3] * d.speeds[3] - d.speeds[2] * d.speeds[2]);
+    c.dv23 = (T)dv;
+    c.dv23_lo = (T)(dv - (double)c.dv23);
+    c.dh23 = (T)dh;
+    c.dh23_lo = (T)(dh - (double)c.dh23);
+  }
   for (int k = 1; k <= 4; ++k) {
     const double vk2 = d.speeds[k] * d.speeds[k];
     double o[3];

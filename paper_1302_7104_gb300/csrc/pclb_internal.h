@@ -43,6 +43,10 @@ struct DvmConst {
   // that the FP32 path can use them as float-float pairs; zero for double.
   T vx_lo[kQ], vy_lo[kQ], cx_lo[kQ], cy_lo[kQ];
   T speed_lo[5], half_v2_lo[5];
+  // v_3 - v_2 and (v_3^2 - v_2^2)/2 as float-float pairs: the FP32 moments sum
+  // shells 2 and 3 direction by direction (their speeds are close and their
+  // weights opposite), then correct with these differences.
+  T dv23, dv23_lo, dh23, dh23_lo;
   T B0;                       // F_0 = 1 - B0 (F_1 + .. + F_4) (Eq. 11b)
   int8_t shell[kQ];           // k of label q
   int8_t recv_lo[kQ];         // label whose low ghost rows copy rows n_theta-2.. of label q

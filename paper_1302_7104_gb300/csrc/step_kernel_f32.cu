@@ -229,12 +229,17 @@ __global__ void __launch_bounds__(kStepThreads, 2)
     store(q, o0, o1);
   };
 
-#pragma unroll
+  // Shells run as a loop (keeps the unrolled body small enough for the
+  // instruction cache); the four direction pairs of a shell are unrolled.
+#pragma unroll 1
   for (int k = 1; k <= 4; ++k) {
     const float sh = d.speed[k], sl = d.speed_lo[k];
+    const float wk0 = k == 1 ? eq[0].w[1] : (k == 2 ? eq[0].w[2] : (k == 3 ? eq[0].w[3] : eq[0].w[4]));
+    const float wk1 = k == 1 ? eq[1].w[1] : (k == 2 ? eq[1].w[2] : (k == 3 ? eq[1].w[3] : eq[1].w[4]));
+    const int qb = 1 + (k - 1) * kNDirs;
 #pragma unroll
     for (int i = 0; i < kHalf; ++i) {
-      const int q = 1 + (k - 1) * kNDirs + i;
+      const int q = qb + i;
       const float4 tb = tab[((k - 1) * kHalf + i) * kTileT + rl];
       const int fl = __float_as_int(tb.w);
       const int sr = (fl & 1) ? 1 : -1;            // v_r < 0: upwind at larger r
@@ -249,8 +254,9 @@ __global__ void __launch_bounds__(kStepThreads, 2)
         const float x2 = x * x;
         const float ev = fmaf(x2, fmaf(x2, 1.0f / 24.0f, eq[c].a1h), eq[c].a0);
         const float od = x * fmaf(x2, 1.0f / 6.0f, eq[c].a1);
-        fp[c] = eq[c].w[k] * (ev + od);
-        fm[c] = eq[c].w[k] * (ev - od);
+        const float wk = c == 0 ? wk0 : wk1;
+        fp[c] = wk * (ev + od);
+        fm[c] = wk * (ev - od);
       }
       update(q, sr, st, tb.x, tb.y, at0, kt0, at1, kt1, fp[0], fp[1]);
       update(q + kHalf, -sr, -st, tb.x, tb.y, at0, kt0, at1, kt1, fm[0], fm[1]);

@@ -140,8 +140,11 @@ def test_diagnostics_match_oracle(prec):
     want = O.diagnostics(w, f)
     with P.PCLB(w, precision=prec) as g:
         got = g.set_f(_to_dev(f, g.dtype)).diagnostics()
-    tol = 1e-13 if prec == "fp64" else 1e-11
-    assert got[:6] == pytest.approx(want, rel=tol)
+    # FP32 moments sum each shell in single precision (relative error ~1e-7 of
+    # the shell totals); momentum totals are small differences of large terms,
+    # so they get an absolute tolerance scaled by the mass.
+    tol = 1e-13 if prec == "fp64" else 2e-7
+    assert got[:6] == pytest.approx(want, rel=tol, abs=tol * want[0])
     assert got[6] == w.n_r * w.n_theta
 
 
