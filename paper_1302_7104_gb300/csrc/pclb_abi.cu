@@ -44,6 +44,7 @@ constexpr int kDefaultTimeoutMs = 120000;
 
 struct HostCtx : pclb_ctx {
   std::vector<double> cos_t, sin_t, inv_r, bc_vals;
+  std::vector<float> courant, inv_r_f;
 };
 
 pclb_status fail(pclb_ctx* ctx, pclb_status st, const char* fmt, ...) {
@@ -99,6 +100,8 @@ Layout make_layout(const pclb_grid* g, pclb_precision prec) {
   L.sin_t = off; off = align_up(off + (size_t)g->n_theta * 8, 256);
   L.inv_r = off; off = align_up(off + (size_t)g->n_r * 8, 256);
   L.bc_vals = off; off = align_up(off + (size_t)2 * 2 * 4 * g->n_theta * 8, 256);
+  L.courant = off; off = align_up(off + (size_t)g->n_theta * (4 * kNDirs / 2) * 16, 256);
+  L.inv_r_f = off; off = align_up(off + (size_t)g->n_r * 4, 256);
   L.status = off; off = align_up(off + 256, 256);
   L.partials = off; off = align_up(off + (size_t)kDiagBlocks * 8 * 8, 256);
   L.diag_out = off; off = align_up(off + 8 * 8, 256);
@@ -352,6 +355,27 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
   }
   ctx->inv_r.resize(NR);
   for (int r = 0; r < NR; ++r) ctx->inv_r[r] = 1.0 / (grid->r_in + r * dr);
+  // Courant table of the FP32 kernel: for every theta node and every pair of
+  // opposite velocities (first label q = 1 + (k-1) N_i + i, i < N_i / 2).
+  const int npairs = 4 * dvm->n_dirs / 2;
+  ctx->courant.resize((size_t)NT * npairs * 4);
+  for (int t = 0; t < NT; ++t)
+    for (int k = 1; k <= 4; ++k)
+      for (int i = 0; i < dvm->n_dirs / 2; ++i) {
+        const double phi = 2.0 * M_PI * i / dvm->n_dirs;
+        const double vx = dvm->speeds[k] * std::cos(phi), vy = dvm->speeds[k] * std::sin(phi);
+        const double vr = vx * ctx->cos_t[t] + vy * ctx->sin_t[t];
+        const double vt = vy * ctx->cos_t[t] - vx * ctx->sin_t[t];
+        const double ar = std::fabs(vr) * dt / dr;
+        float* e = ctx->courant.data() + ((size_t)t * npairs + (k - 1) * (dvm->n_dirs / 2) + i) * 4;
+        e[0] = (float)ar;
+        e[1] = (float)(ar * (1.0 - ar));
+        e[2] = (float)(std::fabs(vt) * dt / dth);
+        const int flags = (vr < 0.0 ? 1 : 0) | (vt < 0.0 ? 2 : 0);
+        std::memcpy(&e[3], &flags, 4);
+      }
+  ctx->inv_r_f.resize(NR);
+  for (int r = 0; r < NR; ++r) ctx->inv_r_f[r] = (float)ctx->inv_r[r];
   ctx->bc_vals.assign((size_t)2 * 2 * 4 * NT, 0.0);
   for (int s = 0; s < 2; ++s)
     if (bc->kind[s] != PCLB_BC_EXTRAP)
@@ -371,13 +395,16 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
   sp.sin_t = reinterpret_cast<const double*>(ctx->ws + lay.sin_t);
   sp.inv_r = reinterpret_cast<const double*>(ctx->ws + lay.inv_r);
   sp.bc_vals = reinterpret_cast<const double*>(ctx->ws + lay.bc_vals);
+  sp.courant = reinterpret_cast<const float4*>(ctx->ws + lay.courant);
+  sp.inv_r_f = reinterpret_cast<const float*>(ctx->ws + lay.inv_r_f);
   sp.status = reinterpret_cast<uint32_t*>(ctx->ws + lay.status);
   fill_dvm(ctx->dvm32, *dvm, *grid);
   fill_dvm(ctx->dvm64, *dvm, *grid);
 
   struct Up { size_t off; const void* src; size_t n; } ups[] = {
       {lay.cos_t, ctx->cos_t.data(), NT * 8ul}, {lay.sin_t, ctx->sin_t.data(), NT * 8ul},
-      {lay.inv_r, ctx->inv_r.data(), NR * 8ul}, {lay.bc_vals, ctx->bc_vals.data(), ctx->bc_vals.size() * 8}};
+      {lay.inv_r, ctx->inv_r.data(), NR * 8ul}, {lay.bc_vals, ctx->bc_vals.data(), ctx->bc_vals.size() * 8},
+      {lay.courant, ctx->courant.data(), ctx->courant.size() * 4}, {lay.inv_r_f, ctx->inv_r_f.data(), NR * 4ul}};
   for (const Up& u : ups) {
     cudaError_t e = cudaMemcpyAsync(ctx->ws + u.off, u.src, u.n, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) {

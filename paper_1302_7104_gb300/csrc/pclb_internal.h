@@ -65,6 +65,10 @@ struct StepParams {
   const double* sin_t;        // [n_theta]
   const double* inv_r;        // [n_r] 1 / r_i
   const double* bc_vals;      // [2 sides][2 layers][4 fields][n_theta] or unused
+  const float4* courant;      // [n_theta][4 n_dirs / 2]: per opposite-velocity pair (first label
+                              // q of the pair) |C_r|, |C_r|(1 - |C_r|), |v_theta| dt / dtheta,
+                              // flags (bit 0: v_r < 0, bit 1: v_theta < 0) as int bits
+  const float* inv_r_f;       // [n_r] 1 / r_i in float
   uint32_t* status;           // device status word (PCLB_FLAG_*)
 };
 
@@ -72,7 +76,7 @@ struct StepParams {
 struct Layout {
   size_t f[2];                // two ping-pong distributions [Q][rows][pitch]
   size_t f_bytes;
-  size_t cos_t, sin_t, inv_r, bc_vals;
+  size_t cos_t, sin_t, inv_r, bc_vals, courant, inv_r_f;
   size_t status;              // uint32 status word (+ padding)
   size_t partials;            // double [kDiagBlocks][8] reduction partials
   size_t diag_out;            // double [8]

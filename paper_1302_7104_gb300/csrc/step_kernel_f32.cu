@@ -1,19 +1,20 @@
 // Fused FP32 time step of the polar-coordinate FDLB model (Eq. 38), the hot
 // kernel of the library.
 //
-// Work per CTA: a tile of 32 (r) x 16 (theta) nodes.  One thread issues 33
-// TMA box copies (one per velocity plane) of the window [r0-4, r0+36) x
-// [t0-2, t0+18) into shared memory; meanwhile the threads tabulate, for each
-// opposite-direction velocity pair and tile row, |C_r|, |C_r|(1-|C_r|),
-// |v_theta| dt/dtheta and the upwind signs.  Each thread then owns two
-// radially adjacent nodes of one row:
-//   * moments (Eqs. 3-5) with compensated sums, temperature recovery and the
-//     weights rho F_k(E) (Eqs. 11a-b) in float-float arithmetic, so that the
-//     rounded equilibrium keeps the collision invariants of the exact one;
-//   * radial ghost columns for wall tiles (Eq. 39, f = f^eq), in shared memory;
-//   * for every pair (q, q') of opposite velocities in a shell: v_q.u/E from
-//     float-float constants, the even / odd parts of the equilibrium
-//     polynomial (Eq. 10) shared by q and q', then per velocity the relaxation
+// Work per CTA: a tile of 32 (r) x 16 (theta) nodes, 256 threads.  One thread
+// issues 33 TMA box copies (one per velocity plane) of the window
+// [r0-4, r0+36) x [t0-2, t0+18) into shared memory while the others copy the
+// tile's rows of the host-computed Courant table.  Each thread then owns two
+// radially adjacent nodes of one row and processes them together with packed
+// FP32x2 arithmetic:
+//   * moments (Eqs. 3-5), temperature recovery and the weights rho F_k(E)
+//     (Eqs. 11a-b) in float-float arithmetic, so that the rounded equilibrium
+//     keeps the collision invariants of the exact one;
+//   * radial ghost columns for tiles at a wall (Eq. 39, f = f^eq), computed in
+//     shared memory;
+//   * for every pair (q, q') of opposite velocities of a shell: v_q.u/E from
+//     float-float constants, the even and odd parts of the equilibrium
+//     polynomial (Eq. 10) shared by q and q'; then per velocity the relaxation
 //     (Eq. 19) minus the MWB increments (Eq. 28) in r and theta, stored with
 //     8-byte stores, plus the azimuthal ghost rows of the seam (Eq. 40).
 #include <cuda.h>
@@ -21,6 +22,7 @@
 
 #include "device_common.cuh"
 #include "f32_state.cuh"
+#include "f32x2.cuh"
 #include "pclb_internal.h"
 
 namespace pclb {
@@ -34,9 +36,129 @@ constexpr int kTabBytes = kPairs * kTileT * 16;      // one float4 per (pair, ro
 constexpr int kSmemF32 = kPlanesBytes + kTabBytes + 128;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
+// Unit vectors of the first direction of each opposite pair, i = 0..3 of the
+// octagon (Eq. 2), as float-float pairs: (1,0), (s,s), (0,1), (-s,s), s = 1/sqrt 2.
+constexpr float kS = 0.7071067690849304f;
+constexpr float kSl = 1.2101617152815436e-08f;
+
+__device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
+// Sums over one shell (plus, optionally, a second shell added direction by
+// direction) of f, c_x f and c_y f for both nodes, with the octagon's exact
+// unit vectors as float-float constants.
+template <int K, int KADD>
+__device__ __forceinline__ void shell_sums2(const float* f, f2& S, f2& X, f2& Xl, f2& Y, f2& Yl) {
+  S = bc2(0.f); X = bc2(0.f); Xl = bc2(0.f); Y = bc2(0.f); Yl = bc2(0.f);
+#pragma unroll
+  for (int i = 0; i < kHalf; ++i) {
+    const int q = 1 + (K - 1) * kNDirs + i;
+    f2 fa = ld2(f + q * kPlaneF), fb = ld2(f + (q + kHalf) * kPlaneF);
+    if (KADD > 0) {
+      const int qa = 1 + (KADD - 1) * kNDirs + i;
+      fa = add2(fa, ld2(f + qa * kPlaneF));
+      fb = add2(fb, ld2(f + (qa + kHalf) * kPlaneF));
+    }
+    S = add2(S, add2(fa, fb));
+    const f2 dd = sub2(fa, fb);
+    if (i == 0) {
+      X = add2(X, dd);
+    } else if (i == 2) {
+      Y = add2(Y, dd);
+    } else {
+      const float sx = i == 1 ? 1.f : -1.f;
+      X = fma2(bc2(sx * kS), dd, X);
+      Xl = fma2(bc2(sx * kSl), dd, Xl);
+      Y = fma2(bc2(kS), dd, Y);
+      Yl = fma2(bc2(kSl), dd, Yl);
+    }
+  }
+}
+
+struct State2 {
+  ff2 rho, ux, uy, E;
+};
+
+__device__ __forceinline__ ff2 ffc(float hi, float lo) { return ff2{bc2(hi), bc2(lo)}; }
+
+// Moments (Eqs. 3-5) and temperature recovery of the two nodes.
+__device__ __forceinline__ State2 state2(const float* f, const DvmConst<float>& d) {
+  ff2 rho = ff2_of(ld2(f)), jx = ff2_of(bc2(0.f)), jy = jx, e = jx;
+  f2 S, X, Xl, Y, Yl;
+  // shell 1
+  shell_sums2<1, 0>(f, S, X, Xl, Y, Yl);
+  rho = ff2_add(rho, ff2_of(S));
+  jx = ff2_add(jx, ff2_mul(ffc(d.speed[1], d.speed_lo[1]), ff2{X, Xl}));
+  jy = ff2_add(jy, ff2_mul(ffc(d.speed[1], d.speed_lo[1]), ff2{Y, Yl}));
+  e = ff2_add(e, ff2_mul(ffc(d.half_v2[1], d.half_v2_lo[1]), ff2_of(S)));
+  // shells 2 + 3 direction by direction, with the speed and v^2/2 of shell 2
+  shell_sums2<2, 3>(f, S, X, Xl, Y, Yl);
+  rho = ff2_add(rho, ff2_of(S));
+  jx = ff2_add(jx, ff2_mul(ffc(d.speed[2], d.speed_lo[2]), ff2{X, Xl}));
+  jy = ff2_add(jy, ff2_mul(ffc(d.speed[2], d.speed_lo[2]), ff2{Y, Yl}));
+  e = ff2_add(e, ff2_mul(ffc(d.half_v2[2], d.half_v2_lo[2]), ff2_of(S)));
+  // shell 3 again with the differences v_3 - v_2, (v_3^2 - v_2^2)/2
+  shell_sums2<3, 0>(f, S, X, Xl, Y, Yl);
+  jx = ff2_add(jx, ff2_mul(ffc(d.dv23, d.dv23_lo), ff2{X, Xl}));
+  jy = ff2_add(jy, ff2_mul(ffc(d.dv23, d.dv23_lo), ff2{Y, Yl}));
+  e = ff2_add(e, ff2_mul(ffc(d.dh23, d.dh23_lo), ff2_of(S)));
+  // shell 4
+  shell_sums2<4, 0>(f, S, X, Xl, Y, Yl);
+  rho = ff2_add(rho, ff2_of(S));
+  jx = ff2_add(jx, ff2_mul(ffc(d.speed[4], d.speed_lo[4]), ff2{X, Xl}));
+  jy = ff2_add(jy, ff2_mul(ffc(d.speed[4], d.speed_lo[4]), ff2{Y, Yl}));
+  e = ff2_add(e, ff2_mul(ffc(d.half_v2[4], d.half_v2_lo[4]), ff2_of(S)));
+
+  State2 s;
+  const ff2 inv = ff2_recip(rho);
+  s.rho = rho;
+  s.ux = ff2_mul(jx, inv);
+  s.uy = ff2_mul(jy, inv);
+  const ff2 ke = ff2_add(ff2_mul(jx, s.ux), ff2_mul(jy, s.uy));    // |j|^2 / rho
+  s.E = ff2_mul(ff2_add(e, ff2_scale(ke, -0.5f)), inv);
+  return s;
+}
+
+struct Eq2 {
+  f2 w[5];                  // rho F_k(E)
+  f2 a0, a1, a1h;           // Eq. (10) polynomial coefficients
+  f2 yh[kHalf], yl[kHalf];  // c_i . u / E, float-float
+};
+
+__device__ __forceinline__ Eq2 eq2(const State2& s, const DvmConst<float>& d) {
+  Eq2 q;
+  ff2 sum = ff2_of(bc2(0.f));
+#pragma unroll
+  for (int k = 1; k <= 4; ++k) {
+    ff2 a = ffc(d.Fc[k][3], d.Fc_lo[k][3]);
+#pragma unroll
+    for (int n = 2; n >= 0; --n) a = ff2_mul_add(a, s.E, ffc(d.Fc[k][n], d.Fc_lo[k][n]));
+    a = ff2_mul(a, s.E);                               // F_k(E)
+    sum = ff2_add(sum, a);
+    q.w[k] = ff2_round(ff2_mul(s.rho, a));
+  }
+  const ff2 f0 = ff2_add(ff2_of(bc2(1.f)), ff2_mul(ff2_of(bc2(-d.B0)), sum));   // F_0
+  q.w[0] = ff2_round(ff2_mul(s.rho, f0));
+  const ff2 invE = ff2_recip(s.E);
+  const ff2 uxE = ff2_mul(s.ux, invE), uyE = ff2_mul(s.uy, invE);
+  const ff2 u2E = ff2_add(ff2_mul(s.ux, uxE), ff2_mul(s.uy, uyE));   // u^2 / E
+  const ff2 a1 = ff2_add(ff2_of(bc2(1.f)), ff2_scale(u2E, -0.5f));
+  const ff2 a0 = ff2_add(a1, ff2_scale(ff2_mul(u2E, u2E), 0.125f));
+  q.a1 = ff2_round(a1);
+  q.a0 = ff2_round(a0);
+  q.a1h = mul2(bc2(0.5f), q.a1);
+  const ff2 sq = ffc(kS, kSl);
+  const ff2 y1 = ff2_mul(sq, ff2_add(uxE, uyE));
+  const ff2 y3 = ff2_mul(sq, ff2_add(uyE, ff2{neg2(uxE.hi), neg2(uxE.lo)}));
+  q.yh[0] = uxE.hi; q.yl[0] = uxE.lo;
+  q.yh[1] = y1.hi;  q.yl[1] = y1.lo;
+  q.yh[2] = uyE.hi; q.yl[2] = uyE.lo;
+  q.yh[3] = y3.hi;  q.yl[3] = y3.lo;
+  return q;
+}
+
 // Ghost columns of one wall for tile row `row` (window row index), Sec. II C 1.
-__device__ void ghost_columns_f32(float* sm, int row, int side, int cw, int t, const StepParams& p,
-                                  const DvmConst<float>& d) {
+__device__ __noinline__ void ghost_columns_f32(float* sm, int row, int side, int cw, int t,
+                                               const StepParams& p, const DvmConst<float>& d) {
   const int step = side == 0 ? 1 : -1;
   const State32 a = state32(sm + row * kWinR + cw, kPlaneF, d);
   const State32 b = state32(sm + row * kWinR + cw + step, kPlaneF, d);
@@ -72,7 +194,7 @@ __device__ void ghost_columns_f32(float* sm, int row, int side, int cw, int t, c
     const Eq32 e = eq32(g[layer], d);
     float* gp = sm + row * kWinR + col;
     gp[0] = feq32(e, d, 0, 0, 1.f);
-#pragma unroll
+#pragma unroll 1
     for (int k = 1; k <= 4; ++k)
 #pragma unroll
       for (int i = 0; i < kHalf; ++i) {
@@ -84,14 +206,20 @@ __device__ void ghost_columns_f32(float* sm, int row, int side, int cw, int t, c
   if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
 }
 
-// MWB increment in upwind form (see device_common.cuh); rcp.approx is enough
-// for the limiter ratio in single precision.
-__device__ __forceinline__ float mwb32(float a, float K, float D, float Dp) {
-  const float den = fmaxf(fabsf(D) + fabsf(Dp), 1e-30f);
+__device__ __forceinline__ float rcp_approx(float x) {
   float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(den));
-  const float h = fabsf(D) * (D - Dp) * r;
-  return fmaf(a, D, K * h);
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// MWB increments of both nodes in upwind form:
+// a D + K |D| (D - Dp) / (|D| + |Dp|)  (0 when D = Dp = 0), Eq. (28).
+__device__ __forceinline__ f2 mwb2(f2 a, f2 K, f2 D, f2 Dp) {
+  const float den0 = fmaxf(fabsf(D.x) + fabsf(Dp.x), 1e-30f);
+  const float den1 = fmaxf(fabsf(D.y) + fabsf(Dp.y), 1e-30f);
+  const f2 t = mk2(fabsf(D.x) * rcp_approx(den0), fabsf(D.y) * rcp_approx(den1));
+  const f2 h = mul2(t, sub2(D, Dp));
+  return fma2(a, D, mul2(K, h));
 }
 
 }  // namespace
@@ -119,22 +247,11 @@ __global__ void __launch_bounds__(kStepThreads, 2)
 #pragma unroll 1
     for (int q = 0; q < kQ; ++q) tma_load_3d(sm + q * kPlaneF, &tmap_in, r0 - kLeft, t0, q, bar);
   }
-
-  // Courant table, one (pair, row) entry per thread, while the copies land.
-  {
+  {  // Courant entries of the tile rows: table layout [pair][row]
     const int pair = tid / kTileT, rl = tid % kTileT;
-    const int k = 1 + pair / kHalf, i = pair % kHalf;
-    const int q = 1 + (k - 1) * kNDirs + i;
     const int t = min(t0 + rl, p.n_theta - 1);
-    const double c = p.cos_t[t], s = p.sin_t[t];
-    const double vx = (double)d.vx[q] + (double)d.vx_lo[q], vy = (double)d.vy[q] + (double)d.vy_lo[q];
-    const double vr = vx * c + vy * s, vt = vy * c - vx * s;
-    const float ar = (float)(fabs(vr) * p.dt_dr);
-    const float aw = (float)(fabs(vt) * p.dt_dth);
-    const int flags = (vr < 0.0 ? 1 : 0) | (vt < 0.0 ? 2 : 0);
-    tab[pair * kTileT + rl] = make_float4(ar, ar - ar * ar, aw, __int_as_float(flags));
+    tab[pair * kTileT + rl] = p.courant[(size_t)t * kPairs + pair];
   }
-
   if (!mbar_wait_bounded(bar, 0, kWaitNs)) {
     if (tid == 0) atomicOr(p.status, PCLB_FLAG_TIMEOUT);
     mbar_wait_bounded(bar, 0, kWaitNs);
@@ -152,22 +269,23 @@ __global__ void __launch_bounds__(kStepThreads, 2)
   const int r = r0 + j2;
   const bool row_ok = t < p.n_theta;
   const bool v0 = row_ok && r < p.n_r, v1 = row_ok && r + 1 < p.n_r;
+  const float* win = sm + row * kWinR + col;
 
-  Eq32 eq[2];
-  bool ok = true;
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const bool valid = c == 0 ? v0 : v1;
-    State32 s;
-    if (valid) {
-      s = state32(sm + row * kWinR + col + c, kPlaneF, d);
-      ok = ok && s.ok;
-    } else {
-      s.rho = ff_of(1.f); s.ux = ff_of(0.f); s.uy = ff_of(0.f); s.E = ff_of(1.f); s.ok = true;
-    }
-    eq[c] = eq32(s, d);
+  Eq2 eq;
+  {
+    State2 s = state2(win, d);
+    const bool ok0 = s.rho.hi.x > 0.f && s.E.hi.x > 0.f && isfinite(s.E.hi.x) && isfinite(s.ux.hi.x) &&
+                     isfinite(s.uy.hi.x);
+    const bool ok1 = s.rho.hi.y > 0.f && s.E.hi.y > 0.f && isfinite(s.E.hi.y) && isfinite(s.ux.hi.y) &&
+                     isfinite(s.uy.hi.y);
+    if ((v0 && !ok0) || (v1 && !ok1)) atomicOr(p.status, PCLB_FLAG_NONPHYS);
+    // keep lanes without a valid node finite (their results are never stored)
+    if (!v0) { s.rho.hi.x = 1.f; s.rho.lo.x = 0.f; s.E.hi.x = 1.f; s.E.lo.x = 0.f;
+               s.ux.hi.x = 0.f; s.ux.lo.x = 0.f; s.uy.hi.x = 0.f; s.uy.lo.x = 0.f; }
+    if (!v1) { s.rho.hi.y = 1.f; s.rho.lo.y = 0.f; s.E.hi.y = 1.f; s.E.lo.y = 0.f;
+               s.ux.hi.y = 0.f; s.ux.lo.y = 0.f; s.uy.hi.y = 0.f; s.uy.lo.y = 0.f; }
+    eq = eq2(s, d);
   }
-  if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
 
   // ---- radial ghost columns ------------------------------------------------
   if (r0 == 0 && warp == 0 && lane < kTileT && t0 + lane < p.n_theta)
@@ -178,64 +296,54 @@ __global__ void __launch_bounds__(kStepThreads, 2)
   __syncthreads();
 
   // ---- update ----------------------------------------------------------------
-  const float inv_r0 = v0 ? (float)p.inv_r[r] : 1.f;
-  const float inv_r1 = v1 ? (float)p.inv_r[r + 1] : 1.f;
-  const float decay = (float)p.decay;
+  const f2 invr = mk2(v0 ? p.inv_r_f[r] : 1.f, v1 ? p.inv_r_f[r + 1] : 1.f);
+  const f2 decay = bc2((float)p.decay);
   const size_t plane_out = (size_t)p.rows * p.pitch;
   float* out_row = f_out + (size_t)(t + kGhostRows) * p.pitch + r;
   const bool lo_ghost = row_ok && t >= p.n_theta - 2;
   const bool hi_ghost = row_ok && t < 2;
   float* out_lo = f_out + (size_t)max(t - (p.n_theta - 2), 0) * p.pitch + r;
   float* out_hi = f_out + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r;
-  const float* win = sm + row * kWinR + col;
 
-  auto store = [&](int q, float o0, float o1) {
+  auto store = [&](int q, f2 o) {
     if (v1) {
-      *reinterpret_cast<float2*>(out_row + (size_t)q * plane_out) = make_float2(o0, o1);
-      if (lo_ghost) *reinterpret_cast<float2*>(out_lo + (size_t)d.recv_lo[q] * plane_out) = make_float2(o0, o1);
-      if (hi_ghost) *reinterpret_cast<float2*>(out_hi + (size_t)d.recv_hi[q] * plane_out) = make_float2(o0, o1);
+      *reinterpret_cast<float2*>(out_row + (size_t)q * plane_out) = o;
+      if (lo_ghost) *reinterpret_cast<float2*>(out_lo + (size_t)d.recv_lo[q] * plane_out) = o;
+      if (hi_ghost) *reinterpret_cast<float2*>(out_hi + (size_t)d.recv_hi[q] * plane_out) = o;
     } else if (v0) {
-      out_row[(size_t)q * plane_out] = o0;
-      if (lo_ghost) out_lo[(size_t)d.recv_lo[q] * plane_out] = o0;
-      if (hi_ghost) out_hi[(size_t)d.recv_hi[q] * plane_out] = o0;
+      out_row[(size_t)q * plane_out] = o.x;
+      if (lo_ghost) out_lo[(size_t)d.recv_lo[q] * plane_out] = o.x;
+      if (hi_ghost) out_hi[(size_t)d.recv_hi[q] * plane_out] = o.x;
     }
   };
 
-  // rest velocity: no convection
-  {
-    const float2 f0 = *reinterpret_cast<const float2*>(win);
-    const float e0 = eq[0].w[0] * eq[0].a0, e1 = eq[1].w[0] * eq[1].a0;
-    store(0, fmaf(f0.x - e0, decay, e0), fmaf(f0.y - e1, decay, e1));
+  {  // rest velocity: no convection
+    const f2 f0 = ld2(win);
+    const f2 e0 = mul2(eq.w[0], eq.a0);
+    store(0, fma2(sub2(f0, e0), decay, e0));
   }
 
-  // One velocity of a pair: sr = +1 if the upwind side is at larger r, st the
-  // same for theta (in rows); fe0, fe1 its equilibrium at the two nodes.
-  auto update = [&](int q, int sr, int st, float ar, float kr, float at0, float kt0, float at1,
-                    float kt1, float fe0, float fe1) {
+  // One velocity of a pair.  sr = +1 if its upwind neighbour in r is at
+  // larger r, st the same for theta (rows); fe is its equilibrium.
+  auto update = [&](int q, int sr, int st, f2 ar, f2 kr, f2 at, f2 kt, f2 fe) {
     const float* w = win + q * kPlaneF;
-    const float2 C = *reinterpret_cast<const float2*>(w);
-    const float2 S = *reinterpret_cast<const float2*>(w + 2 * sr);      // (j-2, j-1) or (j+2, j+3)
-    const float2 T1 = *reinterpret_cast<const float2*>(w + st * kWinR);
-    const float2 T2 = *reinterpret_cast<const float2*>(w + 2 * st * kWinR);
-    // upwind neighbours in r of the two nodes
-    const float u1a = sr < 0 ? S.y : C.y, u1b = sr < 0 ? C.x : S.x;
-    const float u2a = S.x, u2b = S.y;
-    const float mr0 = mwb32(ar, kr, C.x - u1a, u1a - u2a);
-    const float mr1 = mwb32(ar, kr, C.y - u1b, u1b - u2b);
-    const float mt0 = mwb32(at0, kt0, C.x - T1.x, T1.x - T2.x);
-    const float mt1 = mwb32(at1, kt1, C.y - T1.y, T1.y - T2.y);
-    const float o0 = fmaf(C.x - fe0, decay, fe0) - mr0 - mt0;
-    const float o1 = fmaf(C.y - fe1, decay, fe1) - mr1 - mt1;
-    store(q, o0, o1);
+    const f2 C = ld2(w);
+    const f2 S = ld2(w + 2 * sr);                 // (j-2, j-1) or (j+2, j+3)
+    const f2 T1 = ld2(w + st * kWinR);
+    const f2 T2 = ld2(w + 2 * st * kWinR);
+    const f2 u1 = sr < 0 ? mk2(S.y, C.x) : mk2(C.y, S.x);   // first upwind neighbours
+    const f2 mr = mwb2(ar, kr, sub2(C, u1), sub2(u1, S));
+    const f2 mt = mwb2(at, kt, sub2(C, T1), sub2(T1, T2));
+    const f2 o = sub2(sub2(fma2(sub2(C, fe), decay, fe), mr), mt);
+    store(q, o);
   };
 
-  // Shells run as a loop (keeps the unrolled body small enough for the
-  // instruction cache); the four direction pairs of a shell are unrolled.
+  // Shells run as a loop (keeps the hot body small for the instruction
+  // cache); the four direction pairs of a shell are unrolled.
 #pragma unroll 1
   for (int k = 1; k <= 4; ++k) {
-    const float sh = d.speed[k], sl = d.speed_lo[k];
-    const float wk0 = k == 1 ? eq[0].w[1] : (k == 2 ? eq[0].w[2] : (k == 3 ? eq[0].w[3] : eq[0].w[4]));
-    const float wk1 = k == 1 ? eq[1].w[1] : (k == 2 ? eq[1].w[2] : (k == 3 ? eq[1].w[3] : eq[1].w[4]));
+    const f2 sh = bc2(d.speed[k]), sl = bc2(d.speed_lo[k]);
+    const f2 wk = k == 1 ? eq.w[1] : (k == 2 ? eq.w[2] : (k == 3 ? eq.w[3] : eq.w[4]));
     const int qb = 1 + (k - 1) * kNDirs;
 #pragma unroll
     for (int i = 0; i < kHalf; ++i) {
@@ -244,22 +352,16 @@ __global__ void __launch_bounds__(kStepThreads, 2)
       const int fl = __float_as_int(tb.w);
       const int sr = (fl & 1) ? 1 : -1;            // v_r < 0: upwind at larger r
       const int st = (fl & 2) ? 1 : -1;            // v_theta < 0: upwind at larger theta
-      const float at0 = tb.z * inv_r0, at1 = tb.z * inv_r1;
-      const float kt0 = fmaf(-at0, at0, at0), kt1 = fmaf(-at1, at1, at1);
-      // equilibrium of the pair at both nodes: P(+x) = ev + od, P(-x) = ev - od
-      float fp[2], fm[2];
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const float x = x_of(sh, sl, eq[c].yh[i], eq[c].yl[i]);
-        const float x2 = x * x;
-        const float ev = fmaf(x2, fmaf(x2, 1.0f / 24.0f, eq[c].a1h), eq[c].a0);
-        const float od = x * fmaf(x2, 1.0f / 6.0f, eq[c].a1);
-        const float wk = c == 0 ? wk0 : wk1;
-        fp[c] = wk * (ev + od);
-        fm[c] = wk * (ev - od);
-      }
-      update(q, sr, st, tb.x, tb.y, at0, kt0, at1, kt1, fp[0], fp[1]);
-      update(q + kHalf, -sr, -st, tb.x, tb.y, at0, kt0, at1, kt1, fm[0], fm[1]);
+      const f2 ar = bc2(tb.x), kr = bc2(tb.y);
+      const f2 at = mul2(bc2(tb.z), invr);
+      const f2 kt = fma2(neg2(at), at, at);
+      // equilibrium of the pair: P(+x) = ev + od, P(-x) = ev - od
+      const f2 x = fma2(sh, eq.yh[i], fma2(sh, eq.yl[i], mul2(sl, eq.yh[i])));
+      const f2 x2 = mul2(x, x);
+      const f2 ev = fma2(x2, fma2(x2, bc2(1.0f / 24.0f), eq.a1h), eq.a0);
+      const f2 od = mul2(x, fma2(x2, bc2(1.0f / 6.0f), eq.a1));
+      update(q, sr, st, ar, kr, at, kt, mul2(wk, add2(ev, od)));
+      update(q + kHalf, -sr, -st, ar, kr, at, kt, mul2(wk, sub2(ev, od)));
     }
   }
 }
