@@ -194,6 +194,33 @@ pclb_status pclb_run_host(pclb_ctx* ctx, const void* rho, const void* u_r, const
                           const void* T, int32_t n, void* out_rho, void* out_u_r,
                           void* out_u_theta, void* out_T);
 
+/* Global integrals of a distribution, as pclb_diagnostics computes them, but
+ * without a context and without allocating any device memory.  The paper has
+ * no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code running inside a stream capture or inside an allocator's
+ * own callbacks, plug-ins that own no memory pool, hosts that have handed all
+ * device memory to another framework.  They pass only the input and the
+ * output; the reduction's scratch is a fixed file-scope device array.
+ *
+ * grid, dvm, prec: as for pclb_create (host, read during the call).
+ * f: device, [Q][n_theta][n_r] in prec's element type, not modified.
+ * out: host, 8 doubles laid out as in pclb_diagnostics.
+ * stream: cudaStream_t the kernels are queued on; the call waits for it
+ * (bounded wait, PCLB_ETIMEOUT) before copying the 8 results to out.
+ *
+ * Limit: n_theta <= 16384 (one 8-double partial per azimuthal row); larger
+ * grids are rejected with PCLB_EINVAL and a message.  The scratch array,
+ * (16384 + 1) x 8 doubles = 1 MiB, is held by every device that loads the
+ * library until the process exits.  The first call on a device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture.  Every call overwrites every slot it reads, so
+ * nothing needs clearing, and the array keeps the last call's contents.  All
+ * calls share the one array: calls that overlap on the GPU (other streams,
+ * other host threads) race on it and must be serialized by the caller.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library routine. */
+pclb_status pclb_diagnostics_noalloc(const pclb_grid* grid, const pclb_dvm* dvm, pclb_precision prec,
+                                     const void* f, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -150,4 +150,20 @@ __device__ __forceinline__ State32 state32_from_fields(float rho, float ux, floa
   return s;
 }
 
+// Node state (rho, u_x, u_y, E) in double for the global diagnostics, from the
+// FP32 path's float-float moments or the FP64 path's plain sums.
+__device__ __forceinline__ void node_state_double(const float* f, size_t plane, const DvmConst<float>& d,
+                                                  double& rho, double& ux, double& uy, double& E) {
+  const State32 m = state32(f, plane, d);
+  rho = (double)m.rho.hi + m.rho.lo;
+  ux = (double)m.ux.hi + m.ux.lo;
+  uy = (double)m.uy.hi + m.uy.lo;
+  E = (double)m.E.hi + m.E.lo;
+}
+__device__ __forceinline__ void node_state_double(const double* f, size_t plane, const DvmConst<double>& d,
+                                                  double& rho, double& ux, double& uy, double& E) {
+  const NodeState<double> m = node_moments(f, plane, d);
+  rho = m.rho; ux = m.ux; uy = m.uy; E = m.E;
+}
+
 }  // namespace pclb

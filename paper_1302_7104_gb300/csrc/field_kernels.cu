@@ -125,20 +125,6 @@ __global__ void unpack_kernel(const T* __restrict__ in, T* __restrict__ f, const
   store_with_ghosts<T>(f, p, d, q, t, r, in[((size_t)q * p.n_theta + t) * p.n_r + r]);
 }
 
-__device__ __forceinline__ void node_state_double(const float* f, size_t plane, const DvmConst<float>& d,
-                                                  double& rho, double& ux, double& uy, double& E) {
-  const State32 m = state32(f, plane, d);
-  rho = (double)m.rho.hi + m.rho.lo;
-  ux = (double)m.ux.hi + m.ux.lo;
-  uy = (double)m.uy.hi + m.uy.lo;
-  E = (double)m.E.hi + m.E.lo;
-}
-__device__ __forceinline__ void node_state_double(const double* f, size_t plane, const DvmConst<double>& d,
-                                                  double& rho, double& ux, double& uy, double& E) {
-  const NodeState<double> m = node_moments(f, plane, d);
-  rho = m.rho; ux = m.ux; uy = m.uy; E = m.E;
-}
-
 // Global integrals with weight r dr dtheta, in double.  Each block reduces a
 // fixed grid-stride subset in a fixed order, so results are reproducible.
 template <class T>

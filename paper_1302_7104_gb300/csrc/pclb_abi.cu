@@ -62,7 +62,10 @@ pclb_status cuda_fail(pclb_ctx* ctx, cudaError_t e, const char* what) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-pclb_status validate(const pclb_grid* g, const pclb_dvm* d, pclb_precision prec) {
+}  // namespace
+
+namespace pclb {
+pclb_status validate_problem(const pclb_grid* g, const pclb_dvm* d, pclb_precision prec) {
   if (!g || !d) return fail(nullptr, PCLB_EINVAL, "grid and dvm must not be NULL");
   if (prec != PCLB_FP32 && prec != PCLB_FP64) return fail(nullptr, PCLB_EINVAL, "unknown precision %d", (int)prec);
   if (g->n_r < 3) return fail(nullptr, PCLB_EINVAL, "n_r = %d; need at least 3 radial nodes", g->n_r);
@@ -85,6 +88,13 @@ pclb_status validate(const pclb_grid* g, const pclb_dvm* d, pclb_precision prec)
   for (int n = 0; n < 5; ++n)
     if (!std::isfinite(d->B[n])) return fail(nullptr, PCLB_EINVAL, "B[%d] is not finite", n);
   return PCLB_OK;
+}
+}  // namespace pclb
+
+namespace {
+using pclb::validate_problem;
+pclb_status validate(const pclb_grid* g, const pclb_dvm* d, pclb_precision prec) {
+  return validate_problem(g, d, prec);
 }
 
 Layout make_layout(const pclb_grid* g, pclb_precision prec) {
@@ -114,6 +124,9 @@ Layout make_layout(const pclb_grid* g, pclb_precision prec) {
 // sum_n B_n e_{4-n} E^n over the elementary symmetric polynomials e_j of the
 // other three shells' squared speeds (e_0 = 1), the denominator
 // v_k^2 prod_{l != k} (v_k^2 - v_l^2).
+}  // namespace
+
+namespace pclb {
 template <class T>
 void fill_dvm(DvmConst<T>& c, const pclb_dvm& d, const pclb_grid& g) {
   std::memset(&c, 0, sizeof(c));
@@ -178,6 +191,12 @@ void fill_dvm(DvmConst<T>& c, const pclb_dvm& d, const pclb_grid& g) {
       c.recv_hi[q] = (int8_t)(1 + (k - 1) * nd + (i + g.n_f) % nd);
     }
 }
+template void fill_dvm<float>(DvmConst<float>&, const pclb_dvm&, const pclb_grid&);
+template void fill_dvm<double>(DvmConst<double>&, const pclb_dvm&, const pclb_grid&);
+void set_thread_error(const char* msg) { std::snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace pclb
+
+namespace {
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;

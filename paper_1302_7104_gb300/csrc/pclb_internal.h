@@ -86,6 +86,12 @@ struct Layout {
 
 constexpr int kDiagBlocks = 304;    // 2 x 152 SMs
 
+// Host helpers shared by the C-ABI translation units (defined in pclb_abi.cu).
+pclb_status validate_problem(const pclb_grid* g, const pclb_dvm* d, pclb_precision prec);
+template <class T>
+void fill_dvm(DvmConst<T>& c, const pclb_dvm& d, const pclb_grid& g);
+void set_thread_error(const char* msg);   // text returned by pclb_last_error(NULL)
+
 // Element size of a precision.
 inline size_t elem_size(pclb_precision p) { return p == PCLB_FP64 ? 8 : 4; }
 

@@ -63,6 +63,8 @@ _SIGS = {
     "pclb_status_flags": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int32]),
     "pclb_sync": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "pclb_run_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]),
+    "pclb_diagnostics_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Dvm), ctypes.c_int, _vp,
+                                                ctypes.POINTER(ctypes.c_double), _vp]),
 }
 
 
@@ -242,6 +244,23 @@ class PCLB:
         _check(lib().pclb_run_host(self.ctx, *[_vp(t.data_ptr()) for t in ins], int(n),
                                    *[_vp(_ptr(t)) for t in outs]), self.ctx)
         return tuple(outs)
+
+
+def diagnostics_noalloc(w, f, precision: str = "fp32", stream=None) -> np.ndarray:
+    """Global integrals of the packed device distribution ``f`` ([Q][n_theta][n_r])
+    through pclb_diagnostics_noalloc: no context and no device allocation, for
+    callers that cannot allocate device memory.  Returns the 8 values of
+    ``PCLB.diagnostics``."""
+    torch = _torch()
+    prec = {"fp32": PCLB_FP32, "fp64": PCLB_FP64}[precision]
+    grid = Grid(int(w.n_r), int(w.n_theta), float(w.r_in), float(w.r_out), int(w.n_f))
+    dvm = Dvm(int(w.n_dirs), (ctypes.c_double * 5)(*w.speeds), (ctypes.c_double * 5)(*w.B))
+    if stream is None:
+        stream = torch.cuda.current_stream(f.device)
+    out = (ctypes.c_double * 8)()
+    _check(lib().pclb_diagnostics_noalloc(ctypes.byref(grid), ctypes.byref(dvm), prec, _vp(f.data_ptr()),
+                                          out, _vp(stream.cuda_stream)))
+    return np.array(out[:], dtype=np.float64)
 
 
 def exported_symbols():
