@@ -123,7 +123,8 @@ const char* pclb_last_error(const pclb_ctx* ctx);
 /* Bytes of device workspace pclb_create needs for this problem: two
  * ping-pong copies of f with two azimuthal ghost rows on each side and rows
  * padded to 32 elements, small tables, the status word and reduction
- * scratch.  Host-only; queues nothing. */
+ * scratch, three more state-sized buffers for the adjoint (a state copy and
+ * two adjoint variables) and host-I/O staging.  Host-only; queues nothing. */
 pclb_status pclb_workspace_size(const pclb_grid* grid, const pclb_dvm* dvm, pclb_precision prec,
                                 size_t* bytes);
 
@@ -193,6 +194,53 @@ pclb_status pclb_sync(pclb_ctx* ctx, int32_t timeout_ms);
 pclb_status pclb_run_host(pclb_ctx* ctx, const void* rho, const void* u_r, const void* u_theta,
                           const void* T, int32_t n, void* out_rho, void* out_u_r,
                           void* out_u_theta, void* out_T);
+
+/* ---------------------------------------------------------------------------
+ * Reverse mode.  The adjoint of one step (the vector-Jacobian product of the
+ * map f^n -> f^{n+1} of Eq. 38, including the radial ghost nodes of Eq. 39
+ * and the azimuthal periodicity of Eq. 40) is derived from the same
+ * equations; |x| in the switch function of Eq. (37) is differentiated on its
+ * active branch (d|x|/dx = sign x, sign 0 = 0).  The context holds one
+ * adjoint variable lam (the cotangent of the current distribution) in its
+ * workspace, in the same stored layout as f.
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of one stored state (distribution in the library's internal layout:
+ * azimuthal ghost rows and padded rows).  Host-only. */
+pclb_status pclb_state_bytes(pclb_ctx* ctx, size_t* bytes);
+
+/* Copy the current state to / from a caller buffer of pclb_state_bytes bytes
+ * (device, 16-byte aligned).  Bitwise; used for checkpoints and for the
+ * states the adjoint needs. */
+pclb_status pclb_save_state(pclb_ctx* ctx, void* state);
+pclb_status pclb_load_state(pclb_ctx* ctx, const void* state);
+
+/* Set / read the adjoint variable: device, [Q][n_theta][n_r], context
+ * precision. */
+pclb_status pclb_lambda_set(pclb_ctx* ctx, const void* lam);
+pclb_status pclb_lambda_get(pclb_ctx* ctx, void* lam);
+
+/* One adjoint step: lam <- J(f)^T lam, where f is the state the forward step
+ * started from: f_state (device, a buffer filled by pclb_save_state) or, if
+ * NULL, the context's current state.  One fused kernel launch. */
+pclb_status pclb_adjoint_state(pclb_ctx* ctx, const void* f_state);
+
+/* Convenience form in the packed layout: lam_n = J(f_n)^T lam_np1, all three
+ * device, [Q][n_theta][n_r].  Replaces the context's adjoint variable with
+ * lam_n; leaves the forward state alone. */
+pclb_status pclb_adjoint_step(pclb_ctx* ctx, const void* f_n, const void* lam_np1, void* lam_n);
+
+/* lam <- (d fields / d f)^T g at the current state, where fields = (rho,
+ * u_r, u_theta, T) as pclb_moments returns them (Eqs. 3-5).  g_*: device,
+ * [n_theta][n_r], context precision; NULL means a zero cotangent. */
+pclb_status pclb_moments_vjp(pclb_ctx* ctx, const void* g_rho, const void* g_ur, const void* g_ut,
+                             const void* g_T);
+
+/* Gradients of <lam, f^eq(rho, u_r, u_theta, T)> with respect to the fields
+ * (the adjoint of pclb_set_state, Eq. 10): fields as for pclb_set_state,
+ * outputs g_* device [n_theta][n_r] (any may be NULL). */
+pclb_status pclb_set_state_vjp(pclb_ctx* ctx, const void* rho, const void* u_r, const void* u_theta,
+                               const void* T, void* g_rho, void* g_ur, void* g_ut, void* g_T);
 
 /* Global integrals of a distribution, as pclb_diagnostics computes them, but
  * without a context and without allocating any device memory.  The paper has

@@ -68,7 +68,7 @@ def lib():
             L.orc_mwb_increment.restype = ctypes.c_double
             L.orc_mwb_increment.argtypes = [ctypes.c_double] * 6
             for name in ("orc_step", "orc_run", "orc_set_state", "orc_fields", "orc_diagnostics",
-                         "orc_step_jvp", "orc_adjoint_step"):
+                         "orc_step_jvp", "orc_adjoint_step", "orc_set_state_jvp", "orc_fields_jvp"):
                 getattr(L, name).restype = ctypes.c_int
         return _lib
 
@@ -208,6 +208,33 @@ def step_jvp(w, f, df, prob=None):
     out = np.empty_like(f)
     _check(lib().orc_step_jvp(prob.ref, _ptr(f), _ptr(df), _ptr(out)), "step_jvp")
     return out
+
+
+def _ptr_array(arrs):
+    keep = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
+    arr = (_dp * len(keep))(*[_ptr(a) for a in keep])
+    return arr, keep
+
+
+def set_state_jvp(w, fields, dfields, prob=None):
+    """d f^eq(fields) . dfields; fields, dfields: 4 arrays [n_theta][n_r]."""
+    prob = prob or Problem(w)
+    fa, k1 = _ptr_array(fields)
+    da, k2 = _ptr_array(dfields)
+    out = np.zeros(prob.shape)
+    _check(lib().orc_set_state_jvp(prob.ref, fa, da, _ptr(out)), "set_state_jvp")
+    return out
+
+
+def fields_jvp(w, f, df, prob=None):
+    """(d rho, d u_r, d u_theta, d T) = d fields(f) . df."""
+    prob = prob or Problem(w)
+    outs = [np.zeros((w.n_theta, w.n_r)) for _ in range(4)]
+    oa, keep = _ptr_array(outs)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    df = np.ascontiguousarray(df, dtype=np.float64)
+    _check(lib().orc_fields_jvp(prob.ref, _ptr(f), _ptr(df), oa), "fields_jvp")
+    return tuple(keep)
 
 
 def adjoint_step(w, f_n, lam_np1, prob=None):

@@ -338,6 +338,47 @@ bool valid(const orc_problem* P) {
   return true;
 }
 
+// f = f^eq of the fields (initial equilibrium); fields [n_theta][n_r] with
+// polar velocity components, f [Q][n_theta][n_r].
+template <class T>
+int set_state_impl(const orc_problem& P, const Dvm& d, const T* rho, const T* u_r, const T* u_t, const T* E,
+                   T* f) {
+  const int NR = P.n_r, NT = P.n_theta;
+  const double dth = 2.0 * M_PI * P.n_f / (double(P.n_dirs) * NT);
+  std::vector<T> fe(d.Q);
+  int status = 0;
+  for (int it = 0; it < NT; ++it) {
+    const double th = (it + 1) * dth, c = std::cos(th), s = std::sin(th);
+    for (int ir = 0; ir < NR; ++ir) {
+      size_t n = (size_t)it * NR + ir;
+      if (!(val(rho[n]) > 0 && val(E[n]) > 0)) status |= ORC_NONPHYS;
+      T ux = u_r[n] * c - u_t[n] * s, uy = u_r[n] * s + u_t[n] * c;
+      feq_node(d, rho[n], ux, uy, E[n], fe.data());  // E = T / (gamma - 1), gamma = 2
+      for (int q = 0; q < d.Q; ++q) f[((size_t)q * NT + it) * NR + ir] = fe[q];
+    }
+  }
+  return status;
+}
+
+// rho, u_r, u_theta, T of every node (Eqs. 3-5, polar components).
+template <class T>
+void fields_impl(const orc_problem& P, const Dvm& d, const T* f, T* rho, T* u_r, T* u_t, T* E) {
+  const int NR = P.n_r, NT = P.n_theta;
+  const double dth = 2.0 * M_PI * P.n_f / (double(P.n_dirs) * NT);
+  for (int it = 0; it < NT; ++it) {
+    const double th = (it + 1) * dth, c = std::cos(th), s = std::sin(th);
+    for (int ir = 0; ir < NR; ++ir) {
+      size_t n = (size_t)it * NR + ir;
+      T r_, ux, uy, e_;
+      moments_node(d, f + n, (long)NT * NR, r_, ux, uy, e_);
+      if (rho) rho[n] = r_;
+      if (u_r) u_r[n] = ux * c + uy * s;
+      if (u_t) u_t[n] = -ux * s + uy * c;
+      if (E) E[n] = e_;
+    }
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -386,21 +427,25 @@ int orc_set_state(const orc_problem* P, const double* rho, const double* u_r, co
                   const double* T, double* f) {
   if (!valid(P)) return ORC_EINVAL;
   Dvm d = make_dvm(P->n_dirs, P->speeds, P->B);
-  const int NR = P->n_r, NT = P->n_theta;
-  const double dth = 2.0 * M_PI * P->n_f / (double(P->n_dirs) * NT);
-  std::vector<double> fe(d.Q);
-  int status = 0;
-  for (int it = 0; it < NT; ++it) {
-    const double th = (it + 1) * dth, c = std::cos(th), s = std::sin(th);
-    for (int ir = 0; ir < NR; ++ir) {
-      size_t n = (size_t)it * NR + ir;
-      if (!(rho[n] > 0 && T[n] > 0)) status |= ORC_NONPHYS;
-      double ux = u_r[n] * c - u_t[n] * s, uy = u_r[n] * s + u_t[n] * c;
-      feq_node(d, rho[n], ux, uy, T[n], fe.data());  // E = T / (gamma - 1), gamma = 2
-      for (int q = 0; q < d.Q; ++q) f[((size_t)q * NT + it) * NR + ir] = fe[q];
-    }
+  return set_state_impl<double>(*P, d, rho, u_r, u_t, T, f);
+}
+
+// Directional derivative of f^eq(fields): df = d f^eq / d fields . dfields.
+// fields / dfields: 4 arrays each [n_theta][n_r] (rho, u_r, u_theta, T).
+int orc_set_state_jvp(const orc_problem* P, const double* const* fields, const double* const* dfields,
+                      double* df) {
+  if (!valid(P)) return ORC_EINVAL;
+  Dvm d = make_dvm(P->n_dirs, P->speeds, P->B);
+  const size_t N = (size_t)P->n_r * P->n_theta;
+  std::vector<Dual> x[4];
+  for (int k = 0; k < 4; ++k) {
+    x[k].resize(N);
+    for (size_t n = 0; n < N; ++n) x[k][n] = Dual(fields[k][n], dfields[k][n]);
   }
-  return status;
+  std::vector<Dual> y((size_t)d.Q * N);
+  int st = set_state_impl<Dual>(*P, d, x[0].data(), x[1].data(), x[2].data(), x[3].data(), y.data());
+  for (size_t i = 0; i < y.size(); ++i) df[i] = y[i].d;
+  return st;
 }
 
 // rho, u_r, u_theta, T of every node from f (any output may be NULL).
@@ -408,20 +453,21 @@ int orc_fields(const orc_problem* P, const double* f, double* rho, double* u_r, 
                double* T) {
   if (!valid(P)) return ORC_EINVAL;
   Dvm d = make_dvm(P->n_dirs, P->speeds, P->B);
-  const int NR = P->n_r, NT = P->n_theta;
-  const double dth = 2.0 * M_PI * P->n_f / (double(P->n_dirs) * NT);
-  for (int it = 0; it < NT; ++it) {
-    const double th = (it + 1) * dth, c = std::cos(th), s = std::sin(th);
-    for (int ir = 0; ir < NR; ++ir) {
-      size_t n = (size_t)it * NR + ir;
-      double r_, ux, uy, E;
-      moments_node(d, f + n, (long)NT * NR, r_, ux, uy, E);
-      if (rho) rho[n] = r_;
-      if (u_r) u_r[n] = ux * c + uy * s;
-      if (u_t) u_t[n] = -ux * s + uy * c;
-      if (T) T[n] = E;
-    }
-  }
+  fields_impl<double>(*P, d, f, rho, u_r, u_t, T);
+  return 0;
+}
+
+// Directional derivative of the fields: dfields[k] = d field_k / d f . df.
+int orc_fields_jvp(const orc_problem* P, const double* f, const double* df, double* const* dfields) {
+  if (!valid(P)) return ORC_EINVAL;
+  Dvm d = make_dvm(P->n_dirs, P->speeds, P->B);
+  const size_t N = (size_t)P->n_r * P->n_theta;
+  std::vector<Dual> x((size_t)d.Q * N), o[4];
+  for (size_t i = 0; i < x.size(); ++i) x[i] = Dual(f[i], df[i]);
+  for (int k = 0; k < 4; ++k) o[k].resize(N);
+  fields_impl<Dual>(*P, d, x.data(), o[0].data(), o[1].data(), o[2].data(), o[3].data());
+  for (int k = 0; k < 4; ++k)
+    for (size_t n = 0; n < N; ++n) dfields[k][n] = o[k][n].d;
   return 0;
 }
 

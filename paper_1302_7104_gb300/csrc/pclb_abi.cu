@@ -33,6 +33,15 @@ cudaError_t launch_unpack(const T*, T*, const StepParams&, const DvmConst<T>&, c
 template <class T>
 cudaError_t launch_diagnostics(const T*, double*, double*, const StepParams&, const DvmConst<T>&,
                                double, double, double, cudaStream_t);
+template <class T>
+cudaError_t launch_adjoint(const CUtensorMap*, const CUtensorMap*, T*, const StepParams&, const DvmConst<T>&,
+                           cudaStream_t);
+template <class T>
+cudaError_t launch_moments_vjp(const T*, const T*, const T*, const T*, const T*, T*, const StepParams&,
+                               const DvmConst<T>&, cudaStream_t);
+template <class T>
+cudaError_t launch_set_state_vjp(const T*, const T*, const T*, const T*, const T*, T*, T*, T*, T*,
+                                 const StepParams&, const DvmConst<T>&, cudaStream_t);
 }  // namespace pclb
 
 using namespace pclb;
@@ -45,6 +54,7 @@ constexpr int kDefaultTimeoutMs = 120000;
 struct HostCtx : pclb_ctx {
   std::vector<double> cos_t, sin_t, inv_r, bc_vals;
   std::vector<float> courant, inv_r_f;
+  std::vector<double> courant64;
 };
 
 pclb_status fail(pclb_ctx* ctx, pclb_status st, const char* fmt, ...) {
@@ -106,11 +116,15 @@ Layout make_layout(const pclb_grid* g, pclb_precision prec) {
   size_t off = 0;
   L.f[0] = off; off += L.f_bytes;
   L.f[1] = off; off += L.f_bytes;
+  L.adj_f = off; off += L.f_bytes;
+  L.lam[0] = off; off += L.f_bytes;
+  L.lam[1] = off; off += L.f_bytes;
   L.cos_t = off; off = align_up(off + (size_t)g->n_theta * 8, 256);
   L.sin_t = off; off = align_up(off + (size_t)g->n_theta * 8, 256);
   L.inv_r = off; off = align_up(off + (size_t)g->n_r * 8, 256);
   L.bc_vals = off; off = align_up(off + (size_t)2 * 2 * 4 * g->n_theta * 8, 256);
-  L.courant = off; off = align_up(off + (size_t)g->n_theta * (4 * kNDirs / 2) * 16, 256);
+  L.courant = off; off = align_up(off + (size_t)(g->n_theta + 2 * kGhostRows) * (4 * kNDirs / 2) * 16, 256);
+  L.courant64 = off; off = align_up(off + (size_t)(g->n_theta + 2 * kGhostRows) * (4 * kNDirs / 2) * 32, 256);
   L.inv_r_f = off; off = align_up(off + (size_t)g->n_r * 4, 256);
   L.status = off; off = align_up(off + 256, 256);
   L.partials = off; off = align_up(off + (size_t)kDiagBlocks * 8 * 8, 256);
@@ -211,21 +225,28 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
   return fn;
 }
 
-pclb_status make_tmap(pclb_ctx* ctx, int which) {
+// TMA descriptor of one stored distribution (f or lam layout) at `base`,
+// with a box of kWinR columns by box_rows rows and one label.
+pclb_status encode_map(pclb_ctx* ctx, const void* base, int box_rows, CUtensorMap* out) {
   auto enc = get_encode_fn();
   if (!enc) return fail(ctx, PCLB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return fail(ctx, PCLB_EINVAL, "state buffer not 16-byte aligned");
   const size_t es = elem_size(ctx->prec);
   cuuint64_t dims[3] = {(cuuint64_t)ctx->grid.n_r, (cuuint64_t)ctx->sp.rows, (cuuint64_t)kQ};
   cuuint64_t strides[2] = {(cuuint64_t)ctx->sp.pitch * es, (cuuint64_t)ctx->sp.pitch * ctx->sp.rows * es};
-  cuuint32_t box[3] = {(cuuint32_t)kWinR, (cuuint32_t)kWinT, 1};
+  cuuint32_t box[3] = {(cuuint32_t)kWinR, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(&ctx->tmap[which],
-                   ctx->prec == PCLB_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                   3, ctx->ws + ctx->lay.f[which], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(out, ctx->prec == PCLB_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                   3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(ctx, PCLB_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
   return PCLB_OK;
+}
+
+int adj_box_rows(const pclb_ctx* ctx) { return (ctx->prec == PCLB_FP64 ? kAdjRows64 : kAdjRows32) + 4; }
+
+pclb_status make_tmap(pclb_ctx* ctx, int which) {
+  return encode_map(ctx, ctx->ws + ctx->lay.f[which], kWinT, &ctx->tmap[which]);
 }
 
 pclb_status bounded_sync(pclb_ctx* ctx, int timeout_ms) {
@@ -285,6 +306,16 @@ pclb_status do_step(pclb_ctx* ctx, int n) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "step kernel launch");
     ctx->cur = dst;
   }
+  return PCLB_OK;
+}
+
+template <class T>
+pclb_status do_adjoint(pclb_ctx* ctx, const CUtensorMap* tmap_f) {
+  const int src = ctx->cur_lam, dst = 1 - ctx->cur_lam;
+  cudaError_t e = launch_adjoint<T>(tmap_f, &ctx->tmap_adj[3 + src], reinterpret_cast<T*>(ctx->ws + ctx->lay.lam[dst]),
+                                    ctx->sp, dvm_of<T>(ctx), ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint kernel launch");
+  ctx->cur_lam = dst;
   return PCLB_OK;
 }
 
@@ -374,17 +405,24 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
   }
   ctx->inv_r.resize(NR);
   for (int r = 0; r < NR; ++r) ctx->inv_r[r] = 1.0 / (grid->r_in + r * dr);
-  // Courant table of the FP32 kernel: for every theta node and every pair of
-  // opposite velocities (first label q = 1 + (k-1) N_i + i, i < N_i / 2).
+  // Courant table: for every stored row (theta node t = row - 2, including the
+  // two ghost rows on each side at theta = (t + 1) dtheta outside the period)
+  // and every pair of opposite velocities (first label q = 1 + (k-1) N_i + i,
+  // i < N_i / 2).
   const int npairs = 4 * dvm->n_dirs / 2;
-  ctx->courant.resize((size_t)NT * npairs * 4);
-  for (int t = 0; t < NT; ++t)
+  const int nrows = NT + 2 * kGhostRows;
+  ctx->courant.resize((size_t)nrows * npairs * 4);
+  ctx->courant64.resize((size_t)nrows * npairs * 4);
+  for (int t = 0; t < nrows; ++t)
     for (int k = 1; k <= 4; ++k)
       for (int i = 0; i < dvm->n_dirs / 2; ++i) {
         const double phi = 2.0 * M_PI * i / dvm->n_dirs;
         const double vx = dvm->speeds[k] * std::cos(phi), vy = dvm->speeds[k] * std::sin(phi);
-        const double vr = vx * ctx->cos_t[t] + vy * ctx->sin_t[t];
-        const double vt = vy * ctx->cos_t[t] - vx * ctx->sin_t[t];
+        const double th = (t - kGhostRows + 1) * dth;
+        const double ct = t >= kGhostRows && t < NT + kGhostRows ? ctx->cos_t[t - kGhostRows] : std::cos(th);
+        const double st = t >= kGhostRows && t < NT + kGhostRows ? ctx->sin_t[t - kGhostRows] : std::sin(th);
+        const double vr = vx * ct + vy * st;
+        const double vt = vy * ct - vx * st;
         const double ar = std::fabs(vr) * dt / dr;
         float* e = ctx->courant.data() + ((size_t)t * npairs + (k - 1) * (dvm->n_dirs / 2) + i) * 4;
         e[0] = (float)ar;
@@ -392,6 +430,11 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
         e[2] = (float)(std::fabs(vt) * dt / dth);
         const int flags = (vr < 0.0 ? 1 : 0) | (vt < 0.0 ? 2 : 0);
         std::memcpy(&e[3], &flags, 4);
+        double* e64 = ctx->courant64.data() + ((size_t)t * npairs + (k - 1) * (dvm->n_dirs / 2) + i) * 4;
+        e64[0] = ar;
+        e64[1] = ar * (1.0 - ar);
+        e64[2] = std::fabs(vt) * dt / dth;
+        e64[3] = (double)flags;
       }
   ctx->inv_r_f.resize(NR);
   for (int r = 0; r < NR; ++r) ctx->inv_r_f[r] = (float)ctx->inv_r[r];
@@ -415,6 +458,7 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
   sp.inv_r = reinterpret_cast<const double*>(ctx->ws + lay.inv_r);
   sp.bc_vals = reinterpret_cast<const double*>(ctx->ws + lay.bc_vals);
   sp.courant = reinterpret_cast<const float4*>(ctx->ws + lay.courant);
+  sp.courant64 = reinterpret_cast<const double*>(ctx->ws + lay.courant64);
   sp.inv_r_f = reinterpret_cast<const float*>(ctx->ws + lay.inv_r_f);
   sp.status = reinterpret_cast<uint32_t*>(ctx->ws + lay.status);
   fill_dvm(ctx->dvm32, *dvm, *grid);
@@ -423,7 +467,8 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
   struct Up { size_t off; const void* src; size_t n; } ups[] = {
       {lay.cos_t, ctx->cos_t.data(), NT * 8ul}, {lay.sin_t, ctx->sin_t.data(), NT * 8ul},
       {lay.inv_r, ctx->inv_r.data(), NR * 8ul}, {lay.bc_vals, ctx->bc_vals.data(), ctx->bc_vals.size() * 8},
-      {lay.courant, ctx->courant.data(), ctx->courant.size() * 4}, {lay.inv_r_f, ctx->inv_r_f.data(), NR * 4ul}};
+      {lay.courant, ctx->courant.data(), ctx->courant.size() * 4},
+      {lay.courant64, ctx->courant64.data(), ctx->courant64.size() * 8}, {lay.inv_r_f, ctx->inv_r_f.data(), NR * 4ul}};
   for (const Up& u : ups) {
     cudaError_t e = cudaMemcpyAsync(ctx->ws + u.off, u.src, u.n, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) {
@@ -438,8 +483,12 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
     delete ctx;
     return s2;
   }
-  for (int w = 0; w < 2; ++w) {
-    pclb_status s2 = make_tmap(ctx, w);
+  ctx->cur_lam = 0;
+  ctx->has_lam = false;
+  const size_t adj_bufs[5] = {lay.f[0], lay.f[1], lay.adj_f, lay.lam[0], lay.lam[1]};
+  for (int w = 0; w < 7; ++w) {
+    pclb_status s2 = w < 2 ? make_tmap(ctx, w)
+                           : encode_map(ctx, ctx->ws + adj_bufs[w - 2], adj_box_rows(ctx), &ctx->tmap_adj[w - 2]);
     if (s2 != PCLB_OK) {
       std::snprintf(g_err, sizeof(g_err), "%s", ctx->err);
       delete ctx;
@@ -591,6 +640,120 @@ pclb_status pclb_run_host(pclb_ctx* ctx, const void* rho, const void* u_r, const
     if (e != cudaSuccess) return cuda_fail(ctx, e, "output copy");
   }
   return bounded_sync(ctx, kDefaultTimeoutMs);
+}
+
+pclb_status pclb_state_bytes(pclb_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return fail(ctx, PCLB_EINVAL, "ctx and bytes must not be NULL");
+  *bytes = ctx->lay.f_bytes;
+  return PCLB_OK;
+}
+
+pclb_status pclb_save_state(pclb_ctx* ctx, void* state) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!state) return fail(ctx, PCLB_EINVAL, "state must not be NULL");
+  if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
+  cudaError_t e = cudaMemcpyAsync(state, ctx->ws + ctx->lay.f[ctx->cur], ctx->lay.f_bytes, cudaMemcpyDeviceToDevice,
+                                  ctx->stream);
+  return e == cudaSuccess ? PCLB_OK : cuda_fail(ctx, e, "state copy");
+}
+
+pclb_status pclb_load_state(pclb_ctx* ctx, const void* state) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!state) return fail(ctx, PCLB_EINVAL, "state must not be NULL");
+  cudaError_t e = cudaMemcpyAsync(ctx->ws + ctx->lay.f[ctx->cur], state, ctx->lay.f_bytes, cudaMemcpyDeviceToDevice,
+                                  ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "state copy");
+  ctx->has_state = true;
+  return PCLB_OK;
+}
+
+pclb_status pclb_lambda_set(pclb_ctx* ctx, const void* lam) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!lam) return fail(ctx, PCLB_EINVAL, "lam must not be NULL");
+  void* dst = ctx->ws + ctx->lay.lam[ctx->cur_lam];
+  cudaError_t e = ctx->prec == PCLB_FP32
+                      ? launch_unpack<float>((const float*)lam, (float*)dst, ctx->sp, ctx->dvm32, ctx->stream)
+                      : launch_unpack<double>((const double*)lam, (double*)dst, ctx->sp, ctx->dvm64, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lambda unpack launch");
+  ctx->has_lam = true;
+  return PCLB_OK;
+}
+
+pclb_status pclb_lambda_get(pclb_ctx* ctx, void* lam) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!lam) return fail(ctx, PCLB_EINVAL, "lam must not be NULL");
+  if (!ctx->has_lam) return fail(ctx, PCLB_ESTATE, "no adjoint variable: call pclb_lambda_set or pclb_moments_vjp");
+  const void* src = ctx->ws + ctx->lay.lam[ctx->cur_lam];
+  cudaError_t e = ctx->prec == PCLB_FP32 ? launch_pack<float>((const float*)src, (float*)lam, ctx->sp, ctx->stream)
+                                         : launch_pack<double>((const double*)src, (double*)lam, ctx->sp, ctx->stream);
+  return e == cudaSuccess ? PCLB_OK : cuda_fail(ctx, e, "lambda pack launch");
+}
+
+pclb_status pclb_adjoint_state(pclb_ctx* ctx, const void* f_state) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!ctx->has_lam) return fail(ctx, PCLB_ESTATE, "no adjoint variable: call pclb_lambda_set or pclb_moments_vjp");
+  const CUtensorMap* map;
+  CUtensorMap local;
+  if (f_state == nullptr) {
+    if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
+    map = &ctx->tmap_adj[ctx->cur];
+  } else {
+    pclb_status st = encode_map(ctx, f_state, adj_box_rows(ctx), &local);
+    if (st != PCLB_OK) return st;
+    map = &local;
+  }
+  return ctx->prec == PCLB_FP32 ? do_adjoint<float>(ctx, map) : do_adjoint<double>(ctx, map);
+}
+
+pclb_status pclb_adjoint_step(pclb_ctx* ctx, const void* f_n, const void* lam_np1, void* lam_n) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!f_n || !lam_np1 || !lam_n) return fail(ctx, PCLB_EINVAL, "f_n, lam_np1 and lam_n must not be NULL");
+  void* adj = ctx->ws + ctx->lay.adj_f;
+  cudaError_t e = ctx->prec == PCLB_FP32
+                      ? launch_unpack<float>((const float*)f_n, (float*)adj, ctx->sp, ctx->dvm32, ctx->stream)
+                      : launch_unpack<double>((const double*)f_n, (double*)adj, ctx->sp, ctx->dvm64, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "state unpack launch");
+  pclb_status st = pclb_lambda_set(ctx, lam_np1);
+  if (st != PCLB_OK) return st;
+  st = ctx->prec == PCLB_FP32 ? do_adjoint<float>(ctx, &ctx->tmap_adj[2]) : do_adjoint<double>(ctx, &ctx->tmap_adj[2]);
+  if (st != PCLB_OK) return st;
+  return pclb_lambda_get(ctx, lam_n);
+}
+
+pclb_status pclb_moments_vjp(pclb_ctx* ctx, const void* g_rho, const void* g_ur, const void* g_ut, const void* g_T) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
+  void* lam = ctx->ws + ctx->lay.lam[ctx->cur_lam];
+  const void* f = ctx->ws + ctx->lay.f[ctx->cur];
+  cudaError_t e;
+  if (ctx->prec == PCLB_FP32)
+    e = launch_moments_vjp<float>((const float*)f, (const float*)g_rho, (const float*)g_ur, (const float*)g_ut,
+                                  (const float*)g_T, (float*)lam, ctx->sp, ctx->dvm32, ctx->stream);
+  else
+    e = launch_moments_vjp<double>((const double*)f, (const double*)g_rho, (const double*)g_ur,
+                                   (const double*)g_ut, (const double*)g_T, (double*)lam, ctx->sp, ctx->dvm64,
+                                   ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "moments vjp launch");
+  ctx->has_lam = true;
+  return PCLB_OK;
+}
+
+pclb_status pclb_set_state_vjp(pclb_ctx* ctx, const void* rho, const void* u_r, const void* u_theta, const void* T,
+                               void* g_rho, void* g_ur, void* g_ut, void* g_T) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!rho || !u_r || !u_theta || !T) return fail(ctx, PCLB_EINVAL, "field pointers must not be NULL");
+  if (!ctx->has_lam) return fail(ctx, PCLB_ESTATE, "no adjoint variable: call pclb_lambda_set first");
+  const void* lam = ctx->ws + ctx->lay.lam[ctx->cur_lam];
+  cudaError_t e;
+  if (ctx->prec == PCLB_FP32)
+    e = launch_set_state_vjp<float>((const float*)rho, (const float*)u_r, (const float*)u_theta, (const float*)T,
+                                    (const float*)lam, (float*)g_rho, (float*)g_ur, (float*)g_ut, (float*)g_T, ctx->sp,
+                                    ctx->dvm32, ctx->stream);
+  else
+    e = launch_set_state_vjp<double>((const double*)rho, (const double*)u_r, (const double*)u_theta,
+                                     (const double*)T, (const double*)lam, (double*)g_rho, (double*)g_ur,
+                                     (double*)g_ut, (double*)g_T, ctx->sp, ctx->dvm64, ctx->stream);
+  return e == cudaSuccess ? PCLB_OK : cuda_fail(ctx, e, "set_state vjp launch");
 }
 
 }  // extern "C"

@@ -28,6 +28,9 @@ constexpr int kLeft = 4;            // column of interior r0 inside the window
 constexpr int kStepThreads = 256;   // 8 warps; each thread owns 2 nodes (rows w and w + 8)
 constexpr int kPitchAlign = 32;     // row pitch in elements (128 B for float)
 constexpr int kGhostRows = 2;       // azimuthal ghost rows stored on each side
+// Tile rows of the adjoint kernel (its window holds f and lam for all labels).
+constexpr int kAdjRows32 = 8;
+constexpr int kAdjRows64 = 4;
 
 // Per-velocity constants, in the arithmetic type T of the kernel, plus the
 // double-precision ones the moment / temperature recovery uses.
@@ -65,9 +68,11 @@ struct StepParams {
   const double* sin_t;        // [n_theta]
   const double* inv_r;        // [n_r] 1 / r_i
   const double* bc_vals;      // [2 sides][2 layers][4 fields][n_theta] or unused
-  const float4* courant;      // [n_theta][4 n_dirs / 2]: per opposite-velocity pair (first label
+  const float4* courant;      // [n_theta + 4][4 n_dirs / 2] (stored rows, ghosts included): per
+                              // opposite-velocity pair (first label
                               // q of the pair) |C_r|, |C_r|(1 - |C_r|), |v_theta| dt / dtheta,
                               // flags (bit 0: v_r < 0, bit 1: v_theta < 0) as int bits
+  const double* courant64;    // the same table in double: [n_theta + 4][pairs][4] (flags as value)
   const float* inv_r_f;       // [n_r] 1 / r_i in float
   uint32_t* status;           // device status word (PCLB_FLAG_*)
 };
@@ -75,8 +80,10 @@ struct StepParams {
 // Workspace layout (byte offsets from the caller's base pointer).
 struct Layout {
   size_t f[2];                // two ping-pong distributions [Q][rows][pitch]
+  size_t adj_f;               // a state copy for pclb_adjoint_step
+  size_t lam[2];              // ping-pong adjoint variables, same layout as f
   size_t f_bytes;
-  size_t cos_t, sin_t, inv_r, bc_vals, courant, inv_r_f;
+  size_t cos_t, sin_t, inv_r, bc_vals, courant, courant64, inv_r_f;
   size_t status;              // uint32 status word (+ padding)
   size_t partials;            // double [kDiagBlocks][8] reduction partials
   size_t diag_out;            // double [8]
@@ -110,6 +117,9 @@ struct pclb_ctx {
   int cur;                    // which of the two f buffers holds the state
   bool has_state;
   CUtensorMap tmap[2];        // TMA descriptors of the two f buffers
+  CUtensorMap tmap_adj[5];    // adjoint-window descriptors: f[0], f[1], adj_f, lam[0], lam[1]
+  int cur_lam;                // which lam buffer holds the adjoint variable
+  bool has_lam;
   pclb::StepParams sp;
   pclb::DvmConst<float> dvm32;
   pclb::DvmConst<double> dvm64;

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kStepThreads, 2)
   {  // Courant entries of the tile rows: table layout [pair][row]
     const int pair = tid / kTileT, rl = tid % kTileT;
     const int t = min(t0 + rl, p.n_theta - 1);
-    tab[pair * kTileT + rl] = p.courant[(size_t)t * kPairs + pair];
+    tab[pair * kTileT + rl] = p.courant[(size_t)(t + kGhostRows) * kPairs + pair];
   }
   if (!mbar_wait_bounded(bar, 0, kWaitNs)) {
     if (tid == 0) atomicOr(p.status, PCLB_FLAG_TIMEOUT);

@@ -63,6 +63,15 @@ _SIGS = {
     "pclb_status_flags": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int32]),
     "pclb_sync": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "pclb_run_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]),
+    "pclb_state_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "pclb_save_state": (ctypes.c_int, [_vp, _vp]),
+    "pclb_load_state": (ctypes.c_int, [_vp, _vp]),
+    "pclb_lambda_set": (ctypes.c_int, [_vp, _vp]),
+    "pclb_lambda_get": (ctypes.c_int, [_vp, _vp]),
+    "pclb_adjoint_state": (ctypes.c_int, [_vp, _vp]),
+    "pclb_adjoint_step": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "pclb_moments_vjp": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "pclb_set_state_vjp": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pclb_diagnostics_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.POINTER(Dvm), ctypes.c_int, _vp,
                                                 ctypes.POINTER(ctypes.c_double), _vp]),
 }
@@ -230,6 +239,72 @@ class PCLB:
 
     def sync(self, timeout_ms: int = 120000):
         _check(lib().pclb_sync(self.ctx, int(timeout_ms)), self.ctx)
+
+    # -- reverse mode --------------------------------------------------------
+    def state_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().pclb_state_bytes(self.ctx, ctypes.byref(n)), self.ctx)
+        return int(n.value)
+
+    def new_state(self):
+        """A device buffer for one stored state (uint8 tensor)."""
+        return _torch().empty(self.state_bytes(), dtype=_torch().uint8, device=self.device)
+
+    def save_state(self, buf=None):
+        buf = self.new_state() if buf is None else buf
+        _check(lib().pclb_save_state(self.ctx, _vp(buf.data_ptr())), self.ctx)
+        return buf
+
+    def load_state(self, buf):
+        _check(lib().pclb_load_state(self.ctx, _vp(buf.data_ptr())), self.ctx)
+        self._hold = [buf]
+        return self
+
+    def lambda_set(self, lam):
+        torch = _torch()
+        t = torch.as_tensor(lam, dtype=self.dtype, device=self.device).contiguous()
+        if tuple(t.shape) != (self.q, self.n_theta, self.n_r):
+            raise ValueError("lam must be [Q][n_theta][n_r]")
+        _check(lib().pclb_lambda_set(self.ctx, _vp(t.data_ptr())), self.ctx)
+        self._hold = [t]
+        return self
+
+    def lambda_get(self, out=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty((self.q, self.n_theta, self.n_r), dtype=self.dtype, device=self.device)
+        _check(lib().pclb_lambda_get(self.ctx, _vp(out.data_ptr())), self.ctx)
+        return out
+
+    def adjoint_state(self, f_state=None):
+        """lam <- J(f)^T lam for the state f saved in ``f_state`` (or the current one)."""
+        _check(lib().pclb_adjoint_state(self.ctx, _vp(None if f_state is None else f_state.data_ptr())), self.ctx)
+        return self
+
+    def adjoint_step(self, f_n, lam_np1, out=None):
+        torch = _torch()
+        f = torch.as_tensor(f_n, dtype=self.dtype, device=self.device).contiguous()
+        lam = torch.as_tensor(lam_np1, dtype=self.dtype, device=self.device).contiguous()
+        if out is None:
+            out = torch.empty_like(lam)
+        _check(lib().pclb_adjoint_step(self.ctx, _vp(f.data_ptr()), _vp(lam.data_ptr()), _vp(out.data_ptr())),
+               self.ctx)
+        self._hold = [f, lam]
+        return out
+
+    def moments_vjp(self, g_rho=None, g_ur=None, g_ut=None, g_T=None):
+        gs = [None if g is None else self._field(g) for g in (g_rho, g_ur, g_ut, g_T)]
+        _check(lib().pclb_moments_vjp(self.ctx, *[_vp(_ptr(g)) for g in gs]), self.ctx)
+        self._hold = gs
+        return self
+
+    def set_state_vjp(self, rho, u_r, u_theta, T):
+        fs = [self._field(x) for x in (rho, u_r, u_theta, T)]
+        outs = [self.empty_field() for _ in range(4)]
+        _check(lib().pclb_set_state_vjp(self.ctx, *[_vp(_ptr(t)) for t in fs], *[_vp(_ptr(t)) for t in outs]),
+               self.ctx)
+        self._hold = fs
+        return tuple(outs)
 
     def run_host(self, rho, u_r, u_theta, T, n: int, outs=None):
         """End-to-end call with host arrays (numpy or CPU tensors, ideally

@@ -1,0 +1,119 @@
+"""The GPU adjoint step and the field VJPs against the oracle (GPU).
+
+FP64: the adjoint step equals the oracle's vector-Jacobian product (built
+column by column from forward-mode derivatives of the oracle's step) within
+1e-12 of its largest entry; on larger grids the transpose identity
+<lam, J df> = <J^T lam, df> holds against the oracle's JVP.  FP32: within
+1e-4.  The field VJPs satisfy the same identity against the oracle's JVPs.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1302_7104_gb300 import inputs as I
+from paper_1302_7104_gb300 import pclb as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _state(w, seed=3, noise=0.02):
+    f = O.set_state(w)
+    rng = np.random.default_rng(seed)
+    return np.ascontiguousarray(f * (1.0 + noise * rng.normal(size=f.shape)))
+
+
+SMALL = {
+    "extrap": lambda: I.random_smooth(6, 8, seed=3),
+    "dirichlet_wall": lambda: I.random_smooth(7, 8, seed=4, bc_kind=(I.BC_DIRICHLET, I.BC_WALL)),
+    "wall_extrap": lambda: I.random_smooth(5, 9, seed=5, bc_kind=(I.BC_WALL, I.BC_EXTRAP)),
+    "sector_nf1": lambda: I.random_smooth(6, 5, seed=6, n_f=1),
+    "smallest": lambda: I.random_smooth(3, 2, seed=7),
+    "rm_piecewise_uniform": lambda: I.rm(n_r=9, n_theta=6),
+}
+
+
+def _dev(a, dtype):
+    return torch.as_tensor(a, dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_fp64_adjoint_step_equals_oracle_vjp(name):
+    w = SMALL[name]()
+    f = _state(w) if name != "rm_piecewise_uniform" else O.set_state(w)
+    lam = np.random.default_rng(9).normal(size=f.shape)
+    want = O.adjoint_step(w, f, lam)
+    with P.PCLB(w, precision="fp64") as g:
+        got = g.adjoint_step(_dev(f, torch.float64), _dev(lam, torch.float64)).cpu().numpy()
+    err = np.max(np.abs(got - want)) / np.max(np.abs(want))
+    assert err <= 1e-12, err
+
+
+@pytest.mark.parametrize("shape,bc", [((40, 20), (I.BC_EXTRAP, I.BC_EXTRAP)),
+                                      ((67, 13), (I.BC_DIRICHLET, I.BC_WALL)),
+                                      ((33, 9), (I.BC_WALL, I.BC_DIRICHLET))])
+def test_fp64_adjoint_transpose_identity_on_multi_tile_grids(shape, bc):
+    w = I.random_smooth(*shape, seed=11, bc_kind=bc)
+    f = _state(w)
+    rng = np.random.default_rng(12)
+    lam = rng.normal(size=f.shape)
+    with P.PCLB(w, precision="fp64") as g:
+        adj = g.adjoint_step(_dev(f, torch.float64), _dev(lam, torch.float64)).cpu().numpy()
+    for _ in range(2):
+        df = rng.normal(size=f.shape)
+        lhs = np.sum(lam * O.step_jvp(w, f, df))
+        rhs = np.sum(adj * df)
+        assert rhs == pytest.approx(lhs, rel=1e-11, abs=1e-11 * np.sum(np.abs(lam * df)))
+
+
+@pytest.mark.parametrize("name", ["extrap", "dirichlet_wall", "sector_nf1"])
+def test_fp32_adjoint_step_close_to_oracle(name):
+    w = SMALL[name]()
+    f = _state(w).astype(np.float32).astype(np.float64)
+    lam = np.random.default_rng(9).normal(size=f.shape).astype(np.float32).astype(np.float64)
+    want = O.adjoint_step(w, f, lam)
+    with P.PCLB(w, precision="fp32") as g:
+        got = g.adjoint_step(_dev(f, torch.float32), _dev(lam, torch.float32)).double().cpu().numpy()
+    err = np.max(np.abs(got - want)) / np.max(np.abs(want))
+    assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_adjoint_on_saved_states_equals_packed_form(prec):
+    w = I.random_smooth(37, 19, seed=13)
+    with P.PCLB(w, precision=prec) as g:
+        g.set_state().step(2)
+        st = g.save_state()
+        f = g.get_f()
+        lam = torch.randn((33, 19, 37), dtype=g.dtype, device="cuda")
+        a = g.adjoint_step(f, lam)
+        g.lambda_set(lam).adjoint_state(st)
+        b = g.lambda_get()
+        assert torch.equal(a, b)
+        g.lambda_set(lam).adjoint_state(None)   # the current state is the same one
+        assert torch.equal(g.lambda_get(), a)
+
+
+def test_fp64_field_vjps_are_transposes_of_oracle_jvps():
+    w = I.random_smooth(35, 17, seed=14, bc_kind=(I.BC_DIRICHLET, I.BC_EXTRAP))
+    rng = np.random.default_rng(15)
+    fields = [np.array(x) for x in w.fields()]
+    f = _state(w)
+    with P.PCLB(w, precision="fp64") as g:
+        # moments: <g, J_m df> = <J_m^T g, df>
+        gs = [rng.normal(size=fields[0].shape) for _ in range(4)]
+        g.set_f(_dev(f, torch.float64)).moments_vjp(*gs)
+        lam = g.lambda_get().cpu().numpy()
+        df = rng.normal(size=f.shape)
+        jv = O.fields_jvp(w, f, df)
+        lhs = sum(np.sum(a * b) for a, b in zip(gs, jv))
+        assert np.sum(lam * df) == pytest.approx(lhs, rel=1e-11)
+        # set_state: <lam, J_s dfields> = <J_s^T lam, dfields>
+        lam2 = rng.normal(size=f.shape)
+        g.lambda_set(_dev(lam2, torch.float64))
+        grads = [x.cpu().numpy() for x in g.set_state_vjp(*fields)]
+        dfields = [rng.normal(size=fields[0].shape) for _ in range(4)]
+        jv2 = O.set_state_jvp(w, fields, dfields)
+        rhs = sum(np.sum(a * b) for a, b in zip(grads, dfields))
+        assert rhs == pytest.approx(np.sum(lam2 * jv2), rel=1e-11)

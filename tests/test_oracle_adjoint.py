@@ -78,3 +78,30 @@ def test_adjoint_of_complete_relaxation_conserves_moment_weights():
     lam = np.zeros_like(f)
     lam[9] = 1.0
     assert np.max(np.abs(O.adjoint_step(w, f, lam) - lam)) > 1e-3
+
+
+def test_set_state_jvp_matches_central_differences():
+    w = I.random_smooth(7, 6, seed=12)
+    fields = [np.array(x) for x in w.fields()]
+    rng = np.random.default_rng(5)
+    dfields = [rng.normal(size=x.shape) * 0.1 for x in fields]
+    jv = O.set_state_jvp(w, fields, dfields)
+    eps = 1e-6
+
+    def at(sign):
+        return O.set_state(w, *[x + sign * eps * d for x, d in zip(fields, dfields)])
+
+    fd = (at(1) - at(-1)) / (2 * eps)
+    assert np.max(np.abs(fd - jv)) <= 1e-7 * np.max(np.abs(jv))
+
+
+def test_fields_jvp_matches_central_differences():
+    w = I.random_smooth(7, 6, seed=13)
+    f = O.set_state(w)
+    rng = np.random.default_rng(6)
+    df = rng.normal(size=f.shape) * 0.01
+    jv = O.fields_jvp(w, f, df)
+    eps = 1e-6
+    plus, minus = O.fields(w, f + eps * df), O.fields(w, f - eps * df)
+    for a, b, j in zip(plus, minus, jv):
+        assert np.max(np.abs((a - b) / (2 * eps) - j)) <= 1e-7 * max(np.max(np.abs(j)), 1e-12)
