@@ -10,6 +10,8 @@ Prints ONE JSON line.  Keys beyond the base contract:
   roofline      dominant kernel (the fused step) against measured HBM bandwidth
   cpu_baseline  the FP64 CPU oracle timed on this host on a bounded sample
   fp64          the same workload through the FP64 path (value + roofline)
+  adjoint       the FP32 adjoint step on the same workload, its ratio to the
+                forward step, and one reverse step with recompute
   e2e           the metric through pclb_run_host with page-locked host buffers
   clocks        SM clocks / throttle reasons sampled during the timed region
 
@@ -63,7 +65,8 @@ def _peaks():
 
 def _kernel_hash() -> str:
     h = hashlib.sha256()
-    for rel in ("paper_1302_7104_gb300/csrc/step_kernel.cu", "paper_1302_7104_gb300/csrc/device_common.cuh",
+    for rel in ("paper_1302_7104_gb300/csrc/step_kernel_f32.cu", "paper_1302_7104_gb300/csrc/f32_state.cuh",
+                "paper_1302_7104_gb300/csrc/f32x2.cuh", "paper_1302_7104_gb300/csrc/device_common.cuh",
                 "paper_1302_7104_gb300/csrc/pclb_internal.h"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
@@ -175,7 +178,7 @@ def time_steps(g, steps: int, warmup: int, torch):
     return start.elapsed_time(end) / 1e3
 
 
-def cpu_baseline(wname: str, n_theta: int = 256, steps: int = 2):
+def cpu_baseline(wname: str, n_theta: int = 2048, steps: int = 12):
     """The FP64 oracle as it stands, on a radial band of the workload: the full
     radial resolution with `n_theta` azimuthal nodes, `steps` steps."""
     import oracle as O
@@ -240,8 +243,45 @@ def run_ours(args):
     e2e_secs = time.perf_counter() - t0
     e2e_value = updates * e2e_steps * ws / e2e_secs
     io_bytes = 4 * cells * 4
-    g.close()
     del pinned, outs
+
+    # adjoint step on the same workload (lam <- J(f)^T lam for a saved state),
+    # and one reverse step as the checkpointed backward pass runs it
+    # (recompute one forward step, save the state, one adjoint step)
+    adjoint = None
+    if not args.no_adjoint:
+        g.set_state()
+        state = g.save_state()
+        g.moments_vjp(g_rho=torch.ones((w.n_theta, w.n_r), dtype=torch.float32, device=f"cuda:{local}"))
+        ka = max(3, min(args.steps, 10))
+        for _ in range(2):
+            g.adjoint_state(state)
+        g.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(g.stream)
+        for _ in range(ka):
+            g.adjoint_state(state)
+        e1.record(g.stream)
+        e1.synchronize()
+        t_adj = e0.elapsed_time(e1) / 1e3 / ka
+        e0.record(g.stream)
+        for _ in range(ka):
+            g.step(1)
+            g.save_state(state)
+            g.adjoint_state(state)
+        e1.record(g.stream)
+        e1.synchronize()
+        t_rev = e0.elapsed_time(e1) / 1e3 / ka
+        alg = updates * 12.0   # read f and lam, write lam
+        adjoint = {"ms_per_step": t_adj * 1e3, "value": updates / t_adj, "unit": UNIT,
+                   "ratio_to_forward": t_adj / per_launch,
+                   "reverse_step_ms": t_rev * 1e3, "reverse_ratio_to_forward": t_rev / per_launch,
+                   "roofline": {"bound": "hbm", "achieved": alg / t_adj / 1e9, "peak": hbm, "unit": "GB/s",
+                                "frac": alg / t_adj / 1e9 / hbm, "alg_bytes_per_launch": alg,
+                                "kernel": "pclb::adjoint_kernel<float>"}}
+        del state
+    g.close()
 
     # FP64 step on the same workload
     fp64 = None
@@ -278,6 +318,8 @@ def run_ours(args):
     }
     if fp64 is not None:
         line["fp64"] = fp64
+    if adjoint is not None:
+        line["adjoint"] = adjoint
     if clk is not None:
         line["clocks"] = clk
     if not args.no_cpu_baseline and ws == 1:
@@ -329,6 +371,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="kh", choices=["kh", "rm", "rm_adj", "shock", "rot"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

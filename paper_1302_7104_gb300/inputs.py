@@ -269,10 +269,19 @@ def rm_amplitudes(seed: int = 20130228, n_modes: int = 16, scale: float = 0.01) 
     return np.random.default_rng(seed).uniform(0.0, scale, size=n_modes)
 
 
+def rm_background(R, TH, amp: float):
+    """Smooth, bounded background modulation 1 + amp s(r, theta) used to keep
+    every region of an RM state non-uniform (for finite-difference checks: a
+    limiter sitting exactly on its kink has no derivative)."""
+    return 1.0 + amp * np.sin(3.0 * TH + 1.7 * R) * np.cos(2.3 * R - TH)
+
+
 def rm_adj(n_r: int = 512, n_theta: int = 1024, steps: int = 2000, cfl: float = STABLE_CFL,
            tau: float = 1e-5, a: Optional[np.ndarray] = None, seed: int = 20130228,
-           r_in: float = 1.0, r_out: float = 3.0) -> Workload:
-    """RM with interface r = 2 + sum_k a_k cos(k theta), k = 1..16."""
+           r_in: float = 1.0, r_out: float = 3.0, background: float = 0.0) -> Workload:
+    """RM with interface r = 2 + sum_k a_k cos(k theta), k = 1..16.  A nonzero
+    ``background`` multiplies rho and T by rm_background (pressure changes
+    slightly; used only by gradient checks)."""
     if a is None:
         a = rm_amplitudes(seed)
     R, TH = _mesh(n_r, n_theta, r_in, r_out)
@@ -280,10 +289,15 @@ def rm_adj(n_r: int = 512, n_theta: int = 1024, steps: int = 2000, cfl: float = 
     k = np.arange(1, len(a) + 1, dtype=np.float64)
     r_if = 2.0 + np.tensordot(np.cos(np.multiply.outer(TH, k)), a, axes=([2], [0]))
     rho, u_r, u_th, T, post = _rm_fields(R, TH, r_if, dr)
+    if background:
+        m = rm_background(R, TH, background)
+        rho = rho * m
+        T = T * m
     return Workload("rm_adj", n_r, n_theta, r_in, r_out, tau, dt_from_cfl(cfl, n_r, n_theta, r_in, r_out),
                     steps, rho, u_r, u_th, T, bc_kind=(BC_EXTRAP, BC_DIRICHLET),
                     bc_values=_rm_bc(n_theta, post), smooth=False,
-                    extra={"a": np.asarray(a, dtype=np.float64), "seed": seed, "post_shock": post})
+                    extra={"a": np.asarray(a, dtype=np.float64), "seed": seed, "post_shock": post,
+                           "background": background})
 
 
 def kh(n_r: int = 4096, n_theta: int = 4096, steps: int = 10000, cfl: float = STABLE_CFL,

@@ -30,7 +30,10 @@ SMALL = {
     "wall_extrap": lambda: I.random_smooth(5, 9, seed=5, bc_kind=(I.BC_WALL, I.BC_EXTRAP)),
     "sector_nf1": lambda: I.random_smooth(6, 5, seed=6, n_f=1),
     "smallest": lambda: I.random_smooth(3, 2, seed=7),
-    "rm_piecewise_uniform": lambda: I.rm(n_r=9, n_theta=6),
+    # RM state with its shock and interface, made non-uniform by the noise:
+    # where two neighbours are bitwise equal the switch function sits on its
+    # kink and the two implementations' roundings pick different branches.
+    "rm_noisy": lambda: I.rm(n_r=9, n_theta=6),
 }
 
 
@@ -41,7 +44,7 @@ def _dev(a, dtype):
 @pytest.mark.parametrize("name", list(SMALL))
 def test_fp64_adjoint_step_equals_oracle_vjp(name):
     w = SMALL[name]()
-    f = _state(w) if name != "rm_piecewise_uniform" else O.set_state(w)
+    f = _state(w)
     lam = np.random.default_rng(9).normal(size=f.shape)
     want = O.adjoint_step(w, f, lam)
     with P.PCLB(w, precision="fp64") as g:
