@@ -1,7 +1,7 @@
 """Throughput benchmark of the polar-coordinate FDLB step on GB300.
 
 Default workload: the Kelvin-Helmholtz annulus, N_r x N_theta = 4096 x 4096,
-33 velocities, FP32 with double-precision temperature recovery.  One "step"
+33 velocities, FP32 (float-float moments, temperature and weights).  One "step"
 is one time step of the combined scheme over the whole grid (one fused kernel
 launch).  The distribution (2 x 2.2 GB) is far larger than L2, so no flush is
 needed between steps.
@@ -111,20 +111,31 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # wait for the first sample so that the timed region is covered
+        t_end = time.perf_counter() + 5.0
+        while not self.lines and time.perf_counter() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self, begin: bool):
+        if begin:
+            self.t_begin = time.perf_counter()
+        else:
+            self.t_end = time.perf_counter()
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(0.05)   # let the sample taken at the end of the region arrive
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -132,9 +143,15 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
+        t0 = getattr(self, "t_begin", None)
+        t1 = getattr(self, "t_end", None)
+        lines = self.lines
+        if t0 is not None and t1 is not None:
+            inside = [(t, ln) for t, ln in lines if t0 <= t <= t1 + 0.04]
+            lines = inside
         sm, mx, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
+        for _, ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 7:
                 continue
@@ -150,7 +167,7 @@ class ClockSampler:
             return None
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "interval_ms": 20}
 
 
 def _dist():
@@ -163,18 +180,22 @@ def _dist():
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def time_steps(g, steps: int, warmup: int, torch):
+def time_steps(g, steps: int, warmup: int, torch, clocks=None):
     """Warm up, then time exactly `steps` steps with CUDA events on the
     context's stream.  Returns seconds."""
     g.step(warmup)
     g.sync()
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
+    if clocks is not None:
+        clocks.mark(True)
     start.record(g.stream)
     for _ in range(steps):
         g.step(1)
     end.record(g.stream)
     end.synchronize()
+    if clocks is not None:
+        clocks.mark(False)
     return start.elapsed_time(end) / 1e3
 
 
@@ -218,7 +239,7 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    secs = time_steps(g, args.steps, args.warmup, torch)
+    secs = time_steps(g, args.steps, args.warmup, torch, clocks)
     clk = clocks.stop()
     flags = g.status_flags()
     if ws > 1:
@@ -307,10 +328,10 @@ def run_ours(args):
                    "n_theta": w.n_theta, "velocities": Q, "cells": cells, "tau": w.tau, "dt": w.dt,
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2": "state 2 x %.2f GB > 129 MB L2, no flush needed" % (updates * 4 / 1e9),
-                   "T_recovery": "fp64"},
+                   "T_recovery": "float-float"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src,
-                     "kernel": "pclb::step_kernel<float>", "alg_bytes_per_launch": alg_bytes},
+                     "kernel": "pclb::step_kernel_f32", "alg_bytes_per_launch": alg_bytes},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
                 "d2h_bytes_per_step": io_bytes, "steps": e2e_steps},
         "gpu_launches": args.steps,

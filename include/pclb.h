@@ -40,11 +40,14 @@
  *    been queued unless stated, and pclb_last_error() describes the cause.
  *    No C++ exception crosses this interface.
  *
- * Precision: PCLB_FP32 stores f in float and computes the step in float,
- * except that the velocity moments are summed with a compensated (two-sum)
- * accumulation across shells and the temperature recovery
- * T = (e - |j|^2 / (2 rho)) / rho is done in double.  PCLB_FP64 computes
- * everything in double.
+ * Precision: PCLB_FP32 stores f in float and computes the step in float.
+ * The parts whose rounding would otherwise dominate are carried in
+ * float-float (a pair of floats, ~44 significant bits): the velocity moments
+ * are accumulated across shells with two-sum / two-product corrections, the
+ * temperature recovery T = (e - |j|^2 / (2 rho)) / rho and the weights F_k(T)
+ * of Eq. (11) are evaluated in float-float, and so is x = v.u / T with
+ * float-float velocity constants.  The adjoint step (PCLB_FP32) recovers the
+ * moments in double.  PCLB_FP64 computes everything in double.
  */
 #ifndef PCLB_H
 #define PCLB_H

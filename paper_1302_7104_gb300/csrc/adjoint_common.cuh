@@ -8,25 +8,51 @@
 
 namespace pclb {
 
+// sign(x) in {-1, 0, 1}
 template <class T>
-__device__ __forceinline__ T sgn(T x) { return T((x > T(0)) - (x < T(0))); }
+__device__ __forceinline__ T sgn(T x) { return copysign(x != T(0) ? T(1) : T(0), x); }
 
-// Partial derivatives of M = a D + K h(D, Dp) with respect to D and Dp.
+// 1/x for the partials below: the hardware approximation in FP32 (relative
+// error ~1 ulp), the correctly rounded quotient in FP64.
+__device__ __forceinline__ float recip_fast(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double recip_fast(double x) { return 1.0 / x; }
+
+template <class T>
+__device__ __forceinline__ T smallest_normal();
+template <>
+__device__ __forceinline__ float smallest_normal<float>() { return 1.17549435e-38f; }
+template <>
+__device__ __forceinline__ double smallest_normal<double>() { return 2.2250738585072014e-308; }
+
+// Partial derivatives of M = a D + K h(D, Dp), h = |D|(D - Dp)/(|D| + |Dp|),
+// with respect to D and Dp.  With n = |D| + |Dp|, a' = |D|/n, b' = |Dp|/n and
+// s = sign(D) sign(Dp):
+//   h_D = a'(1 + b') - s b'^2,   h_Dp = -(1 + s) a'^2,
+// both 0 when n = 0 (sign(0) = 0: the derivative on the active branch).  The
+// pair is unchanged when D and Dp change sign together.
 template <class T>
 __device__ __forceinline__ void mwb_partials(T a, T K, T D, T Dp, T& MD, T& MDp) {
   const T aD = abs(D), aP = abs(Dp), n = aD + aP;
-  T hD = T(0), hP = T(0);
-  if (n > T(0)) {
-    const T inv2 = T(1) / (n * n);
-    hD = (sgn(D) * (D - Dp) * aP + aD * n) * inv2;
-    hP = -aD * (aD + D * sgn(Dp)) * inv2;
-  }
+  const T rn = n >= smallest_normal<T>() ? recip_fast(n) : T(0);
+  const T ar = aD * rn, br = aP * rn;
+  const T s = sgn(D) * sgn(Dp);
+  const T hD = ar * (T(1) + br) - s * br * br;
+  const T hP = -(T(1) + s) * ar * ar;
   MD = a + K * hD;
   MDp = K * hP;
 }
 
 // G = sum_q lam(q) d f^eq_q / d(rho, u_x, u_y, E) at the given state (Eq. 10,
-// weights Eq. 11).
+// weights Eq. 11).  With P(x) the polynomial of Eq. (10), P_x, P_s its
+// derivatives in x = v.u/E and s = u^2/E:
+//   G_rho = sum lam F P,  G_u = rho sum lam F (P_x v + 2 P_s u) / E,
+//   G_E = rho sum lam (F' P - F (x P_x + s P_s) / E).
+// Opposite velocities of a shell (x and -x) share the even and odd parts of
+// P, P_x and P_s.
 template <class T, class LamFn>
 __device__ __forceinline__ void eq_cotangent(T rho, T ux, T uy, T E, const DvmConst<T>& d, LamFn lam,
                                              T G[4]) {
@@ -46,28 +72,41 @@ __device__ __forceinline__ void eq_cotangent(T rho, T ux, T uy, T E, const DvmCo
   const T s = (ux * ux + uy * uy) * invE;
   const T a1 = T(1) - T(0.5) * s;
   const T a0 = a1 + T(0.125) * s * s;
-  T A = 0, Bx = 0, By = 0, Cs = 0, Dx = 0, Fq = 0;
+  const T uxE = ux * invE, uyE = uy * invE;
+  // rest velocity: x = 0
+  const T l0 = lam(0);
+  T A = l0 * F[0] * a0, Bx = 0, By = 0, Cs = l0 * F[0] * (T(-0.5) + T(0.25) * s), Dx = 0;
+  T Fq = l0 * Fd[0] * a0;
+  constexpr int half = kNDirs / 2;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const int qb = k == 0 ? 0 : 1 + (k - 1) * kNDirs;
-    const int qe = k == 0 ? 1 : qb + kNDirs;
-#pragma unroll 1
-    for (int q = qb; q < qe; ++q) {
+  for (int k = 1; k <= 4; ++k) {
+    T Ak = 0, Bxk = 0, Byk = 0, Ck = 0, Dk = 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const int q = 1 + (k - 1) * kNDirs + i;
       const T vx = d.vx[q], vy = d.vy[q];
-      const T x = (vx * ux + vy * uy) * invE;
+      const T x = vx * uxE + vy * uyE;
       const T x2 = x * x;
-      const T P = a0 + x * (a1 + x * (T(0.5) * a1 + x * (T(1.0 / 6.0) + x * T(1.0 / 24.0))));
-      const T Px = a1 * (T(1) + x) + x2 * (T(0.5) + x * T(1.0 / 6.0));
-      const T Ps = T(-0.5) + T(0.25) * s - T(0.5) * x - T(0.25) * x2;
-      const T l = lam(q);
-      const T lF = l * F[k];
-      A += lF * P;
-      Bx += lF * Px * vx;
-      By += lF * Px * vy;
-      Cs += lF * Ps;
-      Dx += lF * x * Px;
-      Fq += l * Fd[k] * P;
+      const T Pe = a0 + x2 * (T(0.5) * a1 + x2 * T(1.0 / 24.0));   // P(+-x) = Pe +- Po
+      const T Po = x * (a1 + x2 * T(1.0 / 6.0));
+      const T Xe = a1 + x2 * T(0.5);                                // P_x(+-x) = Xe +- Xo
+      const T Xo = x * (a1 + x2 * T(1.0 / 6.0));
+      const T Se = T(-0.5) + T(0.25) * s - T(0.25) * x2;           // P_s(+-x) = Se -+ x/2
+      const T lp = lam(q), lm = lam(q + half);
+      const T ls = lp + lm, ld = lp - lm;
+      Ak += ls * Pe + ld * Po;
+      const T lpx = ld * Xe + ls * Xo;        // lp Px(x) - lm Px(-x)
+      Bxk += lpx * vx;
+      Byk += lpx * vy;
+      Ck += ls * Se - ld * T(0.5) * x;
+      Dk += x * (ls * Xo + ld * Xe);          // lp x Px(x) + lm (-x) Px(-x)
     }
+    A += F[k] * Ak;
+    Bx += F[k] * Bxk;
+    By += F[k] * Byk;
+    Cs += F[k] * Ck;
+    Dx += F[k] * Dk;
+    Fq += Fd[k] * Ak;
   }
   G[0] = A;
   G[1] = rho * (Bx + T(2) * ux * Cs) * invE;

@@ -24,7 +24,7 @@ __device__ __forceinline__ void store_ghosted(T* f, const StepParams& p, const D
 
 template <class T>
 __global__ void moments_vjp_kernel(const T* __restrict__ f, const T* g_rho, const T* g_ur, const T* g_ut,
-                                   const T* g_T, T* __restrict__ lam, const StepParams p, const DvmConst<T> d) {
+                                   const T* g_T, T* __restrict__ lam, const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
   if (r >= p.n_r || t >= p.n_theta) return;
@@ -49,7 +49,7 @@ template <class T>
 __global__ void set_state_vjp_kernel(const T* __restrict__ rho, const T* __restrict__ u_r,
                                      const T* __restrict__ u_t, const T* __restrict__ temp,
                                      const T* __restrict__ lam, T* g_rho, T* g_ur, T* g_ut, T* g_T,
-                                     const StepParams p, const DvmConst<T> d) {
+                                     const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
   if (r >= p.n_r || t >= p.n_theta) return;

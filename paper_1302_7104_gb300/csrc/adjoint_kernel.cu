@@ -41,10 +41,24 @@ struct AdjTile<double> {
   static constexpr int TT = kAdjRows64;
 };
 
+// Courant entry of one pair of opposite velocities at one theta row:
+// (|C_r|, |C_r|(1 - |C_r|), |v_theta| dt / dtheta, flags) with flag bit 0 set
+// when v_r < 0 and bit 1 when v_theta < 0 for the first label of the pair.
+template <class T>
+struct alignas(4 * sizeof(T)) CourEntry {
+  T a_r, k_r, a_w;
+  int fl;
+};
+
 template <class T>
 struct AdjSize {
-  static constexpr int plane = kWinR * (AdjTile<T>::TT + 4);
-  static constexpr int smem = 2 * kQ * plane * (int)sizeof(T) + 2 * 2 * AdjTile<T>::TT * 4 * (int)sizeof(T) + 128;
+  static constexpr int TT = AdjTile<T>::TT;
+  static constexpr int plane = kWinR * (TT + 4);
+  static constexpr int npairs = 4 * kNDirs / 2;
+  static constexpr int win_bytes = 2 * kQ * plane * (int)sizeof(T);
+  static constexpr int gw_bytes = 2 * 2 * TT * 4 * (int)sizeof(T);
+  static constexpr int tab_bytes = (TT + 4) * npairs * (int)sizeof(CourEntry<T>);
+  static constexpr int smem = win_bytes + gw_bytes + tab_bytes + 128;
 };
 
 namespace {
@@ -90,19 +104,70 @@ __device__ __forceinline__ Cour<T> courant(const StepParams& p, const DvmConst<T
   return c;
 }
 
+// Sum over the nodes n whose MWB increments (Eq. 28) in r and theta read
+// f_q(c) of lam_q(n) dM_q(n)/df_q(c), for one label at this node c.  f and l
+// point at c in the label's f and lam windows; ur is the radial upwind offset
+// (+-1 column); at[o], kt[o] are a = |C_theta| and K = a(1 - a) of the theta
+// rows o - 2 (o = 0..4) at this radius, and bit o of vt_neg is set when row
+// o - 2 takes its upwind neighbour at the next row (v_theta < 0).  The node
+// n = c + j u_n reads f(n), f(n + u_n), f(n + 2 u_n) with D = f(n) - f(n + u_n),
+// Dp = f(n + u_n) - f(n + 2 u_n), so
+//   dM(n)/df(n) = M_D,  dM(n)/df(n + u_n) = M_Dp - M_D,  dM(n)/df(n + 2 u_n) = -M_Dp.
+template <class T>
+__device__ __forceinline__ T adjoint_stencil(const T* f, const T* l, int ur, T ar, T kr, const T* at, const T* kt,
+                                             int vt_neg) {
+  const T f0 = f[0];
+  // radial: the nodes c, c - u, c - 2u
+  const T fm2 = f[-2 * ur], fm1 = f[-ur], fp1 = f[ur], fp2 = f[2 * ur];
+  const T dm2 = fm2 - fm1, dm1 = fm1 - f0, d0 = f0 - fp1, d1 = fp1 - fp2;
+  T MD0, MP0, MD1, MP1, MD2, MP2;
+  mwb_partials<T>(ar, kr, d0, d1, MD0, MP0);
+  mwb_partials<T>(ar, kr, dm1, d0, MD1, MP1);
+  mwb_partials<T>(ar, kr, dm2, dm1, MD2, MP2);
+  T acc = l[0] * MD0 + l[-ur] * (MP1 - MD1) - l[-2 * ur] * MP2;
+  // azimuthal: rows -2..2 of this column, e_j = f(row j) - f(row j + 1)
+  constexpr int S = kWinR;
+  const T gm2 = f[-2 * S], gm1 = f[-S], gp1 = f[S], gp2 = f[2 * S];
+  const T em2 = gm2 - gm1, em1 = gm1 - f0, e0 = f0 - gp1, e1 = gp1 - gp2;
+  T MD, MP;
+  if (vt_neg & 4)
+    mwb_partials<T>(at[2], kt[2], e0, e1, MD, MP);     // this node, upwind at row +1
+  else
+    mwb_partials<T>(at[2], kt[2], em1, em2, MD, MP);   // upwind at row -1 (signs flipped)
+  acc += l[0] * MD;
+  if (vt_neg & 2) {          // row -1 reads this node as its first upwind neighbour
+    mwb_partials<T>(at[1], kt[1], em1, e0, MD, MP);
+    acc += l[-S] * (MP - MD);
+  }
+  if (!(vt_neg & 8)) {       // row +1, likewise
+    mwb_partials<T>(at[3], kt[3], e0, em1, MD, MP);
+    acc += l[S] * (MP - MD);
+  }
+  if (vt_neg & 1) {          // row -2 reads this node as its second upwind neighbour
+    mwb_partials<T>(at[0], kt[0], em2, em1, MD, MP);
+    acc -= l[-2 * S] * MP;
+  }
+  if (!(vt_neg & 16)) {      // row +2, likewise
+    mwb_partials<T>(at[4], kt[4], e1, e0, MD, MP);
+    acc -= l[2 * S] * MP;
+  }
+  return acc;
+}
+
 }  // namespace
 
 template <class T>
 __global__ void __launch_bounds__(AdjTile<T>::TT * 32, 1)
     adjoint_kernel(const __grid_constant__ CUtensorMap tmap_f, const __grid_constant__ CUtensorMap tmap_l,
-                   T* __restrict__ lam_out, const StepParams p, const DvmConst<T> d) {
+                   T* __restrict__ lam_out, const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
   constexpr int TT = AdjTile<T>::TT;
   constexpr int PLANE = AdjSize<T>::plane;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* sf = reinterpret_cast<T*>(smem_raw);
   T* sl = sf + kQ * PLANE;
   T* gw = sl + kQ * PLANE;                          // [side][node][TT][4]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(gw + 2 * 2 * TT * 4);
+  CourEntry<T>* ctab = reinterpret_cast<CourEntry<T>*>(gw + 2 * 2 * TT * 4);   // [TT + 4][npairs]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ctab + (TT + 4) * AdjSize<T>::npairs);
 
   const int r0 = blockIdx.x * kTileR;
   const int t0 = blockIdx.y * TT;
@@ -116,6 +181,13 @@ __global__ void __launch_bounds__(AdjTile<T>::TT * 32, 1)
     mbar_fence_init();
   }
   for (int i = tid; i < 2 * 2 * TT * 4; i += blockDim.x) gw[i] = T(0);
+  // Courant entries of the stored rows t0 .. t0 + TT + 3 (theta rows t0 - 2 .. t0 + TT + 1)
+  for (int i = tid; i < (TT + 4) * AdjSize<T>::npairs; i += blockDim.x) {
+    const int srow = t0 + i / AdjSize<T>::npairs, pair = i % AdjSize<T>::npairs;
+    CourEntry<T> e{T(0), T(0), T(0), 0};
+    if (srow < p.rows) courant_entry(p, srow, pair, e.a_r, e.k_r, e.a_w, e.fl);
+    ctab[i] = e;
+  }
   __syncthreads();
   if (tid == 0) {
     mbar_arrive_expect_tx(bar, (uint32_t)(2 * kQ * PLANE * sizeof(T)));
@@ -226,74 +298,61 @@ __global__ void __launch_bounds__(AdjTile<T>::TT * 32, 1)
     to_moment_cotangent<T>(m.rho, m.ux, m.uy, m.E, G, g);
   }
   __syncthreads();   // wall feedback ready
-  T gwl[4] = {T(0), T(0), T(0), T(0)};
-  if (valid) {
-    for (int j = 0; j < 4; ++j) {
-      if (inner && r == 0) gwl[j] += gw[((0 * 2 + 0) * TT + rowl) * 4 + j];
-      if (inner && r == 1) gwl[j] += gw[((0 * 2 + 1) * TT + rowl) * 4 + j];
-      if (outer && r == p.n_r - 1) gwl[j] += gw[((1 * 2 + 0) * TT + rowl) * 4 + j];
-      if (outer && r == p.n_r - 2) gwl[j] += gw[((1 * 2 + 1) * TT + rowl) * 4 + j];
-    }
-  }
   if (!valid) return;
-
+  // gs = (1 - d) g + g_wall: every label receives psi_q . gs
   const T decay = (T)p.decay;
+  T gs[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    T w = T(0);
+    if (inner && r == 0) w += gw[((0 * 2 + 0) * TT + rowl) * 4 + j];
+    if (inner && r == 1) w += gw[((0 * 2 + 1) * TT + rowl) * 4 + j];
+    if (outer && r == p.n_r - 1) w += gw[((1 * 2 + 0) * TT + rowl) * 4 + j];
+    if (outer && r == p.n_r - 2) w += gw[((1 * 2 + 1) * TT + rowl) * 4 + j];
+    gs[j] = (T(1) - decay) * g[j] + w;
+  }
+
   const T inv_r = (T)p.inv_r[r];
   const size_t plane_out = (size_t)p.rows * p.pitch;
-#pragma unroll 1
-  for (int q = 0; q < kQ; ++q) {
-    const T* fp = sf + q * PLANE;
-    const T* lp = sl + q * PLANE;
-    const int k = d.shell[q];
-    const T vx = d.vx[q], vy = d.vy[q], hq = d.half_v2[k];
-    const T psi_g = g[0] + g[1] * vx + g[2] * vy + g[3] * hq;
-    const T psi_w = gwl[0] + gwl[1] * vx + gwl[2] * vy + gwl[3] * hq;
-    T out = decay * lp[row * kWinR + col] + (T(1) - decay) * psi_g + psi_w;
-    if (q != 0) {
-      // radial gather: nodes n = c, c - u, c - 2u of this row (same Courant numbers)
-      const Cour<T> cr = courant<T>(p, d, q, srow);
-      const int u = cr.up_r;
-      const T* fr = fp + row * kWinR;
-      const T* lr = lp + row * kWinR;
-      T MD0, MP0, MD1, MP1, MD2, MP2;
-      mwb_partials<T>(cr.a_r, cr.k_r, fr[col] - fr[col + u], fr[col + u] - fr[col + 2 * u], MD0, MP0);
-      mwb_partials<T>(cr.a_r, cr.k_r, fr[col - u] - fr[col], fr[col] - fr[col + u], MD1, MP1);
-      mwb_partials<T>(cr.a_r, cr.k_r, fr[col - 2 * u] - fr[col - u], fr[col - u] - fr[col], MD2, MP2);
-      out -= lr[col] * MD0 + lr[col - u] * (MP1 - MD1) - lr[col - 2 * u] * MP2;
-      // azimuthal gather: each neighbour row n has its own upwind side
-      const T* fc = fp + col;
-      const T* lc = lp + col;
-      {
-        const int un = cr.up_t;
-        const T at = cr.a_w * inv_r, kt = at - at * at;
-        T MD, MP;
-        mwb_partials<T>(at, kt, fc[row * kWinR] - fc[(row + un) * kWinR],
-                        fc[(row + un) * kWinR] - fc[(row + 2 * un) * kWinR], MD, MP);
-        out -= lc[row * kWinR] * MD;
-      }
-#pragma unroll
-      for (int o = -2; o <= 2; ++o) {
-        if (o == 0) continue;
-        const int n = row + o;
-        const Cour<T> cn = courant<T>(p, d, q, srow + o);
-        const int un = cn.up_t;
-        // this node is the first (o = -un) or second (o = -2 un) upwind neighbour of n
-        if (o != -un && o != -2 * un) continue;
-        const T at = cn.a_w * inv_r, kt = at - at * at;
-        T MD, MP;
-        mwb_partials<T>(at, kt, fc[n * kWinR] - fc[(n + un) * kWinR],
-                        fc[(n + un) * kWinR] - fc[(n + 2 * un) * kWinR], MD, MP);
-        if (o == -un)
-          out -= lc[n * kWinR] * (MP - MD);
-        else
-          out += lc[n * kWinR] * MP;
-      }
-    }
-    T* dst = lam_out + (size_t)q * plane_out + r;
-    dst[(size_t)srow * p.pitch] = out;
+  const int win = row * kWinR + col;
+  auto store = [&](int q, T v) {
+    lam_out[(size_t)q * plane_out + (size_t)srow * p.pitch + r] = v;
     if (t >= p.n_theta - 2)
-      lam_out[(size_t)d.recv_lo[q] * plane_out + (size_t)(t - (p.n_theta - 2)) * p.pitch + r] = out;
-    if (t < 2) lam_out[(size_t)d.recv_hi[q] * plane_out + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r] = out;
+      lam_out[(size_t)d.recv_lo[q] * plane_out + (size_t)(t - (p.n_theta - 2)) * p.pitch + r] = v;
+    if (t < 2) lam_out[(size_t)d.recv_hi[q] * plane_out + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r] = v;
+  };
+  // rest velocity: no convection
+  store(0, decay * sl[win] + gs[0] + gs[3] * d.half_v2[0]);
+
+  const CourEntry<T>* crow = ctab + rowl * AdjSize<T>::npairs;   // stored row srow - 2
+#pragma unroll 1
+  for (int pair = 0; pair < AdjSize<T>::npairs; ++pair) {
+    const int k = 1 + pair / (kNDirs / 2);
+    const int q = 1 + (k - 1) * kNDirs + pair % (kNDirs / 2);
+    const int q2 = q + kNDirs / 2;                       // opposite velocity
+    // theta Courant numbers of the five rows o = -2..2 at this radius; flag
+    // bits of the first label (the second has the opposite signs)
+    T at[5], kt[5];
+    int vt_neg = 0;
+#pragma unroll
+    for (int o = 0; o < 5; ++o) {
+      const CourEntry<T> e = crow[o * AdjSize<T>::npairs + pair];
+      at[o] = e.a_w * inv_r;
+      kt[o] = at[o] - at[o] * at[o];
+      vt_neg |= ((e.fl >> 1) & 1) << o;
+    }
+    const CourEntry<T> e0 = crow[2 * AdjSize<T>::npairs + pair];
+    const int ur = (e0.fl & 1) ? 1 : -1;          // radial upwind offset of the first label
+    const T A = gs[0] + gs[3] * d.half_v2[k];
+    const T B = gs[1] * d.vx[q] + gs[2] * d.vy[q];
+    const T* f1 = sf + q * PLANE + win;
+    const T* l1 = sl + q * PLANE + win;
+    const T* f2 = sf + q2 * PLANE + win;
+    const T* l2 = sl + q2 * PLANE + win;
+    const T c1 = adjoint_stencil<T>(f1, l1, ur, e0.a_r, e0.k_r, at, kt, vt_neg);
+    const T c2 = adjoint_stencil<T>(f2, l2, -ur, e0.a_r, e0.k_r, at, kt, vt_neg ^ 0x1f);
+    store(q, decay * l1[0] + A + B - c1);
+    store(q2, decay * l2[0] + A - B - c2);
   }
 }
 

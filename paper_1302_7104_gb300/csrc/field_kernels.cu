@@ -26,7 +26,7 @@ __device__ __forceinline__ void store_with_ghosts(T* f, const StepParams& p, con
 template <class T>
 __global__ void set_state_kernel(T* __restrict__ f, const T* __restrict__ rho, const T* __restrict__ u_r,
                                  const T* __restrict__ u_t, const T* __restrict__ temp,
-                                 const StepParams p, const DvmConst<T> d) {
+                                 const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
   if (r >= p.n_r || t >= p.n_theta) return;
@@ -49,8 +49,8 @@ __global__ void set_state_kernel(T* __restrict__ f, const T* __restrict__ rho, c
 // FP32 path: the same float-float node state and equilibrium as the step.
 __global__ void set_state_f32_kernel(float* __restrict__ f, const float* __restrict__ rho,
                                      const float* __restrict__ u_r, const float* __restrict__ u_t,
-                                     const float* __restrict__ temp, const StepParams p,
-                                     const DvmConst<float> d) {
+                                     const float* __restrict__ temp, const __grid_constant__ StepParams p,
+                                     const __grid_constant__ DvmConst<float> d) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
   if (r >= p.n_r || t >= p.n_theta) return;
@@ -76,7 +76,7 @@ __global__ void set_state_f32_kernel(float* __restrict__ f, const float* __restr
 }
 
 __global__ void moments_f32_kernel(const float* __restrict__ f, float* rho, float* u_r, float* u_t,
-                                   float* temp, const StepParams p, const DvmConst<float> d) {
+                                   float* temp, const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<float> d) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
   if (r >= p.n_r || t >= p.n_theta) return;
@@ -93,7 +93,7 @@ __global__ void moments_f32_kernel(const float* __restrict__ f, float* rho, floa
 
 template <class T>
 __global__ void moments_kernel(const T* __restrict__ f, T* rho, T* u_r, T* u_t, T* temp,
-                               const StepParams p, const DvmConst<T> d) {
+                               const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
   if (r >= p.n_r || t >= p.n_theta) return;
@@ -108,7 +108,7 @@ __global__ void moments_kernel(const T* __restrict__ f, T* rho, T* u_r, T* u_t, 
 }
 
 template <class T>
-__global__ void pack_kernel(const T* __restrict__ f, T* __restrict__ out, const StepParams p) {
+__global__ void pack_kernel(const T* __restrict__ f, T* __restrict__ out, const __grid_constant__ StepParams p) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y, q = blockIdx.z;
   if (r >= p.n_r) return;
@@ -117,8 +117,8 @@ __global__ void pack_kernel(const T* __restrict__ f, T* __restrict__ out, const 
 }
 
 template <class T>
-__global__ void unpack_kernel(const T* __restrict__ in, T* __restrict__ f, const StepParams p,
-                              const DvmConst<T> d) {
+__global__ void unpack_kernel(const T* __restrict__ in, T* __restrict__ f, const __grid_constant__ StepParams p,
+                              const __grid_constant__ DvmConst<T> d) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y, q = blockIdx.z;
   if (r >= p.n_r) return;
@@ -128,8 +128,8 @@ __global__ void unpack_kernel(const T* __restrict__ in, T* __restrict__ f, const
 // Global integrals with weight r dr dtheta, in double.  Each block reduces a
 // fixed grid-stride subset in a fixed order, so results are reproducible.
 template <class T>
-__global__ void diag_partial_kernel(const T* __restrict__ f, double* partials, const StepParams p,
-                                    const DvmConst<T> d, double dr, double dth, double r_in) {
+__global__ void diag_partial_kernel(const T* __restrict__ f, double* partials, const __grid_constant__ StepParams p,
+                                    const __grid_constant__ DvmConst<T> d, double dr, double dth, double r_in) {
   const size_t plane = (size_t)p.rows * p.pitch;
   const size_t n_nodes = (size_t)p.n_r * p.n_theta;
   double acc[4] = {0, 0, 0, 0};

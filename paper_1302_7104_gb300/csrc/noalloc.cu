@@ -34,7 +34,7 @@ static __device__ __align__(256) double g_noalloc_scratch[(kNoAllocMaxRows + 1) 
 // One block per azimuthal row of the packed [Q][n_theta][n_r] array.
 template <class T>
 __global__ void diag_rows_kernel(const T* __restrict__ f, double* __restrict__ partials, int n_r,
-                                 int n_theta, const DvmConst<T> d, double dr, double dth, double r_in) {
+                                 int n_theta, const __grid_constant__ DvmConst<T> d, double dr, double dth, double r_in) {
   const int t = blockIdx.x;
   const size_t plane = (size_t)n_theta * n_r;
   double acc[4] = {0, 0, 0, 0};

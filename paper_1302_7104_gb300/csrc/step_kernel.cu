@@ -36,7 +36,7 @@ constexpr int step_smem_bytes() {
 template <class T>
 __global__ void __launch_bounds__(kStepThreads, (sizeof(T) == 4 ? 2 : 1))
     step_kernel(const __grid_constant__ CUtensorMap tmap_in, T* __restrict__ f_out,
-                const StepParams p, const DvmConst<T> d) {
+                const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + kQ * kPlane * sizeof(T));

@@ -226,7 +226,7 @@ __device__ __forceinline__ f2 mwb2(f2 a, f2 K, f2 D, f2 Dp) {
 
 __global__ void __launch_bounds__(kStepThreads, 2)
     step_kernel_f32(const __grid_constant__ CUtensorMap tmap_in, float* __restrict__ f_out,
-                    const StepParams p, const DvmConst<float> d) {
+                    const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<float> d) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
   float4* tab = reinterpret_cast<float4*>(smem_raw + kPlanesBytes);
