@@ -37,6 +37,12 @@ METRIC = "cell·velocity updates/s + %HBM roofline: FP32 vs FP64 step; adjoint/f
 UNIT = "cell·velocity updates/s"
 Q = 33
 FALLBACK_HBM_GBS = 6800.0
+# FP64 step: algorithmic flops per cell-velocity update (equilibrium 13,
+# relaxation 3, MWB in r 8 and theta 11, combination 2, per-node moments,
+# temperature and weights 9 amortised over the 33 velocities)
+FP64_FLOPS_PER_UPDATE = 46.0
+# 152 SMs x 2 FP64 FMA lanes per SM per clock x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 # ---------------------------------------------------------------------------
@@ -63,11 +69,19 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def _kernel_hash() -> str:
+_KERNEL_SOURCES = {
+    "fp32": ("paper_1302_7104_gb300/csrc/step_kernel_f32.cu", "paper_1302_7104_gb300/csrc/f32_state.cuh",
+             "paper_1302_7104_gb300/csrc/f32x2.cuh", "paper_1302_7104_gb300/csrc/device_common.cuh",
+             "paper_1302_7104_gb300/csrc/pclb_internal.h"),
+    "fp64": ("paper_1302_7104_gb300/csrc/step_kernel.cu", "paper_1302_7104_gb300/csrc/ghost_cols.cuh",
+             "paper_1302_7104_gb300/csrc/device_common.cuh", "paper_1302_7104_gb300/csrc/pclb_internal.h"),
+}
+
+
+def _kernel_hash(tag: str = "fp32") -> str:
+    """Hash of the sources of the FP32 ("fp32") or FP64 ("fp64") step kernel."""
     h = hashlib.sha256()
-    for rel in ("paper_1302_7104_gb300/csrc/step_kernel_f32.cu", "paper_1302_7104_gb300/csrc/f32_state.cuh",
-                "paper_1302_7104_gb300/csrc/f32x2.cuh", "paper_1302_7104_gb300/csrc/device_common.cuh",
-                "paper_1302_7104_gb300/csrc/pclb_internal.h"):
+    for rel in _KERNEL_SOURCES[tag]:
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -86,7 +100,7 @@ def _profiled_traffic(kernel_tag: str, cells: int):
             continue
         k, v = line.split(":", 1)
         rec[k.strip()] = v.strip()
-    if rec.get("source_hash") != _kernel_hash():
+    if rec.get(f"{kernel_tag}_source_hash") != _kernel_hash(kernel_tag):
         return None
     key = f"{kernel_tag}_bytes_per_cell"
     if key not in rec:
@@ -170,6 +184,25 @@ class ClockSampler:
                 "samples": len(sm), "interval_ms": 20}
 
 
+def max_over_ranks(secs: float, device=None) -> float:
+    """The job's time: the longest of the ranks' timed regions (one value per
+    rank, all-reduced with MAX when a process group is up)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return secs
+    t = torch.tensor([secs], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(updates_per_step: int, steps: int, world_size: int, secs: float) -> float:
+    """Whole-job rate of `world_size` independent replicas, each doing
+    `steps` steps of `updates_per_step` updates in at most `secs` (weak
+    scaling: the work per GPU is fixed)."""
+    return updates_per_step * steps * world_size / secs
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -242,11 +275,8 @@ def run_ours(args):
     secs = time_steps(g, args.steps, args.warmup, torch, clocks)
     clk = clocks.stop()
     flags = g.status_flags()
-    if ws > 1:
-        t = torch.tensor([secs], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        secs = float(t.item())
-    value = updates * args.steps * ws / secs
+    secs = max_over_ranks(secs, device=f"cuda:{local}")
+    value = job_throughput(updates, args.steps, ws, secs)
     per_launch = secs / args.steps
     alg_bytes = updates * 8.0
     achieved = alg_bytes / per_launch / 1e9
@@ -313,10 +343,15 @@ def run_ours(args):
         k64 = max(3, min(args.steps, 10))
         s64 = time_steps(g64, k64, 2, torch)
         g64.close()
-        fp64 = {"value": updates * k64 / s64, "unit": UNIT, "steps": k64, "ms_per_step": s64 / k64 * 1e3,
-                "roofline": {"bound": "hbm", "achieved": updates * 16.0 / (s64 / k64) / 1e9, "peak": hbm,
-                             "unit": "GB/s", "frac": updates * 16.0 / (s64 / k64) / 1e9 / hbm,
-                             "traffic": _profiled_traffic("fp64", cells)}}
+        t64 = s64 / k64
+        tflops = updates * FP64_FLOPS_PER_UPDATE / t64 / 1e12
+        fp64 = {"value": updates * k64 / s64, "unit": UNIT, "steps": k64, "ms_per_step": t64 * 1e3,
+                "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": tflops / FP64_PEAK_TFLOPS, "flops_per_update": FP64_FLOPS_PER_UPDATE,
+                             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                             "hbm_frac": updates * 16.0 / t64 / 1e9 / hbm,
+                             "traffic": _profiled_traffic("fp64", cells),
+                             "kernel": "pclb::step_kernel<double>"}}
 
     if rank != 0:
         return 0

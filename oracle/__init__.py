@@ -68,7 +68,8 @@ def lib():
             L.orc_mwb_increment.restype = ctypes.c_double
             L.orc_mwb_increment.argtypes = [ctypes.c_double] * 6
             for name in ("orc_step", "orc_run", "orc_set_state", "orc_fields", "orc_diagnostics",
-                         "orc_step_jvp", "orc_adjoint_step", "orc_set_state_jvp", "orc_fields_jvp"):
+                         "orc_step_jvp", "orc_adjoint_step", "orc_set_state_jvp", "orc_fields_jvp",
+                         "orc_step_nodes", "orc_adjoint_entries"):
                 getattr(L, name).restype = ctypes.c_int
         return _lib
 
@@ -243,4 +244,35 @@ def adjoint_step(w, f_n, lam_np1, prob=None):
     lam = np.ascontiguousarray(lam_np1, dtype=np.float64)
     out = np.empty_like(f_n)
     _check(lib().orc_adjoint_step(prob.ref, _ptr(f_n), _ptr(lam), _ptr(out)), "adjoint_step")
+    return out
+
+
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+
+def step_nodes(w, f, it, ir, prob=None):
+    """f^{n+1} at the nodes (it[j], ir[j]) (0-based), shape [n, Q], from the
+    whole f^n; the same operations as ``step``."""
+    prob = prob or Problem(w)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    it = np.ascontiguousarray(it, dtype=np.int32)
+    ir = np.ascontiguousarray(ir, dtype=np.int32)
+    out = np.zeros((len(it), prob.Q))
+    _check(lib().orc_step_nodes(prob.ref, _ptr(f), ctypes.c_int(len(it)), it.ctypes.data_as(_ip),
+                                ir.ctypes.data_as(_ip), _ptr(out)), "step_nodes")
+    return out
+
+
+def adjoint_entries(w, f_n, lam_np1, q, it, ir, prob=None):
+    """Entries lam^n[q[j], it[j], ir[j]] of the adjoint step (vector-Jacobian
+    product), each by a node-local forward-mode sweep."""
+    prob = prob or Problem(w)
+    f_n = np.ascontiguousarray(f_n, dtype=np.float64)
+    lam = np.ascontiguousarray(lam_np1, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    it = np.ascontiguousarray(it, dtype=np.int32)
+    ir = np.ascontiguousarray(ir, dtype=np.int32)
+    out = np.zeros(len(q))
+    _check(lib().orc_adjoint_entries(prob.ref, _ptr(f_n), _ptr(lam), ctypes.c_int(len(q)), q.ctypes.data_as(_ip),
+                                     it.ctypes.data_as(_ip), ir.ctypes.data_as(_ip), _ptr(out)), "adjoint_entries")
     return out

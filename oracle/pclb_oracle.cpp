@@ -73,6 +73,13 @@ inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
 
 inline double val(double x) { return x; }
 inline double val(const Dual& x) { return x.v; }
+// A stored input value as the independent variable of a forward-mode sweep.
+template <class T>
+T seeded(double x);
+template <>
+inline double seeded<double>(double x) { return x; }
+template <>
+inline Dual seeded<Dual>(double x) { return Dual(x, 1.0); }
 inline double sgn(double x) { return (x > 0) - (x < 0); }
 inline double absval(double x) { return std::fabs(x); }
 // |x| with d|x|/dx = sign(x), sign(0) = 0.
@@ -217,12 +224,95 @@ namespace {
 
 // One time step of Eq. (38) with the boundary nodes of Sec. II C.
 // f_in, f_out: [Q][n_theta][n_r].  Returns a status bitmask.
+// Ghost nodes of one theta row at one wall, Sec. II C 1: macroscopic
+// quantities from Eq. (39) (or prescribed), f = f^eq there.  fa, fb: the Q
+// values at the wall node (i_r = 1 or N_r) and the next node inward; fe1,
+// fe2: f^eq at the adjacent and the outer ghost node.
 template <class T>
-int step_impl(const orc_problem& P, const Dvm& d, const T* f_in, T* f_out, bool parallel) {
+int radial_ghost_layers(const orc_problem& P, const Dvm& d, int it, int side, const T* fa, const T* fb, T* fe1,
+                        T* fe2) {
+  const int NT = P.n_theta;
+  const double dth = 2.0 * M_PI * P.n_f / (double(P.n_dirs) * NT);       // Sec. II C 2
+  const double theta = (it + 1) * dth;
+  const double c = std::cos(theta), s = std::sin(theta);
+  T ra, uxa, uya, Ea, rb, uxb, uyb, Eb;
+  moments_node(d, fa, 1, ra, uxa, uya, Ea);
+  moments_node(d, fb, 1, rb, uxb, uyb, Eb);
+  T rho1 = 2.0 * ra - rb, rho2 = 2.0 * rho1 - ra;   // Eq. (39), applied twice
+  T E1 = 2.0 * Ea - Eb, E2 = 2.0 * E1 - Ea;         // "temperature in a similar way"
+  T ux1 = 2.0 * uxa - uxb, ux2 = 2.0 * ux1 - uxa;
+  T uy1 = 2.0 * uya - uyb, uy2 = 2.0 * uy1 - uya;
+  const int kind = P.bc_kind[side];
+  const double* V = P.bc_values[side];
+  auto given = [&](int layer, int field) { return V[((size_t)layer * 4 + field) * NT + it]; };
+  if (kind == 1 || kind == 2) {  // prescribed polar velocity at the ghost nodes
+    ux1 = T(given(0, 1) * c - given(0, 2) * s);
+    uy1 = T(given(0, 1) * s + given(0, 2) * c);
+    ux2 = T(given(1, 1) * c - given(1, 2) * s);
+    uy2 = T(given(1, 1) * s + given(1, 2) * c);
+  }
+  if (kind == 2) {
+    rho1 = T(given(0, 0)); E1 = T(given(0, 3));
+    rho2 = T(given(1, 0)); E2 = T(given(1, 3));
+  }
+  int status = 0;
+  if (!(val(rho1) > 0 && val(rho2) > 0 && val(E1) > 0 && val(E2) > 0)) status |= ORC_NONPHYS;
+  feq_node(d, rho1, ux1, uy1, E1, fe1);
+  feq_node(d, rho2, ux2, uy2, E2, fe2);
+  return status;
+}
+
+// Label whose values fill the azimuthal ghost rows of label q, Eq. (40): the
+// direction index rotated by N_f, for rows below the first (lo) and above the
+// last (hi) interior row.
+inline void azimuthal_labels(const orc_problem& P, const Dvm& d, int q, int& q_lo, int& q_hi) {
+  q_lo = q_hi = q;
+  if (d.shell[q] > 0) {
+    int k = d.shell[q], i = d.dir[q];
+    int i_lo = paper_mod(i + P.n_f, P.n_dirs);
+    int i_hi = paper_mod(i - P.n_f + P.n_dirs, P.n_dirs);
+    q_lo = 1 + (k - 1) * P.n_dirs + (i_lo - 1);
+    q_hi = 1 + (k - 1) * P.n_dirs + (i_hi - 1);
+  }
+}
+
+// Combined scheme, Eq. (38), at node (it, ir) (0-based interior indices).
+// G(q, jt, jr) gives f with two ghost layers on every side (jt, jr from -2
+// to N + 1).  Writes the Q updated values to out.
+template <class T, class Get>
+int update_node(const orc_problem& P, const Dvm& d, int it, int ir, Get G, T* out) {
   const int NR = P.n_r, NT = P.n_theta, Q = d.Q;
   const double dr = (P.r_out - P.r_in) / (NR - 1);                       // Sec. II C 1
   const double dth = 2.0 * M_PI * P.n_f / (double(P.n_dirs) * NT);       // Sec. II C 2
   const double decay = std::exp(-P.dt / P.tau);                          // Eq. (19)
+  const double theta = (it + 1) * dth;
+  const double c = std::cos(theta), s = std::sin(theta);
+  const double r = P.r_in + ir * dr;
+  int status = 0;
+  std::vector<T> fc(Q), fe(Q);
+  for (int q = 0; q < Q; ++q) fc[q] = G(q, it, ir);
+  T rho, ux, uy, E;
+  moments_node(d, fc.data(), 1, rho, ux, uy, E);
+  if (!(val(rho) > 0 && val(E) > 0)) status |= ORC_NONPHYS;
+  feq_node(d, rho, ux, uy, E, fe.data());
+  for (int q = 0; q < Q; ++q) {
+    const double v_r = d.vx[q] * c + d.vy[q] * s;
+    const double v_t = -d.vx[q] * s + d.vy[q] * c;
+    const double C_r = v_r * P.dt / dr;
+    const double C_t = v_t * P.dt / (r * dth);
+    T f = fc[q];
+    T relax = fe[q] + (f - fe[q]) * decay;
+    T term_r = mwb_increment(C_r, G(q, it, ir - 2), G(q, it, ir - 1), f, G(q, it, ir + 1), G(q, it, ir + 2));
+    T term_t = mwb_increment(C_t, G(q, it - 2, ir), G(q, it - 1, ir), f, G(q, it + 1, ir), G(q, it + 2, ir));
+    out[q] = relax - term_r - term_t;
+    if (!std::isfinite(val(out[q]))) status |= ORC_NONFINITE;
+  }
+  return status;
+}
+
+template <class T>
+int step_impl(const orc_problem& P, const Dvm& d, const T* f_in, T* f_out, bool parallel) {
+  const int NR = P.n_r, NT = P.n_theta, Q = d.Q;
 
   // Extended array with two ghost layers on every side; corner ghosts are
   // never read by the axis-aligned stencils and stay NaN.
@@ -237,57 +327,32 @@ int step_impl(const orc_problem& P, const Dvm& d, const T* f_in, T* f_out, bool 
 
   int status = 0;
 
-  // (1) Radial ghost nodes, Sec. II C 1: macroscopic quantities from Eq. (39)
-  //     (or prescribed), f = f^eq there.
-  for (int it = 0; it < NT; ++it) {
-    const double theta = (it + 1) * dth;
-    const double c = std::cos(theta), s = std::sin(theta);
-    for (int side = 0; side < 2; ++side) {
-      const int ia = side == 0 ? 0 : NR - 1;       // wall node i_r = 1 or N_r
-      const int ib = side == 0 ? 1 : NR - 2;       // next node inward
-      const int g1 = side == 0 ? -1 : NR;          // adjacent ghost (i_r = 0 or N_r + 1)
-      const int g2 = side == 0 ? -2 : NR + 1;      // outer ghost (i_r = -1 or N_r + 2)
-      const long stride = (long)ET * ER;
-      T ra, uxa, uya, Ea, rb, uxb, uyb, Eb;
-      moments_node(d, &G(0, it, ia), stride, ra, uxa, uya, Ea);
-      moments_node(d, &G(0, it, ib), stride, rb, uxb, uyb, Eb);
-      T rho1 = 2.0 * ra - rb, rho2 = 2.0 * rho1 - ra;   // Eq. (39), applied twice
-      T E1 = 2.0 * Ea - Eb, E2 = 2.0 * E1 - Ea;         // "temperature in a similar way"
-      T ux1 = 2.0 * uxa - uxb, ux2 = 2.0 * ux1 - uxa;
-      T uy1 = 2.0 * uya - uyb, uy2 = 2.0 * uy1 - uya;
-      const int kind = P.bc_kind[side];
-      const double* V = P.bc_values[side];
-      auto given = [&](int layer, int field) { return V[((size_t)layer * 4 + field) * NT + it]; };
-      if (kind == 1 || kind == 2) {  // prescribed polar velocity at the ghost nodes
-        ux1 = T(given(0, 1) * c - given(0, 2) * s);
-        uy1 = T(given(0, 1) * s + given(0, 2) * c);
-        ux2 = T(given(1, 1) * c - given(1, 2) * s);
-        uy2 = T(given(1, 1) * s + given(1, 2) * c);
+  // (1) Radial ghost nodes, Sec. II C 1.
+  {
+    std::vector<T> fa(Q), fb(Q), fe1(Q), fe2(Q);
+    for (int it = 0; it < NT; ++it)
+      for (int side = 0; side < 2; ++side) {
+        const int ia = side == 0 ? 0 : NR - 1;       // wall node i_r = 1 or N_r
+        const int ib = side == 0 ? 1 : NR - 2;       // next node inward
+        const int g1 = side == 0 ? -1 : NR;          // adjacent ghost (i_r = 0 or N_r + 1)
+        const int g2 = side == 0 ? -2 : NR + 1;      // outer ghost (i_r = -1 or N_r + 2)
+        for (int q = 0; q < Q; ++q) {
+          fa[q] = G(q, it, ia);
+          fb[q] = G(q, it, ib);
+        }
+        status |= radial_ghost_layers(P, d, it, side, fa.data(), fb.data(), fe1.data(), fe2.data());
+        for (int q = 0; q < Q; ++q) {
+          G(q, it, g1) = fe1[q];
+          G(q, it, g2) = fe2[q];
+        }
       }
-      if (kind == 2) {
-        rho1 = T(given(0, 0)); E1 = T(given(0, 3));
-        rho2 = T(given(1, 0)); E2 = T(given(1, 3));
-      }
-      if (!(val(rho1) > 0 && val(rho2) > 0 && val(E1) > 0 && val(E2) > 0)) status |= ORC_NONPHYS;
-      std::vector<T> fe(Q);
-      feq_node(d, rho1, ux1, uy1, E1, fe.data());
-      for (int q = 0; q < Q; ++q) G(q, it, g1) = fe[q];
-      feq_node(d, rho2, ux2, uy2, E2, fe.data());
-      for (int q = 0; q < Q; ++q) G(q, it, g2) = fe[q];
-    }
   }
 
   // (2) Azimuthal ghost nodes, Eq. (40): copies of the rows at the other end
   //     of the period with the direction label rotated by N_f.
   for (int q = 0; q < Q; ++q) {
-    int q_lo = q, q_hi = q;  // source labels for i_theta <= 0 and i_theta > N_theta
-    if (d.shell[q] > 0) {
-      int k = d.shell[q], i = d.dir[q];
-      int i_lo = paper_mod(i + P.n_f, P.n_dirs);
-      int i_hi = paper_mod(i - P.n_f + P.n_dirs, P.n_dirs);
-      q_lo = 1 + (k - 1) * P.n_dirs + (i_lo - 1);
-      q_hi = 1 + (k - 1) * P.n_dirs + (i_hi - 1);
-    }
+    int q_lo, q_hi;
+    azimuthal_labels(P, d, q, q_lo, q_hi);
     for (int ir = 0; ir < NR; ++ir) {
       G(q, -2, ir) = G(q_lo, NT - 2, ir);
       G(q, -1, ir) = G(q_lo, NT - 1, ir);
@@ -297,34 +362,70 @@ int step_impl(const orc_problem& P, const Dvm& d, const T* f_in, T* f_out, bool 
   }
 
   // (3) Combined scheme, Eq. (38), at every node.
+  auto Gv = [&](int q, int it, int ir) -> T { return G(q, it, ir); };
 #pragma omp parallel for schedule(static) reduction(| : status) if (parallel)
   for (int it = 0; it < NT; ++it) {
-    const double theta = (it + 1) * dth;
-    const double c = std::cos(theta), s = std::sin(theta);
-    std::vector<T> fe(Q);
+    std::vector<T> out(Q);
     for (int ir = 0; ir < NR; ++ir) {
-      const double r = P.r_in + ir * dr;
-      T rho, ux, uy, E;
-      moments_node(d, &G(0, it, ir), (long)ET * ER, rho, ux, uy, E);
-      if (!(val(rho) > 0 && val(E) > 0)) status |= ORC_NONPHYS;
-      feq_node(d, rho, ux, uy, E, fe.data());
-      for (int q = 0; q < Q; ++q) {
-        const double v_r = d.vx[q] * c + d.vy[q] * s;
-        const double v_t = -d.vx[q] * s + d.vy[q] * c;
-        const double C_r = v_r * P.dt / dr;
-        const double C_t = v_t * P.dt / (r * dth);
-        T f = G(q, it, ir);
-        T relax = fe[q] + (f - fe[q]) * decay;
-        T term_r = mwb_increment(C_r, G(q, it, ir - 2), G(q, it, ir - 1), f, G(q, it, ir + 1),
-                                 G(q, it, ir + 2));
-        T term_t = mwb_increment(C_t, G(q, it - 2, ir), G(q, it - 1, ir), f, G(q, it + 1, ir),
-                                 G(q, it + 2, ir));
-        T out = relax - term_r - term_t;
-        if (!std::isfinite(val(out))) status |= ORC_NONFINITE;
-        f_out[((size_t)q * NT + it) * NR + ir] = out;
-      }
+      status |= update_node(P, d, it, ir, Gv, out.data());
+      for (int q = 0; q < Q; ++q) f_out[((size_t)q * NT + it) * NR + ir] = out[q];
     }
   }
+  return status;
+}
+
+// The same step evaluated only at chosen nodes, reading f_in in place: the
+// extended values the stencils need are formed on demand with exactly the
+// operations of step_impl (wrapped rows with rotated labels; radial ghost
+// layers of the rows that are read).  seed >= 0 marks one stored entry
+// q * NT * NR + it * NR + ir whose derivative is 1 (T = Dual), for the
+// node-local adjoint below.
+template <class T>
+int step_nodes_impl(const orc_problem& P, const Dvm& d, const double* f_in, long seed, int n, const int32_t* it_list,
+                    const int32_t* ir_list, T* out) {
+  const int NR = P.n_r, NT = P.n_theta, Q = d.Q;
+  std::vector<int> qlo(Q), qhi(Q);
+  for (int q = 0; q < Q; ++q) azimuthal_labels(P, d, q, qlo[q], qhi[q]);
+  auto stored = [&](int q, int it, int ir) -> T {   // interior entry, it in [0, NT)
+    const long idx = ((long)q * NT + it) * NR + ir;
+    T v = T(f_in[idx]);
+    if (idx == seed) v = seeded<T>(f_in[idx]);
+    return v;
+  };
+  int status = 0;
+  std::vector<T> fa(Q), fb(Q), fe1(Q), fe2(Q);
+  // radial ghost layers of row `it` at `side`, recomputed when first needed
+  std::vector<std::vector<T>> gcache;
+  std::vector<long> gkey;
+  auto ghost = [&](int it, int side, int layer, int q) -> T {
+    const long key = ((long)it * 2 + side);
+    for (size_t j = 0; j < gkey.size(); ++j)
+      if (gkey[j] == key) return gcache[j][(size_t)layer * Q + q];
+    const int ia = side == 0 ? 0 : NR - 1, ib = side == 0 ? 1 : NR - 2;
+    for (int p = 0; p < Q; ++p) {
+      fa[p] = stored(p, it, ia);
+      fb[p] = stored(p, it, ib);
+    }
+    status |= radial_ghost_layers(P, d, it, side, fa.data(), fb.data(), fe1.data(), fe2.data());
+    std::vector<T> both(2 * Q);
+    for (int p = 0; p < Q; ++p) {
+      both[p] = fe1[p];
+      both[Q + p] = fe2[p];
+    }
+    gkey.push_back(key);
+    gcache.push_back(both);
+    return gcache.back()[(size_t)layer * Q + q];
+  };
+  auto G = [&](int q, int it, int ir) -> T {
+    if (it < 0 || it >= NT) {                     // azimuthal ghost rows, Eq. (40)
+      if (ir < 0 || ir >= NR) return T(std::numeric_limits<double>::quiet_NaN());   // corner
+      return it < 0 ? stored(qlo[q], it + NT, ir) : stored(qhi[q], it - NT, ir);
+    }
+    if (ir < 0) return ghost(it, 0, ir == -1 ? 0 : 1, q);
+    if (ir >= NR) return ghost(it, 1, ir == NR ? 0 : 1, q);
+    return stored(q, it, ir);
+  };
+  for (int j = 0; j < n; ++j) status |= update_node(P, d, it_list[j], ir_list[j], G, out + (size_t)j * Q);
   return status;
 }
 
@@ -345,9 +446,10 @@ int set_state_impl(const orc_problem& P, const Dvm& d, const T* rho, const T* u_
                    T* f) {
   const int NR = P.n_r, NT = P.n_theta;
   const double dth = 2.0 * M_PI * P.n_f / (double(P.n_dirs) * NT);
-  std::vector<T> fe(d.Q);
   int status = 0;
+#pragma omp parallel for schedule(static) reduction(| : status)
   for (int it = 0; it < NT; ++it) {
+    std::vector<T> fe(d.Q);
     const double th = (it + 1) * dth, c = std::cos(th), s = std::sin(th);
     for (int ir = 0; ir < NR; ++ir) {
       size_t n = (size_t)it * NR + ir;
@@ -550,6 +652,55 @@ int orc_adjoint_step(const orc_problem* P, const double* f_n, const double* lam_
       for (long i = 0; i < N; ++i) acc += lam_np1[i] * y[i].d;
       lam_n[j] = acc;
     }
+  }
+  return status;
+}
+
+// f^{n+1} at chosen nodes only: out[j * Q + q] for the node (it[j], ir[j])
+// (0-based), from the whole f^n.  Same operations as orc_step.
+int orc_step_nodes(const orc_problem* P, const double* f_in, int n, const int32_t* it, const int32_t* ir,
+                   double* out) {
+  if (!valid(P)) return ORC_EINVAL;
+  for (int j = 0; j < n; ++j)
+    if (it[j] < 0 || it[j] >= P->n_theta || ir[j] < 0 || ir[j] >= P->n_r) return ORC_EINVAL;
+  Dvm d = make_dvm(P->n_dirs, P->speeds, P->B);
+  return step_nodes_impl<double>(*P, d, f_in, -1, n, it, ir, out);
+}
+
+// Chosen entries of the adjoint step, lam^n_q(it, ir) = sum over every output
+// (q', node) of lam^{n+1}_q'(node) d f^{n+1}_q'(node) / d f^n_q(it, ir), by
+// its definition: one forward-mode sweep seeded at the entry, over the nodes
+// whose update can read it (the same theta row within two radial nodes, the
+// same radius within two rows, azimuthal rows wrapped).
+int orc_adjoint_entries(const orc_problem* P, const double* f_n, const double* lam_np1, int n, const int32_t* q,
+                        const int32_t* it, const int32_t* ir, double* out) {
+  if (!valid(P)) return ORC_EINVAL;
+  const int NR = P->n_r, NT = P->n_theta;
+  Dvm d = make_dvm(P->n_dirs, P->speeds, P->B);
+  const int Q = d.Q;
+  for (int j = 0; j < n; ++j)
+    if (q[j] < 0 || q[j] >= Q || it[j] < 0 || it[j] >= NT || ir[j] < 0 || ir[j] >= NR) return ORC_EINVAL;
+  int status = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : status)
+  for (int j = 0; j < n; ++j) {
+    std::vector<int32_t> nt, nr;
+    auto add = [&](int t, int r) {
+      t = ((t % NT) + NT) % NT;
+      for (size_t m = 0; m < nt.size(); ++m)
+        if (nt[m] == t && nr[m] == r) return;
+      nt.push_back(t);
+      nr.push_back(r);
+    };
+    for (int a = -2; a <= 2; ++a) add(it[j] + a, ir[j]);
+    for (int b = -2; b <= 2; ++b)
+      if (ir[j] + b >= 0 && ir[j] + b < NR) add(it[j], ir[j] + b);
+    const long seed = ((long)q[j] * NT + it[j]) * NR + ir[j];
+    std::vector<Dual> y(nt.size() * Q);
+    status |= step_nodes_impl<Dual>(*P, d, f_n, seed, (int)nt.size(), nt.data(), nr.data(), y.data());
+    double acc = 0.0;
+    for (size_t m = 0; m < nt.size(); ++m)
+      for (int p = 0; p < Q; ++p) acc += lam_np1[((size_t)p * NT + nt[m]) * NR + nr[m]] * y[m * Q + p].d;
+    out[j] = acc;
   }
   return status;
 }

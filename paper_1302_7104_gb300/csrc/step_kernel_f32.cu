@@ -212,14 +212,13 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// MWB increments of both nodes in upwind form:
-// a D + K |D| (D - Dp) / (|D| + |Dp|)  (0 when D = Dp = 0), Eq. (28).
-__device__ __forceinline__ f2 mwb2(f2 a, f2 K, f2 D, f2 Dp) {
+// Limiter part of the MWB increment of both nodes, |D| (D - Dp) / (|D| + |Dp|)
+// (0 when D = Dp = 0), Eq. (28) in upwind form.
+__device__ __forceinline__ f2 limiter2(f2 D, f2 Dp) {
   const float den0 = fmaxf(fabsf(D.x) + fabsf(Dp.x), 1e-30f);
   const float den1 = fmaxf(fabsf(D.y) + fabsf(Dp.y), 1e-30f);
   const f2 t = mk2(fabsf(D.x) * rcp_approx(den0), fabsf(D.y) * rcp_approx(den1));
-  const f2 h = mul2(t, sub2(D, Dp));
-  return fma2(a, D, mul2(K, h));
+  return mul2(t, sub2(D, Dp));
 }
 
 }  // namespace
@@ -305,8 +304,12 @@ __global__ void __launch_bounds__(kStepThreads, 2)
   float* out_lo = f_out + (size_t)max(t - (p.n_theta - 2), 0) * p.pitch + r;
   float* out_hi = f_out + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r;
 
+  // tiles away from the radial walls and the seam take the plain store
+  const bool plain_tile = r0 + kTileR <= p.n_r && t0 >= 2 && t0 + kTileT <= p.n_theta - 2;
   auto store = [&](int q, f2 o) {
-    if (v1) {
+    if (plain_tile) {
+      *reinterpret_cast<float2*>(out_row + (size_t)q * plane_out) = o;
+    } else if (v1) {
       *reinterpret_cast<float2*>(out_row + (size_t)q * plane_out) = o;
       if (lo_ghost) *reinterpret_cast<float2*>(out_lo + (size_t)d.recv_lo[q] * plane_out) = o;
       if (hi_ghost) *reinterpret_cast<float2*>(out_hi + (size_t)d.recv_hi[q] * plane_out) = o;
@@ -325,16 +328,20 @@ __global__ void __launch_bounds__(kStepThreads, 2)
 
   // One velocity of a pair.  sr = +1 if its upwind neighbour in r is at
   // larger r, st the same for theta (rows); fe is its equilibrium.
-  auto update = [&](int q, int sr, int st, f2 ar, f2 kr, f2 at, f2 kt, f2 fe) {
+  // nar, nkr, nat, nkt: the negated a = |C| and K = |C|(1 - |C|) in r and theta
+  auto update = [&](int q, int sr, int st, f2 nar, f2 nkr, f2 nat, f2 nkt, f2 fe) {
     const float* w = win + q * kPlaneF;
     const f2 C = ld2(w);
     const f2 S = ld2(w + 2 * sr);                 // (j-2, j-1) or (j+2, j+3)
     const f2 T1 = ld2(w + st * kWinR);
     const f2 T2 = ld2(w + 2 * st * kWinR);
     const f2 u1 = sr < 0 ? mk2(S.y, C.x) : mk2(C.y, S.x);   // first upwind neighbours
-    const f2 mr = mwb2(ar, kr, sub2(C, u1), sub2(u1, S));
-    const f2 mt = mwb2(at, kt, sub2(C, T1), sub2(T1, T2));
-    const f2 o = sub2(sub2(fma2(sub2(C, fe), decay, fe), mr), mt);
+    const f2 Dr = sub2(C, u1), Dt = sub2(C, T1);
+    f2 o = fma2(sub2(C, fe), decay, fe);
+    o = fma2(nar, Dr, o);
+    o = fma2(nat, Dt, o);
+    o = fma2(nkr, limiter2(Dr, sub2(u1, S)), o);
+    o = fma2(nkt, limiter2(Dt, sub2(T1, T2)), o);
     store(q, o);
   };
 
@@ -352,16 +359,16 @@ __global__ void __launch_bounds__(kStepThreads, 2)
       const int fl = __float_as_int(tb.w);
       const int sr = (fl & 1) ? 1 : -1;            // v_r < 0: upwind at larger r
       const int st = (fl & 2) ? 1 : -1;            // v_theta < 0: upwind at larger theta
-      const f2 ar = bc2(tb.x), kr = bc2(tb.y);
-      const f2 at = mul2(bc2(tb.z), invr);
-      const f2 kt = fma2(neg2(at), at, at);
+      const f2 nar = bc2(-tb.x), nkr = bc2(-tb.y);
+      const f2 nat = mul2(bc2(-tb.z), invr);
+      const f2 nkt = fma2(nat, nat, nat);            // -(a - a^2) with a = -nat
       // equilibrium of the pair: P(+x) = ev + od, P(-x) = ev - od
       const f2 x = fma2(sh, eq.yh[i], fma2(sh, eq.yl[i], mul2(sl, eq.yh[i])));
       const f2 x2 = mul2(x, x);
       const f2 ev = fma2(x2, fma2(x2, bc2(1.0f / 24.0f), eq.a1h), eq.a0);
       const f2 od = mul2(x, fma2(x2, bc2(1.0f / 6.0f), eq.a1));
-      update(q, sr, st, ar, kr, at, kt, mul2(wk, add2(ev, od)));
-      update(q + kHalf, -sr, -st, ar, kr, at, kt, mul2(wk, sub2(ev, od)));
+      update(q, sr, st, nar, nkr, nat, nkt, mul2(wk, add2(ev, od)));
+      update(q + kHalf, -sr, -st, nar, nkr, nat, nkt, mul2(wk, sub2(ev, od)));
     }
   }
 }

@@ -1,0 +1,104 @@
+"""Parity at the full size of the benchmark workload: the Kelvin-Helmholtz
+annulus, N_r x N_theta = 4096 x 4096, 33 velocities, through the same C ABI
+call and launch configuration the benchmark times (one fused step launch over
+the whole grid).
+
+The oracle cannot step 16.8 M nodes in a test's time budget as a whole-grid
+reference in FP64 per case, so the comparison is on sampled outputs, each of
+which the oracle computes by itself: every node next to a wall, every node of
+the azimuthal seam rows, nodes on tile edges and random interior nodes
+(``oracle.step_nodes``), and sampled adjoint entries
+(``oracle.adjoint_entries``).  Inputs are the oracle's equilibrium of the KH
+fields with a seeded 1% multiplicative perturbation (non-equilibrium part),
+rounded to the precision under test; the GPU receives them through
+pclb_set_f.  Tolerances are those of the small-grid parity tests: FP64 1e-12
+and FP32 2e-6 of max|f| for one step, FP32 adjoint 1e-4 of max|lam^n|.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1302_7104_gb300 import inputs as I
+from paper_1302_7104_gb300 import pclb as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TILE_R, TILE_T = 32, 16
+
+
+@pytest.fixture(scope="module")
+def kh():
+    w = I.kh()
+    f = O.set_state(w)
+    rng = np.random.default_rng(20130228)
+    for q in range(f.shape[0]):
+        f[q] *= 1.0 + 0.01 * rng.standard_normal(f.shape[1:], dtype=np.float32)
+    return w, f
+
+
+def _sample_nodes(w, seed=7):
+    nt, nr = w.n_theta, w.n_r
+    rng = np.random.default_rng(seed)
+    it, ir = [], []
+    # walls: the two nodes at each wall and the two next to them, on random rows and the seam rows
+    rows = np.concatenate([rng.integers(0, nt, 48), [0, 1, nt - 2, nt - 1]])
+    for c in (0, 1, 2, 3, nr - 4, nr - 3, nr - 2, nr - 1):
+        it += list(rows)
+        ir += [c] * len(rows)
+    # seam rows (azimuthal ghosts with label rotation)
+    cols = rng.integers(0, nr, 48)
+    for t in (0, 1, 2, 3, nt - 4, nt - 3, nt - 2, nt - 1):
+        it += [t] * len(cols)
+        ir += list(cols)
+    # tile edges in r and theta
+    for _ in range(256):
+        it.append(int(rng.integers(1, nt // TILE_T)) * TILE_T + int(rng.integers(-2, 2)))
+        ir.append(int(rng.integers(1, nr // TILE_R)) * TILE_R + int(rng.integers(-2, 2)))
+    # random interior
+    it += list(rng.integers(0, nt, 1024))
+    ir += list(rng.integers(0, nr, 1024))
+    return np.asarray(it, dtype=np.int64), np.asarray(ir, dtype=np.int64)
+
+
+def _gather(t, it, ir):
+    """t[:, it, ir] on the device, returned as float64 [n, Q]."""
+    it_d = torch.as_tensor(it, device=t.device)
+    ir_d = torch.as_tensor(ir, device=t.device)
+    return t[:, it_d, ir_d].double().cpu().numpy().T
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp64", 1e-12)])
+def test_full_size_step_matches_oracle_on_sampled_nodes(kh, prec, tol):
+    w, f = kh
+    dtype = torch.float32 if prec == "fp32" else torch.float64
+    f_in = f.astype(np.float32).astype(np.float64) if prec == "fp32" else f
+    it, ir = _sample_nodes(w)
+    with P.PCLB(w, precision=prec) as g:
+        g.set_f(torch.from_numpy(f_in).to(device="cuda", dtype=dtype)).step(1)
+        got = _gather(g.get_f(), it, ir)
+        assert g.status_flags() == 0
+    want = O.step_nodes(w, f_in, it, ir)
+    err = np.max(np.abs(got - want)) / np.max(np.abs(f_in))
+    assert err <= tol, err
+
+
+def test_full_size_fp32_adjoint_matches_oracle_on_sampled_entries(kh):
+    w, f = kh
+    f32 = torch.from_numpy(f.astype(np.float32))
+    rng = np.random.default_rng(99)
+    lam32 = np.empty(f.shape, dtype=np.float32)
+    for q in range(f.shape[0]):
+        lam32[q] = rng.standard_normal(f.shape[1:], dtype=np.float32)
+    it, ir = _sample_nodes(w, seed=8)
+    q = np.random.default_rng(3).integers(0, f.shape[0], len(it))
+    with P.PCLB(w, precision="fp32") as g:
+        out = g.adjoint_step(f32.to("cuda"), torch.from_numpy(lam32).to("cuda"))
+        got = out[torch.as_tensor(q, device="cuda"), torch.as_tensor(it, device="cuda"),
+                  torch.as_tensor(ir, device="cuda")].double().cpu().numpy()
+        scale = float(out.abs().max())
+        assert g.status_flags() == 0
+    want = O.adjoint_entries(w, f32.numpy().astype(np.float64), lam32.astype(np.float64), q, it, ir)
+    err = np.max(np.abs(got - want)) / scale
+    assert err <= 1e-4, err

@@ -98,9 +98,16 @@ def test_rm_gradient_matches_oracle_finite_differences_on_a_non_uniform_state():
 
 
 def test_fp32_gradient_close_to_fp64_gradient():
+    # On the background-modulated state: the piecewise-uniform RM state has
+    # D = 0 exactly wherever the gas is uniform, where the limiter's
+    # derivative jumps (sign(0) = 0 on one side of the kink, +-1 on the
+    # other), so FP32 rounding of order 1e-7 in the forward states can select
+    # a different one-sided derivative than FP64 at some nodes.  With the
+    # modulation no difference sits on a kink and the two precisions
+    # differentiate the same branches.
     a = I.rm_amplitudes(seed=8)
-    _, g64 = _rm_gradient_gpu(a, 64, 128, 40, "fp64")
-    _, g32 = _rm_gradient_gpu(a, 64, 128, 40, "fp32")
+    _, g64 = _rm_gradient_gpu(a, 64, 128, 40, "fp64", background=1e-3)
+    _, g32 = _rm_gradient_gpu(a, 64, 128, 40, "fp32", background=1e-3)
     assert np.max(np.abs(g32 - g64)) <= 1e-3 * np.max(np.abs(g64))
 
 
