@@ -19,13 +19,19 @@
 //
 // One CTA: 32 (r) x TT (theta) nodes, one node per thread; the windows of f
 // and lam over [r0-4, r0+36) x [t0-2, t0+TT+2) for all 33 labels are staged
-// in shared memory by TMA.
+// in shared memory by TMA.  Velocities are processed in pairs of opposite
+// labels, each in two phases: (A) every node whose upwind stencil can reach
+// the tile forms lam(n) dM(n)/dD and lam(n) dM(n)/dDp once, in r and in
+// theta, into shared memory; (B) every tile node gathers the products of the
+// nodes that read it.  One barrier per pair separates the phases; the
+// products live in two alternating buffers.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
 #include "adjoint_common.cuh"
 #include "ghost_cols.cuh"
+#include "f32_state.cuh"
 #include "pclb_internal.h"
 
 namespace pclb {
@@ -55,10 +61,16 @@ struct AdjSize {
   static constexpr int TT = AdjTile<T>::TT;
   static constexpr int plane = kWinR * (TT + 4);
   static constexpr int npairs = 4 * kNDirs / 2;
+  // products of one label: radial A, B over TT rows x 36 columns (tile
+  // columns -2 .. 33), azimuthal A, B over TT + 4 rows (-2 .. TT + 1) x 32
+  static constexpr int rcols = kTileR + 4;
+  static constexpr int prod = 2 * TT * rcols + 2 * (TT + 4) * kTileR;
   static constexpr int win_bytes = 2 * kQ * plane * (int)sizeof(T);
+  static constexpr int prod_bytes = 2 * 2 * prod * (int)sizeof(T);  // 2 buffers x 2 labels
   static constexpr int gw_bytes = 2 * 2 * TT * 4 * (int)sizeof(T);
+  static constexpr int invr_bytes = kTileR * (int)sizeof(T);
   static constexpr int tab_bytes = (TT + 4) * npairs * (int)sizeof(CourEntry<T>);
-  static constexpr int smem = win_bytes + gw_bytes + tab_bytes + 128;
+  static constexpr int smem = win_bytes + prod_bytes + gw_bytes + invr_bytes + tab_bytes + 128;
 };
 
 namespace {
@@ -104,54 +116,21 @@ __device__ __forceinline__ Cour<T> courant(const StepParams& p, const DvmConst<T
   return c;
 }
 
-// Sum over the nodes n whose MWB increments (Eq. 28) in r and theta read
-// f_q(c) of lam_q(n) dM_q(n)/df_q(c), for one label at this node c.  f and l
-// point at c in the label's f and lam windows; ur is the radial upwind offset
-// (+-1 column); at[o], kt[o] are a = |C_theta| and K = a(1 - a) of the theta
-// rows o - 2 (o = 0..4) at this radius, and bit o of vt_neg is set when row
-// o - 2 takes its upwind neighbour at the next row (v_theta < 0).  The node
-// n = c + j u_n reads f(n), f(n + u_n), f(n + 2 u_n) with D = f(n) - f(n + u_n),
-// Dp = f(n + u_n) - f(n + 2 u_n), so
-//   dM(n)/df(n) = M_D,  dM(n)/df(n + u_n) = M_Dp - M_D,  dM(n)/df(n + 2 u_n) = -M_Dp.
-template <class T>
-__device__ __forceinline__ T adjoint_stencil(const T* f, const T* l, int ur, T ar, T kr, const T* at, const T* kt,
-                                             int vt_neg) {
-  const T f0 = f[0];
-  // radial: the nodes c, c - u, c - 2u
-  const T fm2 = f[-2 * ur], fm1 = f[-ur], fp1 = f[ur], fp2 = f[2 * ur];
-  const T dm2 = fm2 - fm1, dm1 = fm1 - f0, d0 = f0 - fp1, d1 = fp1 - fp2;
-  T MD0, MP0, MD1, MP1, MD2, MP2;
-  mwb_partials<T>(ar, kr, d0, d1, MD0, MP0);
-  mwb_partials<T>(ar, kr, dm1, d0, MD1, MP1);
-  mwb_partials<T>(ar, kr, dm2, dm1, MD2, MP2);
-  T acc = l[0] * MD0 + l[-ur] * (MP1 - MD1) - l[-2 * ur] * MP2;
-  // azimuthal: rows -2..2 of this column, e_j = f(row j) - f(row j + 1)
-  constexpr int S = kWinR;
-  const T gm2 = f[-2 * S], gm1 = f[-S], gp1 = f[S], gp2 = f[2 * S];
-  const T em2 = gm2 - gm1, em1 = gm1 - f0, e0 = f0 - gp1, e1 = gp1 - gp2;
-  T MD, MP;
-  if (vt_neg & 4)
-    mwb_partials<T>(at[2], kt[2], e0, e1, MD, MP);     // this node, upwind at row +1
-  else
-    mwb_partials<T>(at[2], kt[2], em1, em2, MD, MP);   // upwind at row -1 (signs flipped)
-  acc += l[0] * MD;
-  if (vt_neg & 2) {          // row -1 reads this node as its first upwind neighbour
-    mwb_partials<T>(at[1], kt[1], em1, e0, MD, MP);
-    acc += l[-S] * (MP - MD);
-  }
-  if (!(vt_neg & 8)) {       // row +1, likewise
-    mwb_partials<T>(at[3], kt[3], e0, em1, MD, MP);
-    acc += l[S] * (MP - MD);
-  }
-  if (vt_neg & 1) {          // row -2 reads this node as its second upwind neighbour
-    mwb_partials<T>(at[0], kt[0], em2, em1, MD, MP);
-    acc -= l[-2 * S] * MP;
-  }
-  if (!(vt_neg & 16)) {      // row +2, likewise
-    mwb_partials<T>(at[4], kt[4], e1, e0, MD, MP);
-    acc -= l[2 * S] * MP;
-  }
-  return acc;
+// (rho, u_x, u_y, E) of one node for the cotangent of the equilibrium:
+// float-float moments rounded to float in FP32, double in FP64.
+__device__ __forceinline__ void adj_node_state(const float* f, int plane, const DvmConst<float>& d, float& rho,
+                                               float& ux, float& uy, float& E, bool& ok) {
+  const State32 m = state32(f, plane, d);
+  rho = m.rho.hi + m.rho.lo;
+  ux = m.ux.hi + m.ux.lo;
+  uy = m.uy.hi + m.uy.lo;
+  E = m.E.hi + m.E.lo;
+  ok = m.ok;
+}
+__device__ __forceinline__ void adj_node_state(const double* f, int plane, const DvmConst<double>& d, double& rho,
+                                               double& ux, double& uy, double& E, bool& ok) {
+  const NodeState<double> m = node_moments(f, plane, d);
+  rho = m.rho; ux = m.ux; uy = m.uy; E = m.E; ok = m.ok;
 }
 
 }  // namespace
@@ -165,9 +144,11 @@ __global__ void __launch_bounds__(AdjTile<T>::TT * 32, 1)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* sf = reinterpret_cast<T*>(smem_raw);
   T* sl = sf + kQ * PLANE;
-  T* gw = sl + kQ * PLANE;                          // [side][node][TT][4]
-  CourEntry<T>* ctab = reinterpret_cast<CourEntry<T>*>(gw + 2 * 2 * TT * 4);   // [TT + 4][npairs]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(ctab + (TT + 4) * AdjSize<T>::npairs);
+  T* prod = sl + kQ * PLANE;                        // [buffer][label][products]
+  T* gw = prod + 2 * 2 * AdjSize<T>::prod;          // [side][node][TT][4]
+  T* invr = gw + 2 * 2 * TT * 4;                    // 1/r of the tile columns
+  CourEntry<T>* ctab = reinterpret_cast<CourEntry<T>*>(invr + kTileR);   // [TT + 4][npairs]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ctab + (TT + 4) * AdjSize<T>::npairs);   // [0] f, [1] lam
 
   const int r0 = blockIdx.x * kTileR;
   const int t0 = blockIdx.y * TT;
@@ -177,10 +158,12 @@ __global__ void __launch_bounds__(AdjTile<T>::TT * 32, 1)
   if (tid == 0) {
     tma_prefetch_desc(&tmap_f);
     tma_prefetch_desc(&tmap_l);
-    mbar_init(bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     mbar_fence_init();
   }
   for (int i = tid; i < 2 * 2 * TT * 4; i += blockDim.x) gw[i] = T(0);
+  if (tid < kTileR) invr[tid] = r0 + tid < p.n_r ? (T)p.inv_r[r0 + tid] : T(1);
   // Courant entries of the stored rows t0 .. t0 + TT + 3 (theta rows t0 - 2 .. t0 + TT + 1)
   for (int i = tid; i < (TT + 4) * AdjSize<T>::npairs; i += blockDim.x) {
     const int srow = t0 + i / AdjSize<T>::npairs, pair = i % AdjSize<T>::npairs;
@@ -190,16 +173,21 @@ __global__ void __launch_bounds__(AdjTile<T>::TT * 32, 1)
   }
   __syncthreads();
   if (tid == 0) {
-    mbar_arrive_expect_tx(bar, (uint32_t)(2 * kQ * PLANE * sizeof(T)));
+    mbar_arrive_expect_tx(&bar[0], (uint32_t)(kQ * PLANE * sizeof(T)));
+    mbar_arrive_expect_tx(&bar[1], (uint32_t)(kQ * PLANE * sizeof(T)));
 #pragma unroll 1
-    for (int q = 0; q < kQ; ++q) {
-      tma_load_3d(sf + q * PLANE, &tmap_f, r0 - kLeft, t0, q, bar);
-      tma_load_3d(sl + q * PLANE, &tmap_l, r0 - kLeft, t0, q, bar);
-    }
+    for (int q = 0; q < kQ; ++q) tma_load_3d(sf + q * PLANE, &tmap_f, r0 - kLeft, t0, q, &bar[0]);
+#pragma unroll 1
+    for (int q = 0; q < kQ; ++q) tma_load_3d(sl + q * PLANE, &tmap_l, r0 - kLeft, t0, q, &bar[1]);
   }
-  if (!mbar_wait_bounded(bar, 0, kAdjWaitNs)) {
-    if (tid == 0) atomicOr(p.status, PCLB_FLAG_TIMEOUT);
-    mbar_wait_bounded(bar, 0, kAdjWaitNs);
+  // f first (moments, ghost columns); lam is awaited before it is first read
+  const bool f_ok = mbar_wait_bounded(&bar[0], 0, kAdjWaitNs);
+  if (__syncthreads_or(!f_ok)) {
+    if (tid == 0) {
+      atomicOr(p.status, PCLB_FLAG_TIMEOUT);
+      mbar_wait_bounded(&bar[0], 0, kAdjWaitNs);
+      mbar_wait_bounded(&bar[1], 0, kAdjWaitNs);
+    }
     return;
   }
 
@@ -212,6 +200,28 @@ __global__ void __launch_bounds__(AdjTile<T>::TT * 32, 1)
   if (outer && rowl == 1 && lane < TT && t0 + lane < p.n_theta)
     fill_ghost_columns<T, PLANE>(sf, 2 + lane, 1, cw_out, t0 + lane, p, d);
   __syncthreads();
+
+  // this thread's node moments (f only), while lam is still landing
+  const int row = 2 + rowl;
+  const int col = kLeft + lane;
+  const int t = t0 + rowl;
+  const int r = r0 + lane;
+  const bool valid = r < p.n_r && t < p.n_theta;
+  const int srow = t + kGhostRows;
+  T n_rho = T(1), n_ux = T(0), n_uy = T(0), n_E = T(1);
+  if (valid) {
+    bool ok;
+    adj_node_state(sf + row * kWinR + col, PLANE, d, n_rho, n_ux, n_uy, n_E, ok);
+    if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
+  }
+  const bool l_ok = mbar_wait_bounded(&bar[1], 0, kAdjWaitNs);
+  if (__syncthreads_or(!l_ok)) {
+    if (tid == 0) {
+      atomicOr(p.status, PCLB_FLAG_TIMEOUT);
+      mbar_wait_bounded(&bar[1], 0, kAdjWaitNs);
+    }
+    return;
+  }
 
   // ---- cotangent returned by the ghost nodes to the two wall nodes ---------
   auto wall_feedback = [&](int side, int rl) {
@@ -280,25 +290,14 @@ __global__ void __launch_bounds__(AdjTile<T>::TT * 32, 1)
   if (inner && rowl == 0 && lane < TT && t0 + lane < p.n_theta) wall_feedback(0, lane);
   if (outer && rowl == 1 && lane < TT && t0 + lane < p.n_theta) wall_feedback(1, lane);
 
-  // ---- this thread's node ----------------------------------------------------
-  const int row = 2 + rowl;
-  const int col = kLeft + lane;
-  const int t = t0 + rowl;
-  const int r = r0 + lane;
-  const bool valid = r < p.n_r && t < p.n_theta;
-  const int srow = t + kGhostRows;
-
+  // ---- this thread's node: cotangent of its equilibrium ----------------------
   T g[4] = {T(0), T(0), T(0), T(0)};
   if (valid) {
-    const NodeState<T> m = node_moments(sf + row * kWinR + col, PLANE, d);
-    if (!m.ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
     T G[4];
-    eq_cotangent<T>(m.rho, m.ux, m.uy, m.E, d,
-                    [&](int q) -> T { return sl[q * PLANE + row * kWinR + col]; }, G);
-    to_moment_cotangent<T>(m.rho, m.ux, m.uy, m.E, G, g);
+    eq_cotangent<T>(n_rho, n_ux, n_uy, n_E, d, [&](int q) -> T { return sl[q * PLANE + row * kWinR + col]; }, G);
+    to_moment_cotangent<T>(n_rho, n_ux, n_uy, n_E, G, g);
   }
   __syncthreads();   // wall feedback ready
-  if (!valid) return;
   // gs = (1 - d) g + g_wall: every label receives psi_q . gs
   const T decay = (T)p.decay;
   T gs[4];
@@ -312,7 +311,6 @@ __global__ void __launch_bounds__(AdjTile<T>::TT * 32, 1)
     gs[j] = (T(1) - decay) * g[j] + w;
   }
 
-  const T inv_r = (T)p.inv_r[r];
   const size_t plane_out = (size_t)p.rows * p.pitch;
   const int win = row * kWinR + col;
   auto store = [&](int q, T v) {
@@ -322,37 +320,113 @@ __global__ void __launch_bounds__(AdjTile<T>::TT * 32, 1)
     if (t < 2) lam_out[(size_t)d.recv_hi[q] * plane_out + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r] = v;
   };
   // rest velocity: no convection
-  store(0, decay * sl[win] + gs[0] + gs[3] * d.half_v2[0]);
+  if (valid) store(0, decay * sl[win] + gs[0] + gs[3] * d.half_v2[0]);
 
-  const CourEntry<T>* crow = ctab + rowl * AdjSize<T>::npairs;   // stored row srow - 2
+  constexpr int NP = AdjSize<T>::npairs, RC = AdjSize<T>::rcols, PROD = AdjSize<T>::prod;
+  // offsets inside one label's products
+  constexpr int AR = 0, BR = TT * RC, AT = 2 * TT * RC, BT = 2 * TT * RC + (TT + 4) * kTileR;
 #pragma unroll 1
-  for (int pair = 0; pair < AdjSize<T>::npairs; ++pair) {
+  for (int pair = 0; pair < NP; ++pair) {
     const int k = 1 + pair / (kNDirs / 2);
-    const int q = 1 + (k - 1) * kNDirs + pair % (kNDirs / 2);
-    const int q2 = q + kNDirs / 2;                       // opposite velocity
-    // theta Courant numbers of the five rows o = -2..2 at this radius; flag
-    // bits of the first label (the second has the opposite signs)
-    T at[5], kt[5];
-    int vt_neg = 0;
-#pragma unroll
-    for (int o = 0; o < 5; ++o) {
-      const CourEntry<T> e = crow[o * AdjSize<T>::npairs + pair];
-      at[o] = e.a_w * inv_r;
-      kt[o] = at[o] - at[o] * at[o];
-      vt_neg |= ((e.fl >> 1) & 1) << o;
+    const int q1 = 1 + (k - 1) * kNDirs + pair % (kNDirs / 2);
+    const int q2 = q1 + kNDirs / 2;                      // opposite velocity
+    T* pb = prod + (pair & 1) * 2 * PROD;                // this pair's buffer: [label][products]
+
+    // (A) products lam(n) M_D(n), lam(n) M_Dp(n) of every node that can reach the
+    // tile.  Warp w forms those of tile row w at its 32 columns (both labels),
+    // lanes 0..3 the two halo columns of each label on its upwind side, and
+    // warps 0..3 the halo rows -2, -1, TT, TT + 1 for the label whose upwind
+    // side points into the tile.
+    {
+      const CourEntry<T> e = ctab[row * NP + pair];
+      auto radial = [&](int L, int uL, int c) {
+        const int o = row * kWinR + c + kLeft;
+        const T* fw = sf + (L ? q2 : q1) * PLANE + o;
+        T MD, MP;
+        mwb_partials<T>(e.a_r, e.k_r, fw[0] - fw[uL], fw[uL] - fw[2 * uL], MD, MP);
+        const T lam = sl[(L ? q2 : q1) * PLANE + o];
+        pb[L * PROD + AR + rowl * RC + c + 2] = lam * MD;
+        pb[L * PROD + BR + rowl * RC + c + 2] = lam * MP;
+      };
+      auto azimuthal = [&](int L, int uL, int rr, T at, T kt) {
+        const int o = rr * kWinR + lane + kLeft;
+        const T* fw = sf + (L ? q2 : q1) * PLANE + o;
+        T MD, MP;
+        mwb_partials<T>(at, kt, fw[0] - fw[uL * kWinR], fw[uL * kWinR] - fw[2 * uL * kWinR], MD, MP);
+        const T lam = sl[(L ? q2 : q1) * PLANE + o];
+        pb[L * PROD + AT + rr * kTileR + lane] = lam * MD;
+        pb[L * PROD + BT + rr * kTileR + lane] = lam * MP;
+      };
+      const int u = (e.fl & 1) ? 1 : -1;                 // radial upwind offset of q1 in this row
+      const int un = (e.fl & 2) ? 1 : -1;                // azimuthal upwind offset of q1 in this row
+      radial(0, u, lane);
+      radial(1, -u, lane);
+      const T at = e.a_w * invr[lane], kt = at - at * at;
+      azimuthal(0, un, row, at, kt);
+      azimuthal(1, -un, row, at, kt);
+      if (rowl < 4) {
+        // halo rows: warps 0..3 take window rows 0, 1, TT + 2, TT + 3
+        const int rr = rowl < 2 ? rowl : TT + rowl;
+        const CourEntry<T> eh = ctab[rr * NP + pair];
+        const int unh = (eh.fl & 2) ? 1 : -1;
+        const int need = rr < 2 ? 1 : -1;
+        const T ath = eh.a_w * invr[lane], kth = ath - ath * ath;
+        azimuthal(unh == need ? 0 : 1, need, rr, ath, kth);
+      }
+      // halo columns: 4 per tile row (label, column); the warps after the first
+      // four take them, or warp 0 as well when the tile has too few rows.
+      // Upwind at larger r (+1) reads the tile from columns -2, -1, at
+      // smaller r from 32, 33.
+      constexpr int HW = (4 * TT + 31) / 32;
+      constexpr bool kSep = TT >= 4 + HW;
+      if (kSep ? (rowl >= 4 && rowl < 4 + HW) : rowl < HW) {
+        const int h = (kSep ? rowl - 4 : rowl) * 32 + lane;
+        if (h < 4 * TT) {
+          const int hr = h >> 2, L = (h >> 1) & 1, j = h & 1;
+          const CourEntry<T> eh = ctab[(hr + 2) * NP + pair];
+          const int uh = (eh.fl & 1) ? 1 : -1, uL = L ? -uh : uh;
+          const int c = uL == 1 ? j - 2 : kTileR + j;
+          const int o = (hr + 2) * kWinR + c + kLeft;
+          const T* fw = sf + (L ? q2 : q1) * PLANE + o;
+          T MD, MP;
+          mwb_partials<T>(eh.a_r, eh.k_r, fw[0] - fw[uL], fw[uL] - fw[2 * uL], MD, MP);
+          const T lam = sl[(L ? q2 : q1) * PLANE + o];
+          pb[L * PROD + AR + hr * RC + c + 2] = lam * MD;
+          pb[L * PROD + BR + hr * RC + c + 2] = lam * MP;
+        }
+      }
     }
-    const CourEntry<T> e0 = crow[2 * AdjSize<T>::npairs + pair];
-    const int ur = (e0.fl & 1) ? 1 : -1;          // radial upwind offset of the first label
-    const T A = gs[0] + gs[3] * d.half_v2[k];
-    const T B = gs[1] * d.vx[q] + gs[2] * d.vy[q];
-    const T* f1 = sf + q * PLANE + win;
-    const T* l1 = sl + q * PLANE + win;
-    const T* f2 = sf + q2 * PLANE + win;
-    const T* l2 = sl + q2 * PLANE + win;
-    const T c1 = adjoint_stencil<T>(f1, l1, ur, e0.a_r, e0.k_r, at, kt, vt_neg);
-    const T c2 = adjoint_stencil<T>(f2, l2, -ur, e0.a_r, e0.k_r, at, kt, vt_neg ^ 0x1f);
-    store(q, decay * l1[0] + A + B - c1);
-    store(q2, decay * l2[0] + A - B - c2);
+    __syncthreads();
+
+    // (B) gather at this node: node n = c + j u_n reads f(n), f(n + u_n),
+    // f(n + 2 u_n), so dM(n)/df(n) = M_D, dM(n)/df(n + u_n) = M_Dp - M_D,
+    // dM(n)/df(n + 2 u_n) = -M_Dp.
+    if (valid) {
+      const CourEntry<T>* cr = ctab + rowl * NP + pair;  // rows rowl - 2 .. rowl + 2 at stride NP
+      const int u = (cr[2 * NP].fl & 1) ? 1 : -1;
+      int tneg = 0;                                       // bit o: row o - 2 has v_theta < 0 for q1
+#pragma unroll
+      for (int o = 0; o < 5; ++o) tneg |= ((cr[o * NP].fl >> 1) & 1) << o;
+      const T A = gs[0] + gs[3] * d.half_v2[k];
+      const T B = gs[1] * d.vx[q1] + gs[2] * d.vy[q1];
+#pragma unroll
+      for (int L = 0; L < 2; ++L) {
+        const T* P = pb + L * PROD;
+        const int uL = L ? -u : u;
+        const int neg = L ? (tneg ^ 0x1f) : tneg;        // the partner has the opposite velocity
+        const int cc = lane + 2;
+        T acc = P[AR + rowl * RC + cc] - P[AR + rowl * RC + cc - uL] + P[BR + rowl * RC + cc - uL] -
+                P[BR + rowl * RC + cc - 2 * uL];
+        const int rr = rowl + 2;
+        acc += P[AT + rr * kTileR + lane];
+        if (neg & 2) acc += P[BT + (rr - 1) * kTileR + lane] - P[AT + (rr - 1) * kTileR + lane];
+        if (!(neg & 8)) acc += P[BT + (rr + 1) * kTileR + lane] - P[AT + (rr + 1) * kTileR + lane];
+        if (neg & 1) acc -= P[BT + (rr - 2) * kTileR + lane];
+        if (!(neg & 16)) acc -= P[BT + (rr + 2) * kTileR + lane];
+        const int q = L ? q2 : q1;
+        store(q, decay * sl[q * PLANE + win] + (L ? A - B : A + B) - acc);
+      }
+    }
   }
 }
 

@@ -29,7 +29,7 @@ constexpr int kStepThreads = 256;   // 8 warps; each thread owns 2 nodes (rows w
 constexpr int kPitchAlign = 32;     // row pitch in elements (128 B for float)
 constexpr int kGhostRows = 2;       // azimuthal ghost rows stored on each side
 // Tile rows of the adjoint kernel (its window holds f and lam for all labels).
-constexpr int kAdjRows32 = 8;
+constexpr int kAdjRows32 = 12;
 constexpr int kAdjRows64 = 4;
 
 // Per-velocity constants, in the arithmetic type T of the kernel, plus the
