@@ -12,6 +12,8 @@ Prints ONE JSON line.  Keys beyond the base contract:
   fp64          the same workload through the FP64 path (value + roofline)
   adjoint       the FP32 adjoint step on the same workload, its ratio to the
                 forward step, and one reverse step with recompute
+  noneq         the non-equilibrium moments and departures of Sec. IV (all
+                four groups, 48 fields) on the same workload
   e2e           the metric through pclb_run_host with page-locked host buffers
   clocks        SM clocks / throttle reasons sampled during the timed region
 
@@ -332,6 +334,29 @@ def run_ours(args):
                                 "frac": alg / t_adj / 1e9 / hbm, "alg_bytes_per_launch": alg,
                                 "kernel": "pclb::adjoint_kernel<float>"}}
         del state
+
+    # non-equilibrium manifestations (Sec. IV), all four groups, on the same state
+    noneq = None
+    if not args.no_noneq:
+        g.set_state()
+        g.step(1)
+        out = g.noneq(15)
+        g.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        kn = max(3, min(args.steps, 10))
+        e0.record(g.stream)
+        for _ in range(kn):
+            g.noneq(15, out=out)
+        e1.record(g.stream)
+        e1.synchronize()
+        t_n = e0.elapsed_time(e1) / 1e3 / kn
+        nbytes = cells * (Q + 48) * 4.0     # read f, write 4 groups x 12 fields
+        noneq = {"ms": t_n * 1e3, "groups": 4, "fields": 48,
+                 "roofline": {"bound": "hbm", "achieved": nbytes / t_n / 1e9, "peak": hbm, "unit": "GB/s",
+                              "frac": nbytes / t_n / 1e9 / hbm, "alg_bytes_per_launch": nbytes,
+                              "kernel": "pclb::noneq_kernel<float>"}}
+        del out
     g.close()
 
     # FP64 step on the same workload
@@ -376,6 +401,8 @@ def run_ours(args):
         line["fp64"] = fp64
     if adjoint is not None:
         line["adjoint"] = adjoint
+    if noneq is not None:
+        line["noneq"] = noneq
     if clk is not None:
         line["clocks"] = clk
     if not args.no_cpu_baseline and ws == 1:
@@ -428,6 +455,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-noneq", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

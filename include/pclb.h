@@ -170,6 +170,24 @@ pclb_status pclb_step(pclb_ctx* ctx, int32_t n);
  * [n_theta][n_r], context precision; any pointer may be NULL. */
 pclb_status pclb_moments(pclb_ctx* ctx, void* rho, void* u_r, void* u_theta, void* T);
 
+/* Non-equilibrium manifestations of the current state (Sec. IV).  At every
+ * node, with c = v (plain) or c = v - u (central, u the node's velocity) in
+ * polar components at the node, and w = f (moments) or w = f - f^eq
+ * (departures, f^eq the equilibrium of Eq. 10 at the node's own moments):
+ *   M_2 = sum w c c, M_3 = sum w c c c, M_{3,1} = sum w (c.c/2) c,
+ *   M_{4,2} = sum w (c.c/2) c c.
+ * groups: bitwise OR of PCLB_NEQ_* (1..15).  out: device, context precision,
+ * [n_groups x 12][n_theta][n_r], the selected groups in bit order, each as
+ * 12 fields: M_2 rr, r theta, theta theta; M_3 rrr, rr theta, r theta theta,
+ * theta theta theta; M_{3,1} r, theta; M_{4,2} rr, r theta, theta theta.
+ * Errors: PCLB_EINVAL (groups out of range, out NULL), PCLB_ESTATE (no
+ * state). */
+#define PCLB_NEQ_M 1      /* M_m(f) */
+#define PCLB_NEQ_DELTA 2  /* Delta_m = M_m(f - f^eq) */
+#define PCLB_NEQ_MSTAR 4  /* M*_m(f), central */
+#define PCLB_NEQ_DSTAR 8  /* Delta*_m = M*_m(f - f^eq) */
+pclb_status pclb_noneq(pclb_ctx* ctx, int32_t groups, void* out);
+
 /* Global integrals of the current state with the area element r dr dtheta,
  * summed in double: out[0] mass, out[1] x-momentum, out[2] y-momentum,
  * out[3] total energy (rho (E + u^2/2)), out[4] min rho, out[5] min T,

@@ -69,7 +69,7 @@ def lib():
             L.orc_mwb_increment.argtypes = [ctypes.c_double] * 6
             for name in ("orc_step", "orc_run", "orc_set_state", "orc_fields", "orc_diagnostics",
                          "orc_step_jvp", "orc_adjoint_step", "orc_set_state_jvp", "orc_fields_jvp",
-                         "orc_step_nodes", "orc_adjoint_entries"):
+                         "orc_step_nodes", "orc_adjoint_entries", "orc_noneq"):
                 getattr(L, name).restype = ctypes.c_int
         return _lib
 
@@ -275,4 +275,20 @@ def adjoint_entries(w, f_n, lam_np1, q, it, ir, prob=None):
     out = np.zeros(len(q))
     _check(lib().orc_adjoint_entries(prob.ref, _ptr(f_n), _ptr(lam), ctypes.c_int(len(q)), q.ctypes.data_as(_ip),
                                      it.ctypes.data_as(_ip), ir.ctypes.data_as(_ip), _ptr(out)), "adjoint_entries")
+    return out
+
+
+NEQ_M, NEQ_DELTA, NEQ_MSTAR, NEQ_DSTAR = 1, 2, 4, 8
+NEQ_COMPONENTS = ("2rr", "2rt", "2tt", "3rrr", "3rrt", "3rtt", "3ttt", "31r", "31t", "42rr", "42rt", "42tt")
+
+
+def noneq(w, f, groups=15, prob=None):
+    """Non-equilibrium manifestations of Sec. IV: for each selected group (bit
+    0: M_m(f), 1: Delta_m, 2: M*_m(f), 3: Delta*_m) the 12 polar components
+    of M_2, M_3, M_{3,1}, M_{4,2}; returns [n_groups, 12, n_theta, n_r]."""
+    prob = prob or Problem(w)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    ng = bin(int(groups)).count("1")
+    out = np.zeros((ng, 12, w.n_theta, w.n_r))
+    _check(lib().orc_noneq(prob.ref, _ptr(f), ctypes.c_int(int(groups)), _ptr(out)), "noneq")
     return out

@@ -18,6 +18,10 @@
 //     function S(eta) of Eq. (37), in r and in theta;
 //   * the radial ghost nodes of Sec. II C 1 (Eq. 39, ghost f = f^eq) and the
 //     azimuthal ghost nodes of Sec. II C 2 (Eq. 40, index rotation).
+//   * the non-equilibrium manifestations of Sec. IV: the moments M_2, M_3,
+//     M_{3,1}, M_{4,2} of f and their central counterparts M*_m (velocities
+//     relative to the local flow velocity), and the departures
+//     Delta_m = M_m(f - f^eq), Delta*_m = M*_m(f - f^eq);
 //   * the vector-Jacobian product of that step (the adjoint step), by its
 //     plain definition: forward-mode derivatives column by column, each
 //     dotted with the cotangent.
@@ -597,6 +601,68 @@ int orc_diagnostics(const orc_problem* P, const double* f, double* out) {
     }
   out[0] = m; out[1] = jx; out[2] = jy; out[3] = e; out[4] = rmin; out[5] = tmin;
   return 0;
+}
+
+// Non-equilibrium manifestations, Sec. IV.  For weights w_q (f, or f - f^eq)
+// and velocities c_q (v_q, or v_q - u for the central moments), in polar
+// components at the node (c_r = c . e_r, c_theta = c . e_theta):
+//   M_2     = sum w c c                 -> rr, r theta, theta theta
+//   M_3     = sum w c c c               -> rrr, rr theta, r theta theta, theta theta theta
+//   M_{3,1} = sum w (c . c / 2) c       -> r, theta
+//   M_{4,2} = sum w (c . c / 2) c c     -> rr, r theta, theta theta
+// Group g (bit 0: M_m(f), bit 1: Delta_m, bit 2: M*_m(f), bit 3: Delta*_m)
+// fills 12 fields [12][n_theta][n_r] of out, groups in bit order.
+int orc_noneq(const orc_problem* P, const double* f, int groups, double* out) {
+  if (!valid(P) || groups <= 0 || groups > 15) return ORC_EINVAL;
+  Dvm d = make_dvm(P->n_dirs, P->speeds, P->B);
+  const int NR = P->n_r, NT = P->n_theta, Q = d.Q;
+  const double dth = 2.0 * M_PI * P->n_f / (double(P->n_dirs) * NT);
+  const size_t plane = (size_t)NT * NR;
+  int status = 0;
+#pragma omp parallel for schedule(static) reduction(| : status)
+  for (int it = 0; it < NT; ++it) {
+    const double theta = (it + 1) * dth;
+    const double cs = std::cos(theta), sn = std::sin(theta);
+    std::vector<double> fe(Q);
+    for (int ir = 0; ir < NR; ++ir) {
+      const size_t n = (size_t)it * NR + ir;
+      double rho, ux, uy, E;
+      moments_node(d, f + n, (long)plane, rho, ux, uy, E);
+      if (!(rho > 0 && E > 0)) status |= ORC_NONPHYS;
+      feq_node(d, rho, ux, uy, E, fe.data());
+      const double u_r = ux * cs + uy * sn, u_t = -ux * sn + uy * cs;
+      int slot = 0;
+      for (int g = 0; g < 4; ++g) {
+        if (!(groups & (1 << g))) continue;
+        const bool departure = g == 1 || g == 3, central = g >= 2;
+        double m[12] = {0};
+        for (int q = 0; q < Q; ++q) {
+          const double w = departure ? f[q * plane + n] - fe[q] : f[q * plane + n];
+          double cr = d.vx[q] * cs + d.vy[q] * sn, ct = -d.vx[q] * sn + d.vy[q] * cs;
+          if (central) {
+            cr -= u_r;
+            ct -= u_t;
+          }
+          const double h = 0.5 * (cr * cr + ct * ct);
+          m[0] += w * cr * cr;
+          m[1] += w * cr * ct;
+          m[2] += w * ct * ct;
+          m[3] += w * cr * cr * cr;
+          m[4] += w * cr * cr * ct;
+          m[5] += w * cr * ct * ct;
+          m[6] += w * ct * ct * ct;
+          m[7] += w * h * cr;
+          m[8] += w * h * ct;
+          m[9] += w * h * cr * cr;
+          m[10] += w * h * cr * ct;
+          m[11] += w * h * ct * ct;
+        }
+        for (int c = 0; c < 12; ++c) out[((size_t)(slot * 12 + c)) * plane + n] = m[c];
+        ++slot;
+      }
+    }
+  }
+  return status;
 }
 
 // One step of Eq. (38).  f_in, f_out: [Q][n_theta][n_r].

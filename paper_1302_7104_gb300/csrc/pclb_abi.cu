@@ -34,6 +34,8 @@ template <class T>
 cudaError_t launch_diagnostics(const T*, double*, double*, const StepParams&, const DvmConst<T>&,
                                double, double, double, cudaStream_t);
 template <class T>
+cudaError_t launch_noneq(const T*, T*, int, const StepParams&, const DvmConst<T>&, cudaStream_t);
+template <class T>
 cudaError_t launch_adjoint(const CUtensorMap*, const CUtensorMap*, T*, const StepParams&, const DvmConst<T>&,
                            cudaStream_t);
 template <class T>
@@ -569,6 +571,20 @@ pclb_status pclb_moments(pclb_ctx* ctx, void* rho, void* u_r, void* u_theta, voi
     e = launch_moments<double>(fbuf<double>(ctx, ctx->cur), (double*)rho, (double*)u_r, (double*)u_theta,
                                (double*)T, ctx->sp, ctx->dvm64, ctx->stream);
   return check_launch(ctx, e, "moments kernel launch");
+}
+
+pclb_status pclb_noneq(pclb_ctx* ctx, int32_t groups, void* out) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (groups < 1 || groups > 15) return fail(ctx, PCLB_EINVAL, "groups = %d must be in 1..15", (int)groups);
+  if (!out) return fail(ctx, PCLB_EINVAL, "out must not be NULL");
+  if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
+  cudaError_t e;
+  if (ctx->prec == PCLB_FP32)
+    e = launch_noneq<float>(fbuf<float>(ctx, ctx->cur), (float*)out, groups, ctx->sp, ctx->dvm32, ctx->stream);
+  else
+    e = launch_noneq<double>(fbuf<double>(ctx, ctx->cur), (double*)out, groups, ctx->sp, ctx->dvm64,
+                             ctx->stream);
+  return check_launch(ctx, e, "noneq kernel launch");
 }
 
 pclb_status pclb_diagnostics(pclb_ctx* ctx, double* out) {

@@ -24,6 +24,11 @@ STATUS = {0: "PCLB_OK", 1: "PCLB_EINVAL", 2: "PCLB_ENOMEM", 3: "PCLB_ECUDA", 4: 
 FLAG_NONPHYS, FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2, 4
 
 
+# groups of pclb_noneq and the order of its 12 components per group
+NEQ_M, NEQ_DELTA, NEQ_MSTAR, NEQ_DSTAR = 1, 2, 4, 8
+NEQ_COMPONENTS = ("2rr", "2rt", "2tt", "3rrr", "3rrt", "3rtt", "3ttt", "31r", "31t", "42rr", "42rt", "42tt")
+
+
 class PCLBError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
@@ -59,6 +64,7 @@ _SIGS = {
     "pclb_get_f": (ctypes.c_int, [_vp, _vp]),
     "pclb_step": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "pclb_moments": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "pclb_noneq": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
     "pclb_diagnostics": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "pclb_status_flags": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int32]),
     "pclb_sync": (ctypes.c_int, [_vp, ctypes.c_int32]),
@@ -224,6 +230,18 @@ class PCLB:
         outs = list(out) if out is not None else [self.empty_field() for _ in range(4)]
         _check(lib().pclb_moments(self.ctx, *[_vp(_ptr(t)) for t in outs]), self.ctx)
         return tuple(outs)
+
+    def noneq(self, groups: int = NEQ_M | NEQ_DELTA | NEQ_MSTAR | NEQ_DSTAR, out=None):
+        """Non-equilibrium manifestations of the current state (Sec. IV):
+        [n_groups, 12, n_theta, n_r] device tensor of the context's dtype,
+        groups in bit order (NEQ_M, NEQ_DELTA, NEQ_MSTAR, NEQ_DSTAR), the 12
+        polar components in the order of NEQ_COMPONENTS."""
+        torch = _torch()
+        ng = bin(int(groups) & 15).count("1")
+        if out is None:
+            out = torch.empty((ng, 12, self.n_theta, self.n_r), dtype=self.dtype, device=self.device)
+        _check(lib().pclb_noneq(self.ctx, int(groups), _vp(out.data_ptr())), self.ctx)
+        return out
 
     def diagnostics(self) -> np.ndarray:
         out = (ctypes.c_double * 8)()
