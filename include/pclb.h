@@ -81,6 +81,12 @@ typedef enum {
   PCLB_BC_WALL = 1,      /* rho, T extrapolated; u_r, u_theta prescribed at the ghost nodes */
   PCLB_BC_DIRICHLET = 2  /* rho, u_r, u_theta, T prescribed at the ghost nodes */
 } pclb_bc_kind;
+/* Flag added to a kind: the ghost nodes carry, besides f^eq of their
+ * macroscopic state, the departure f - f^eq of the wall node (the
+ * non-equilibrium microscopic boundary of Sec. II C 1, in the form of the
+ * extrapolation scheme it cites: the non-equilibrium part of the nearest
+ * fluid node).  The adjoint entry points refuse it (PCLB_EUNSUPPORTED). */
+#define PCLB_BC_NEQ 8
 
 /* Device status bits accumulated by the kernels (pclb_status_flags). */
 #define PCLB_FLAG_NONPHYS 1u   /* rho <= 0 or T <= 0 at a node or ghost node */

@@ -35,7 +35,9 @@
 //   * the derivative of |x| at x = 0 is taken as 0 (active-branch convention);
 //   * ghost nodes: rho and T extrapolated by Eq. (39), applied twice for the
 //     outer ghost layer; u extrapolated the same way (BC kind 0), prescribed
-//     (kind 1), or everything prescribed (kind 2).
+//     (kind 1), or everything prescribed (kind 2); f = f^eq there, or with
+//     the flag 8 added to the kind, f^eq plus the non-equilibrium part
+//     f - f^eq of the wall node.
 //
 // Parity pins for every function here live in tests/test_oracle_*.py.
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -fopenmp -shared -fPIC.
@@ -231,7 +233,11 @@ namespace {
 // Ghost nodes of one theta row at one wall, Sec. II C 1: macroscopic
 // quantities from Eq. (39) (or prescribed), f = f^eq there.  fa, fb: the Q
 // values at the wall node (i_r = 1 or N_r) and the next node inward; fe1,
-// fe2: f^eq at the adjacent and the outer ghost node.
+// fe2: f at the adjacent and the outer ghost node.  With the non-equilibrium
+// flag (kind & 8) the ghost nodes also carry the departure f - f^eq of the
+// wall node (the non-equilibrium microscopic boundary of Sec. II C 1, in the
+// form of the cited extrapolation scheme: the non-equilibrium part of the
+// nearest fluid node is copied to the boundary).
 template <class T>
 int radial_ghost_layers(const orc_problem& P, const Dvm& d, int it, int side, const T* fa, const T* fb, T* fe1,
                         T* fe2) {
@@ -246,7 +252,8 @@ int radial_ghost_layers(const orc_problem& P, const Dvm& d, int it, int side, co
   T E1 = 2.0 * Ea - Eb, E2 = 2.0 * E1 - Ea;         // "temperature in a similar way"
   T ux1 = 2.0 * uxa - uxb, ux2 = 2.0 * ux1 - uxa;
   T uy1 = 2.0 * uya - uyb, uy2 = 2.0 * uy1 - uya;
-  const int kind = P.bc_kind[side];
+  const int kind = P.bc_kind[side] & 3;
+  const bool neq = (P.bc_kind[side] & 8) != 0;
   const double* V = P.bc_values[side];
   auto given = [&](int layer, int field) { return V[((size_t)layer * 4 + field) * NT + it]; };
   if (kind == 1 || kind == 2) {  // prescribed polar velocity at the ghost nodes
@@ -263,6 +270,15 @@ int radial_ghost_layers(const orc_problem& P, const Dvm& d, int it, int side, co
   if (!(val(rho1) > 0 && val(rho2) > 0 && val(E1) > 0 && val(E2) > 0)) status |= ORC_NONPHYS;
   feq_node(d, rho1, ux1, uy1, E1, fe1);
   feq_node(d, rho2, ux2, uy2, E2, fe2);
+  if (neq) {
+    std::vector<T> ea(d.Q);
+    feq_node(d, ra, uxa, uya, Ea, ea.data());
+    for (int q = 0; q < d.Q; ++q) {
+      const T na = fa[q] - ea[q];
+      fe1[q] = fe1[q] + na;
+      fe2[q] = fe2[q] + na;
+    }
+  }
   return status;
 }
 
@@ -438,8 +454,10 @@ bool valid(const orc_problem* P) {
   if (P->n_r < 3 || P->n_theta < 2) return false;
   if (P->n_dirs < 1 || P->n_f < 1 || P->n_f > P->n_dirs) return false;
   if (!(P->r_out > P->r_in) || !(P->r_in > 0) || !(P->tau > 0) || !(P->dt > 0)) return false;
-  for (int s = 0; s < 2; ++s)
-    if (P->bc_kind[s] != 0 && P->bc_values[s] == nullptr) return false;
+  for (int s = 0; s < 2; ++s) {
+    if ((P->bc_kind[s] & ~(3 | 8)) != 0 || (P->bc_kind[s] & 3) == 3) return false;
+    if ((P->bc_kind[s] & 3) != 0 && P->bc_values[s] == nullptr) return false;
+  }
   return true;
 }
 

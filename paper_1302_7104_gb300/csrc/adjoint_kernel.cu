@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(AdjTile<T>::TT * 32, 1)
     const int outward = -step;                          // upwind offset that reads the ghosts
     const NodeState<T> a = node_moments(sf + row * kWinR + ca, PLANE, d);
     const NodeState<T> b = node_moments(sf + row * kWinR + cb, PLANE, d);
-    const int kind = p.bc_kind[side];
+    const int kind = p.bc_kind[side] & ~PCLB_BC_NEQ;
     T st[2][4];   // ghost states (rho, ux, uy, E), layers 0 and 1
     st[0][0] = T(2) * a.rho - b.rho;  st[1][0] = T(2) * st[0][0] - a.rho;
     st[0][1] = T(2) * a.ux - b.ux;    st[1][1] = T(2) * st[0][1] - a.ux;

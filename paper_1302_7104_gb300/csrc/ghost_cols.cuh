@@ -25,7 +25,8 @@ __device__ void fill_ghost_columns(T* sm, int row, int side, int cw, int t, cons
   E[0] = 2.0 * a.E_d - b.E_d;        E[1] = 2.0 * E[0] - a.E_d;
   ux[0] = T(2) * a.ux - b.ux;        ux[1] = T(2) * ux[0] - a.ux;
   uy[0] = T(2) * a.uy - b.uy;        uy[1] = T(2) * uy[0] - a.uy;
-  const int kind = p.bc_kind[side];
+  const int kind = p.bc_kind[side] & ~PCLB_BC_NEQ;
+  const bool neq = (p.bc_kind[side] & PCLB_BC_NEQ) != 0;
   if (kind != PCLB_BC_EXTRAP) {
     const double c = p.cos_t[t], s = p.sin_t[t];
     for (int layer = 0; layer < 2; ++layer) {
@@ -40,6 +41,8 @@ __device__ void fill_ghost_columns(T* sm, int row, int side, int cw, int t, cons
     }
   }
   bool ok = a.ok && b.ok;
+  // equilibrium of the wall node, for the departure it hands to its ghosts
+  const EqParams<T> ea = eq_params<T>(a.rho_d, a.ux, a.uy, a.E_d, d);
   for (int layer = 0; layer < 2; ++layer) {
     ok = ok && rho[layer] > 0.0 && E[layer] > 0.0;
     const int col = cw - step * (1 + layer);
@@ -51,7 +54,11 @@ __device__ void fill_ghost_columns(T* sm, int row, int side, int cw, int t, cons
       const int q_begin = k == 0 ? 0 : 1 + (k - 1) * kNDirs;
       const int q_end = k == 0 ? 1 : q_begin + kNDirs;
 #pragma unroll 1
-      for (int q = q_begin; q < q_end; ++q) g[q * PLANE] = feq_q<T>(e, d.vx[q], d.vy[q], k);
+      for (int q = q_begin; q < q_end; ++q) {
+        T v = feq_q<T>(e, d.vx[q], d.vy[q], k);
+        if (neq) v += fa[q * PLANE] - feq_q<T>(ea, d.vx[q], d.vy[q], k);
+        g[q * PLANE] = v;
+      }
     }
   }
   if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);

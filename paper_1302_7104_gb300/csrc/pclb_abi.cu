@@ -349,9 +349,10 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, PCLB_EINVAL, "dt must be positive (got %g)", dt);
   if (!bc) return fail(nullptr, PCLB_EINVAL, "bc must not be NULL");
   for (int s = 0; s < 2; ++s) {
-    if (bc->kind[s] < PCLB_BC_EXTRAP || bc->kind[s] > PCLB_BC_DIRICHLET)
+    const int base = bc->kind[s] & ~PCLB_BC_NEQ;
+    if (base < PCLB_BC_EXTRAP || base > PCLB_BC_DIRICHLET)
       return fail(nullptr, PCLB_EINVAL, "bc kind[%d] = %d is unknown", s, bc->kind[s]);
-    if (bc->kind[s] != PCLB_BC_EXTRAP && !bc->values[s])
+    if (base != PCLB_BC_EXTRAP && !bc->values[s])
       return fail(nullptr, PCLB_EINVAL, "bc values[%d] must be given for kind %d", s, bc->kind[s]);
   }
   if (!workspace) return fail(nullptr, PCLB_EINVAL, "workspace must not be NULL");
@@ -389,8 +390,8 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
   ctx->prec = prec;
   ctx->tau = tau;
   ctx->dt = dt;
-  ctx->bc_kind[0] = (pclb_bc_kind)bc->kind[0];
-  ctx->bc_kind[1] = (pclb_bc_kind)bc->kind[1];
+  ctx->bc_kind[0] = bc->kind[0];
+  ctx->bc_kind[1] = bc->kind[1];
   ctx->stream = reinterpret_cast<cudaStream_t>(stream);
   ctx->ws = reinterpret_cast<unsigned char*>(workspace);
   ctx->lay = lay;
@@ -442,7 +443,7 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
   for (int r = 0; r < NR; ++r) ctx->inv_r_f[r] = (float)ctx->inv_r[r];
   ctx->bc_vals.assign((size_t)2 * 2 * 4 * NT, 0.0);
   for (int s = 0; s < 2; ++s)
-    if (bc->kind[s] != PCLB_BC_EXTRAP)
+    if ((bc->kind[s] & ~PCLB_BC_NEQ) != PCLB_BC_EXTRAP)
       std::memcpy(ctx->bc_vals.data() + (size_t)s * 2 * 4 * NT, bc->values[s], sizeof(double) * 2 * 4 * NT);
 
   StepParams& sp = ctx->sp;
@@ -705,8 +706,16 @@ pclb_status pclb_lambda_get(pclb_ctx* ctx, void* lam) {
   return e == cudaSuccess ? PCLB_OK : cuda_fail(ctx, e, "lambda pack launch");
 }
 
+// The adjoint differentiates the ghost nodes as f = f^eq of their state.
+static pclb_status adjoint_supported(pclb_ctx* ctx) {
+  if ((ctx->bc_kind[0] | ctx->bc_kind[1]) & PCLB_BC_NEQ)
+    return fail(ctx, PCLB_EUNSUPPORTED, "the adjoint does not support PCLB_BC_NEQ boundaries");
+  return PCLB_OK;
+}
+
 pclb_status pclb_adjoint_state(pclb_ctx* ctx, const void* f_state) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (adjoint_supported(ctx) != PCLB_OK) return PCLB_EUNSUPPORTED;
   if (!ctx->has_lam) return fail(ctx, PCLB_ESTATE, "no adjoint variable: call pclb_lambda_set or pclb_moments_vjp");
   const CUtensorMap* map;
   CUtensorMap local;
@@ -723,6 +732,7 @@ pclb_status pclb_adjoint_state(pclb_ctx* ctx, const void* f_state) {
 
 pclb_status pclb_adjoint_step(pclb_ctx* ctx, const void* f_n, const void* lam_np1, void* lam_n) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (adjoint_supported(ctx) != PCLB_OK) return PCLB_EUNSUPPORTED;
   if (!f_n || !lam_np1 || !lam_n) return fail(ctx, PCLB_EINVAL, "f_n, lam_np1 and lam_n must not be NULL");
   void* adj = ctx->ws + ctx->lay.adj_f;
   cudaError_t e = ctx->prec == PCLB_FP32

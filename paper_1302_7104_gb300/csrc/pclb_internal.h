@@ -110,7 +110,7 @@ struct pclb_ctx {
   pclb_dvm dvm;
   pclb_precision prec;
   double tau, dt;
-  pclb_bc_kind bc_kind[2];
+  int32_t bc_kind[2];   // pclb_bc_kind, possibly with PCLB_BC_NEQ
   cudaStream_t stream;
   unsigned char* ws;
   pclb::Layout lay;

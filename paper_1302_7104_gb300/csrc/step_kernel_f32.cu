@@ -172,7 +172,8 @@ __device__ __noinline__ void ghost_columns_f32(float* sm, int row, int side, int
   g[1].E = ff_add(ff_scale(g[0].E, 2.f), ff_neg(a.E));
   g[1].ux = ff_add(ff_scale(g[0].ux, 2.f), ff_neg(a.ux));
   g[1].uy = ff_add(ff_scale(g[0].uy, 2.f), ff_neg(a.uy));
-  const int kind = p.bc_kind[side];
+  const int kind = p.bc_kind[side] & ~PCLB_BC_NEQ;
+  const bool neq = (p.bc_kind[side] & PCLB_BC_NEQ) != 0;
   if (kind != PCLB_BC_EXTRAP) {
     const double c = p.cos_t[t], s = p.sin_t[t];
     for (int layer = 0; layer < 2; ++layer) {
@@ -187,20 +188,29 @@ __device__ __noinline__ void ghost_columns_f32(float* sm, int row, int side, int
     }
   }
   bool ok = a.ok && b.ok;
+  // equilibrium of the wall node, for the departure it hands to its ghosts
+  Eq32 ea{};
+  if (neq) ea = eq32(a, d);
+  const float* fa = sm + row * kWinR + cw;
   for (int layer = 0; layer < 2; ++layer) {
     ok = ok && g[layer].rho.hi > 0.f && g[layer].E.hi > 0.f;
     const int col = cw - step * (1 + layer);
     if (col < 0 || col >= kWinR) continue;
     const Eq32 e = eq32(g[layer], d);
     float* gp = sm + row * kWinR + col;
-    gp[0] = feq32(e, d, 0, 0, 1.f);
+    gp[0] = feq32(e, d, 0, 0, 1.f) + (neq ? fa[0] - feq32(ea, d, 0, 0, 1.f) : 0.f);
 #pragma unroll 1
     for (int k = 1; k <= 4; ++k)
 #pragma unroll
       for (int i = 0; i < kHalf; ++i) {
         const int q = 1 + (k - 1) * kNDirs + i;
-        gp[q * kPlaneF] = feq32(e, d, k, i, 1.f);
-        gp[(q + kHalf) * kPlaneF] = feq32(e, d, k, i, -1.f);
+        float v1 = feq32(e, d, k, i, 1.f), v2 = feq32(e, d, k, i, -1.f);
+        if (neq) {
+          v1 += fa[q * kPlaneF] - feq32(ea, d, k, i, 1.f);
+          v2 += fa[(q + kHalf) * kPlaneF] - feq32(ea, d, k, i, -1.f);
+        }
+        gp[q * kPlaneF] = v1;
+        gp[(q + kHalf) * kPlaneF] = v2;
       }
   }
   if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);

@@ -49,6 +49,7 @@ STABLE_CFL = 0.25
 BC_EXTRAP = 0     # rho, u, T linearly extrapolated (Eq. 39)
 BC_WALL = 1       # rho, T extrapolated; u prescribed at the ghost nodes
 BC_DIRICHLET = 2  # rho, u, T prescribed at the ghost nodes
+BC_NEQ = 8        # flag added to a kind: ghosts also carry the wall node's f - f^eq
 
 
 @dataclasses.dataclass
@@ -201,6 +202,47 @@ def rot(n_r: int = 32, n_theta: int = 64, steps: int = 200, cfl: float = STABLE_
     dt = dt_from_cfl(cfl, n_r, n_theta, r_in, r_out)
     return Workload("rot", n_r, n_theta, r_in, r_out, tau, dt, steps, rho, u_r, u_th, T,
                     bc_kind=(BC_DIRICHLET, BC_DIRICHLET), bc_values=tuple(vals))
+
+
+def taylor_couette(n_r: int = 100, n_theta: int = 20, steps: int = 20000, tau: float = 0.2, dt: float = 1e-3,
+                   omega_in: float = -0.1, omega_out: float = 0.1, r_in: float = 1.0, r_out: float = 2.0,
+                   n_f: int = 1, bc_kind: int = BC_WALL) -> Workload:
+    """Fluid between two coaxial cylinders rotating with angular velocities
+    omega_in (r = R1) and omega_out (r = R2), Sec. III A: at rest in
+    equilibrium at t = 0 with rho = 1, T = 1, on one sector (N_f = 1 of the
+    N_i = 8 parts) with the rotated-label azimuthal boundary of Eq. (40).  Both
+    radial boundaries are of kind ``bc_kind`` (WALL by default: rho and T
+    extrapolated, u prescribed at the ghost nodes) with the ghost nodes moving
+    with the cylinder, u_theta = omega r_ghost, u_r = 0.  The paper's run:
+    N_r x N_theta = 100 x 20, dt = 1e-3, tau in {0.2, 0.1, 0.05, 0.01}; the
+    steady state approaches u_theta = A r + B / r (``couette_profile``)."""
+    R, _ = _mesh(n_r, n_theta, r_in, r_out, 8, n_f)
+    rho = np.ones_like(R)
+    zero = np.zeros_like(R)
+    gin, gout = ghost_radii(n_r, r_in, r_out)
+    vals = []
+    for gr, om in ((gin, omega_in), (gout, omega_out)):
+        v = np.zeros((2, 4, n_theta))
+        for layer, rg in enumerate(gr):
+            v[layer, 0, :] = 1.0
+            v[layer, 2, :] = om * rg
+            v[layer, 3, :] = 1.0
+        vals.append(v)
+    w = Workload("taylor_couette", n_r, n_theta, r_in, r_out, tau, dt, steps, rho, zero, zero.copy(),
+                 np.ones_like(R), n_f=n_f, bc_kind=(bc_kind, bc_kind), bc_values=tuple(vals))
+    w.extra = {"omega_in": omega_in, "omega_out": omega_out}
+    return w
+
+
+def couette_profile(r, omega_in: float, omega_out: float, r_in: float, r_out: float):
+    """Steady azimuthal velocity between rotating cylinders, u = A r + B / r
+    with u(R1) = omega_in R1 and u(R2) = omega_out R2 (the no-slip
+    Navier-Stokes solution of Sec. III A)."""
+    d = r_out ** 2 - r_in ** 2
+    a = (omega_out * r_out ** 2 - omega_in * r_in ** 2) / d
+    b = r_in ** 2 * r_out ** 2 * (omega_in - omega_out) / d
+    r = np.asarray(r, dtype=np.float64)
+    return a * r + b / r
 
 
 def shock(n_r: int = 2000, n_theta: int = 16, steps: int = 1000, cfl: float = STABLE_CFL,
