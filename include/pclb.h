@@ -81,6 +81,21 @@ typedef enum {
   PCLB_BC_WALL = 1,      /* rho, T extrapolated; u_r, u_theta prescribed at the ghost nodes */
   PCLB_BC_DIRICHLET = 2  /* rho, u_r, u_theta, T prescribed at the ghost nodes */
 } pclb_bc_kind;
+/* Convection schemes (Sec. II B 3; the paper compares them in its Fig. 5).
+ * Each advances psi_t + a psi_xi = 0 by psi_j -= M_j with C = a dt / dxi. */
+typedef enum {
+  PCLB_SCHEME_MWB = 0,     /* Modified Warming-Beam with the switch S(eta), Eq. (28): the default */
+  PCLB_SCHEME_WB = 1,      /* Warming-Beam, Eq. (25) */
+  PCLB_SCHEME_LW = 2,      /* Lax-Wendroff: centred differences in the Taylor expansion of Eq. (22) */
+  PCLB_SCHEME_UPWIND2 = 3  /* forward-Euler step with the second-order upwind derivative of Eq. (23) */
+} pclb_scheme;
+
+/* Relaxation (Sec. II B 2). */
+typedef enum {
+  PCLB_RELAX_EXACT = 0,  /* f^eq + (f - f^eq) exp(-dt/tau), Eq. (19): the default */
+  PCLB_RELAX_EULER = 1   /* f - dt/tau (f - f^eq), Eq. (18); requires dt <= 2 tau */
+} pclb_relaxation;
+
 /* Flag added to a kind: the ghost nodes carry, besides f^eq of their
  * macroscopic state, the departure f - f^eq of the wall node (the
  * non-equilibrium microscopic boundary of Sec. II C 1, in the form of the
@@ -175,6 +190,14 @@ pclb_status pclb_step(pclb_ctx* ctx, int32_t n);
 /* Macroscopic fields of the current state (Eqs. 3-5): device,
  * [n_theta][n_r], context precision; any pointer may be NULL. */
 pclb_status pclb_moments(pclb_ctx* ctx, void* rho, void* u_r, void* u_theta, void* T);
+
+/* Select the convection scheme and the relaxation of subsequent steps (the
+ * variants the paper compares; a new context uses PCLB_SCHEME_MWB and
+ * PCLB_RELAX_EXACT).  Errors: PCLB_EINVAL (unknown value), PCLB_ECFL
+ * (PCLB_RELAX_EULER with dt > 2 tau, where it is unstable).  The adjoint
+ * entry points support PCLB_SCHEME_MWB only (PCLB_EUNSUPPORTED otherwise);
+ * both relaxations are supported. */
+pclb_status pclb_set_scheme(pclb_ctx* ctx, int32_t scheme, int32_t relaxation);
 
 /* Non-equilibrium manifestations of the current state (Sec. IV).  At every
  * node, with c = v (plain) or c = v - u (central, u the node's velocity) in

@@ -52,6 +52,7 @@ class _Problem(ctypes.Structure):
         ("tau", ctypes.c_double), ("dt", ctypes.c_double),
         ("bc_kind", ctypes.c_int32 * 2),
         ("bc_values", ctypes.POINTER(ctypes.c_double) * 2),
+        ("scheme", ctypes.c_int32), ("relaxation", ctypes.c_int32),
     ]
 
 
@@ -67,6 +68,8 @@ def lib():
             L.orc_q.restype = ctypes.c_int
             L.orc_mwb_increment.restype = ctypes.c_double
             L.orc_mwb_increment.argtypes = [ctypes.c_double] * 6
+            L.orc_scheme_increment.restype = ctypes.c_double
+            L.orc_scheme_increment.argtypes = [ctypes.c_int] + [ctypes.c_double] * 6
             for name in ("orc_step", "orc_run", "orc_set_state", "orc_fields", "orc_diagnostics",
                          "orc_step_jvp", "orc_adjoint_step", "orc_set_state_jvp", "orc_fields_jvp",
                          "orc_step_nodes", "orc_adjoint_entries", "orc_noneq"):
@@ -102,6 +105,8 @@ class Problem:
                 p.bc_values[s] = _ptr(v)
             else:
                 p.bc_values[s] = ctypes.cast(None, _dp)
+        p.scheme = int(getattr(w, "scheme", 0))
+        p.relaxation = int(getattr(w, "relaxation", 0))
         self.p = p
         self.Q = 1 + 4 * p.n_dirs
         self.shape = (self.Q, p.n_theta, p.n_r)
@@ -152,6 +157,15 @@ def moments(f, n_dirs, speeds):
 
 def mwb_increment(C, pm2, pm1, p0, pp1, pp2):
     return lib().orc_mwb_increment(C, pm2, pm1, p0, pp1, pp2)
+
+
+SCHEME_MWB, SCHEME_WB, SCHEME_LW, SCHEME_UPWIND2 = 0, 1, 2, 3
+RELAX_EXACT, RELAX_EULER = 0, 1
+
+
+def scheme_increment(scheme, C, pm2, pm1, p0, pp1, pp2):
+    """Increment M (psi^{n+1} = psi - M) of one convection scheme at one node."""
+    return lib().orc_scheme_increment(int(scheme), C, pm2, pm1, p0, pp1, pp2)
 
 
 def mwb_1d(psi, C):

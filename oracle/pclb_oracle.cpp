@@ -15,7 +15,9 @@
 //   * the weights F_k, Eqs. (11a), (11b), (12), and the equilibrium, Eq. (10);
 //   * one time step of the combined scheme, Eq. (38): analytic relaxation,
 //     Eq. (19), minus the Modified Warming-Beam terms, Eq. (28) with the switch
-//     function S(eta) of Eq. (37), in r and in theta;
+//     function S(eta) of Eq. (37), in r and in theta; and the variants the
+//     paper compares: forward-Euler relaxation (Eq. 18), Warming-Beam
+//     (Eq. 25), Lax-Wendroff and second-order upwind convection;
 //   * the radial ghost nodes of Sec. II C 1 (Eq. 39, ghost f = f^eq) and the
 //     azimuthal ghost nodes of Sec. II C 2 (Eq. 40, index rotation).
 //   * the non-equilibrium manifestations of Sec. IV: the moments M_2, M_3,
@@ -204,6 +206,38 @@ T mwb_increment(double C, T pm2, T pm1, T p0, T pp1, T pp2) {
   return (C + 0.5 * C * (1.0 - std::fabs(C)) * (1.0 - S) * (1.0 - eta)) * delta;
 }
 
+// The other convection schemes the paper compares (Sec. II B 3, Fig. 5), as
+// the increment M with psi_j^{n+1} = psi_j^n - M; arguments psi_{j-2..j+2}.
+// Warming-Beam, Eq. (25): second-order upwind differences in the Taylor
+// expansion of Eq. (22).
+template <class T>
+T wb_increment(double C, T pm2, T pm1, T p0, T pp1, T pp2) {
+  if (C >= 0) return C * (p0 - pm1) + 0.5 * C * (1.0 - C) * (p0 - 2.0 * pm1 + pm2);
+  return C * (pp1 - p0) - 0.5 * C * (1.0 + C) * (p0 - 2.0 * pp1 + pp2);
+}
+// Lax-Wendroff: centred differences in the same Taylor expansion.
+template <class T>
+T lw_increment(double C, T pm2, T pm1, T p0, T pp1, T pp2) {
+  (void)pm2;
+  (void)pp2;
+  return 0.5 * C * (pp1 - pm1) - 0.5 * C * C * (pp1 - 2.0 * p0 + pm1);
+}
+// Second-order upwind: a forward-Euler step with the derivative of Eq. (23).
+template <class T>
+T upwind2_increment(double C, T pm2, T pm1, T p0, T pp1, T pp2) {
+  if (C >= 0) return 0.5 * C * (3.0 * p0 - 4.0 * pm1 + pm2);
+  return -0.5 * C * (3.0 * p0 - 4.0 * pp1 + pp2);
+}
+template <class T>
+T convection_increment(int scheme, double C, T pm2, T pm1, T p0, T pp1, T pp2) {
+  switch (scheme) {
+    case 1: return wb_increment(C, pm2, pm1, p0, pp1, pp2);
+    case 2: return lw_increment(C, pm2, pm1, p0, pp1, pp2);
+    case 3: return upwind2_increment(C, pm2, pm1, p0, pp1, pp2);
+    default: return mwb_increment(C, pm2, pm1, p0, pp1, pp2);
+  }
+}
+
 }  // namespace
 
 // ============================================================================
@@ -218,8 +252,10 @@ typedef struct {
   double speeds[5];         // v_0 .. v_4
   double B[5];              // B[n] = B_n of Table I (B[0] is the F_0 factor)
   double tau, dt;
-  int32_t bc_kind[2];       // inner, outer: 0 extrapolate, 1 wall (u given), 2 all given
+  int32_t bc_kind[2];       // inner, outer: 0 extrapolate, 1 wall (u given), 2 all given (+8: ghost f - f^eq)
   const double* bc_values[2];  // [2 layers][4 fields rho,u_r,u_theta,T][n_theta]
+  int32_t scheme;           // convection: 0 MWB (Eq. 28), 1 Warming-Beam, 2 Lax-Wendroff, 3 second-order upwind
+  int32_t relaxation;       // 0 analytic exponential (Eq. 19), 1 forward Euler
 } orc_problem;
 
 enum { ORC_OK = 0, ORC_NONPHYS = 1, ORC_NONFINITE = 2, ORC_EINVAL = 4 };
@@ -304,7 +340,8 @@ int update_node(const orc_problem& P, const Dvm& d, int it, int ir, Get G, T* ou
   const int NR = P.n_r, NT = P.n_theta, Q = d.Q;
   const double dr = (P.r_out - P.r_in) / (NR - 1);                       // Sec. II C 1
   const double dth = 2.0 * M_PI * P.n_f / (double(P.n_dirs) * NT);       // Sec. II C 2
-  const double decay = std::exp(-P.dt / P.tau);                          // Eq. (19)
+  // Eq. (19), or the forward-Euler step f + dt/tau (f^eq - f) of Eq. (18)
+  const double decay = P.relaxation == 1 ? 1.0 - P.dt / P.tau : std::exp(-P.dt / P.tau);
   const double theta = (it + 1) * dth;
   const double c = std::cos(theta), s = std::sin(theta);
   const double r = P.r_in + ir * dr;
@@ -322,8 +359,10 @@ int update_node(const orc_problem& P, const Dvm& d, int it, int ir, Get G, T* ou
     const double C_t = v_t * P.dt / (r * dth);
     T f = fc[q];
     T relax = fe[q] + (f - fe[q]) * decay;
-    T term_r = mwb_increment(C_r, G(q, it, ir - 2), G(q, it, ir - 1), f, G(q, it, ir + 1), G(q, it, ir + 2));
-    T term_t = mwb_increment(C_t, G(q, it - 2, ir), G(q, it - 1, ir), f, G(q, it + 1, ir), G(q, it + 2, ir));
+    T term_r = convection_increment(P.scheme, C_r, G(q, it, ir - 2), G(q, it, ir - 1), f, G(q, it, ir + 1),
+                                    G(q, it, ir + 2));
+    T term_t = convection_increment(P.scheme, C_t, G(q, it - 2, ir), G(q, it - 1, ir), f, G(q, it + 1, ir),
+                                    G(q, it + 2, ir));
     out[q] = relax - term_r - term_t;
     if (!std::isfinite(val(out[q]))) status |= ORC_NONFINITE;
   }
@@ -454,6 +493,7 @@ bool valid(const orc_problem* P) {
   if (P->n_r < 3 || P->n_theta < 2) return false;
   if (P->n_dirs < 1 || P->n_f < 1 || P->n_f > P->n_dirs) return false;
   if (!(P->r_out > P->r_in) || !(P->r_in > 0) || !(P->tau > 0) || !(P->dt > 0)) return false;
+  if (P->scheme < 0 || P->scheme > 3 || P->relaxation < 0 || P->relaxation > 1) return false;
   for (int s = 0; s < 2; ++s) {
     if ((P->bc_kind[s] & ~(3 | 8)) != 0 || (P->bc_kind[s] & 3) == 3) return false;
     if ((P->bc_kind[s] & 3) != 0 && P->bc_values[s] == nullptr) return false;
@@ -531,6 +571,10 @@ void orc_moments(int n_dirs, const double* speeds, const double* f, double* out)
   const double B[5] = {0, 0, 0, 0, 0};
   Dvm d = make_dvm(n_dirs, speeds, B);
   moments_node(d, f, 1, out[0], out[1], out[2], out[3]);
+}
+
+double orc_scheme_increment(int scheme, double C, double pm2, double pm1, double p0, double pp1, double pp2) {
+  return convection_increment(scheme, C, pm2, pm1, p0, pp1, pp2);
 }
 
 double orc_mwb_increment(double C, double pm2, double pm1, double p0, double pp1, double pp2) {

@@ -335,4 +335,21 @@ __device__ __forceinline__ double mwb_increment(double C, double f0, double u1, 
   return a * D + (a - a * a) * h;
 }
 
+// Convection increment of one node for the scheme SCH (pclb_scheme), in
+// upwind form: D = psi_j - psi_{j+u}, Dp = psi_{j+u} - psi_{j+2u} with u the
+// upwind side, d1 = psi_{j-u} the downwind neighbour, a = |C|, K = a(1 - a):
+//   MWB (Eq. 28)          a D + K h(D, Dp)
+//   Warming-Beam (Eq. 25) a D + K (D - Dp) / 2
+//   Lax-Wendroff          a D + K (Dd - D) / 2,   Dd = d1 - psi_j
+//   2nd-order upwind      a D + a (D - Dp) / 2   (forward Euler with Eq. 23)
+template <int SCH, class T>
+__device__ __forceinline__ T convect(T C, T f0, T u1, T u2, T d1) {
+  if (SCH == PCLB_SCHEME_MWB) return mwb_increment(C, f0, u1, u2);
+  const T a = C < T(0) ? -C : C, K = a - a * a;
+  const T D = f0 - u1, Dp = u1 - u2;
+  if (SCH == PCLB_SCHEME_WB) return a * D + T(0.5) * K * (D - Dp);
+  if (SCH == PCLB_SCHEME_UPWIND2) return a * D + T(0.5) * a * (D - Dp);
+  return a * D + T(0.5) * K * ((d1 - f0) - D);
+}
+
 }  // namespace pclb

@@ -454,6 +454,7 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
   sp.dt_dr = dt / dr;
   sp.dt_dth = dt / dth;
   sp.decay = std::exp(-dt / tau);
+  sp.scheme = PCLB_SCHEME_MWB;
   sp.bc_kind[0] = bc->kind[0];
   sp.bc_kind[1] = bc->kind[1];
   sp.cos_t = reinterpret_cast<const double*>(ctx->ws + lay.cos_t);
@@ -706,10 +707,28 @@ pclb_status pclb_lambda_get(pclb_ctx* ctx, void* lam) {
   return e == cudaSuccess ? PCLB_OK : cuda_fail(ctx, e, "lambda pack launch");
 }
 
-// The adjoint differentiates the ghost nodes as f = f^eq of their state.
+// The adjoint differentiates the ghost nodes as f = f^eq of their state and
+// the MWB increments.
 static pclb_status adjoint_supported(pclb_ctx* ctx) {
   if ((ctx->bc_kind[0] | ctx->bc_kind[1]) & PCLB_BC_NEQ)
     return fail(ctx, PCLB_EUNSUPPORTED, "the adjoint does not support PCLB_BC_NEQ boundaries");
+  if (ctx->scheme != PCLB_SCHEME_MWB)
+    return fail(ctx, PCLB_EUNSUPPORTED, "the adjoint supports the MWB scheme only (scheme %d)", ctx->scheme);
+  return PCLB_OK;
+}
+
+pclb_status pclb_set_scheme(pclb_ctx* ctx, int32_t scheme, int32_t relaxation) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (scheme < PCLB_SCHEME_MWB || scheme > PCLB_SCHEME_UPWIND2)
+    return fail(ctx, PCLB_EINVAL, "scheme = %d is unknown", scheme);
+  if (relaxation != PCLB_RELAX_EXACT && relaxation != PCLB_RELAX_EULER)
+    return fail(ctx, PCLB_EINVAL, "relaxation = %d is unknown", relaxation);
+  if (relaxation == PCLB_RELAX_EULER && ctx->dt > 2.0 * ctx->tau)
+    return fail(ctx, PCLB_ECFL, "forward-Euler relaxation is unstable for dt / tau = %g > 2", ctx->dt / ctx->tau);
+  ctx->scheme = scheme;
+  ctx->relaxation = relaxation;
+  ctx->sp.scheme = scheme;
+  ctx->sp.decay = relaxation == PCLB_RELAX_EULER ? 1.0 - ctx->dt / ctx->tau : std::exp(-ctx->dt / ctx->tau);
   return PCLB_OK;
 }
 

@@ -62,8 +62,9 @@ struct StepParams {
   int rows;                   // stored rows per plane: n_theta + 4
   double dt_dr;               // dt / dr
   double dt_dth;              // dt / dtheta
-  double decay;               // exp(-dt / tau), Eq. (19)
+  double decay;               // exp(-dt / tau), Eq. (19), or 1 - dt / tau (forward Euler)
   int bc_kind[2];
+  int scheme;                 // pclb_scheme of the convection increments
   const double* cos_t;        // [n_theta] cos(theta_i), host-computed in double
   const double* sin_t;        // [n_theta]
   const double* inv_r;        // [n_r] 1 / r_i
@@ -111,6 +112,8 @@ struct pclb_ctx {
   pclb_precision prec;
   double tau, dt;
   int32_t bc_kind[2];   // pclb_bc_kind, possibly with PCLB_BC_NEQ
+  int32_t scheme = 0;       // pclb_scheme
+  int32_t relaxation = 0;   // pclb_relaxation
   cudaStream_t stream;
   unsigned char* ws;
   pclb::Layout lay;

@@ -33,7 +33,7 @@ constexpr int step_smem_bytes() {
   return kQ * kPlane * (int)sizeof(T) + 128;   // planes + barrier slot
 }
 
-template <class T>
+template <class T, int SCH>
 __global__ void __launch_bounds__(kStepThreads, (sizeof(T) == 4 ? 2 : 1))
     step_kernel(const __grid_constant__ CUtensorMap tmap_in, T* __restrict__ f_out,
                 const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
@@ -129,8 +129,8 @@ __global__ void __launch_bounds__(kStepThreads, (sizeof(T) == 4 ? 2 : 1))
         const int st = vt >= T(0) ? -kWinR : kWinR;    // upwind neighbour in theta
         const T* fp = base + row[c] * kWinR;
         const T f0 = fp[0];
-        const T mr = mwb_increment(vr * dt_dr, f0, fp[sr], fp[2 * sr]);
-        const T mt = mwb_increment(vt * dt_dth_r, f0, fp[st], fp[2 * st]);
+        const T mr = convect<SCH>(vr * dt_dr, f0, fp[sr], fp[2 * sr], SCH == PCLB_SCHEME_LW ? fp[-sr] : T(0));
+        const T mt = convect<SCH>(vt * dt_dth_r, f0, fp[st], fp[2 * st], SCH == PCLB_SCHEME_LW ? fp[-st] : T(0));
         const T fe = feq_q<T>(eq[c], vx, vy, k);
         const T out = fe + (f0 - fe) * decay - mr - mt;
         T* dst = f_out + (size_t)q * plane_out + r;
@@ -144,19 +144,30 @@ __global__ void __launch_bounds__(kStepThreads, (sizeof(T) == 4 ? 2 : 1))
   }
 }
 
-template <class T>
-cudaError_t launch_step(const CUtensorMap* tmap_in, T* f_out, const StepParams& p,
-                        const DvmConst<T>& d, cudaStream_t stream) {
+template <class T, int SCH>
+static cudaError_t launch_scheme(const CUtensorMap* tmap_in, T* f_out, const StepParams& p, const DvmConst<T>& d,
+                                 cudaStream_t stream) {
   static bool configured = false;   // one-time attribute set per instantiation
   const int smem = step_smem_bytes<T>();
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<T, SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   dim3 grid((p.n_r + kTileR - 1) / kTileR, (p.n_theta + kTileT - 1) / kTileT);
-  step_kernel<T><<<grid, kStepThreads, smem, stream>>>(*tmap_in, f_out, p, d);
+  step_kernel<T, SCH><<<grid, kStepThreads, smem, stream>>>(*tmap_in, f_out, p, d);
   return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_step(const CUtensorMap* tmap_in, T* f_out, const StepParams& p,
+                        const DvmConst<T>& d, cudaStream_t stream) {
+  switch (p.scheme) {
+    case PCLB_SCHEME_WB: return launch_scheme<T, PCLB_SCHEME_WB>(tmap_in, f_out, p, d, stream);
+    case PCLB_SCHEME_LW: return launch_scheme<T, PCLB_SCHEME_LW>(tmap_in, f_out, p, d, stream);
+    case PCLB_SCHEME_UPWIND2: return launch_scheme<T, PCLB_SCHEME_UPWIND2>(tmap_in, f_out, p, d, stream);
+    default: return launch_scheme<T, PCLB_SCHEME_MWB>(tmap_in, f_out, p, d, stream);
+  }
 }
 
 template cudaError_t launch_step<double>(const CUtensorMap*, double*, const StepParams&,

@@ -233,6 +233,7 @@ __device__ __forceinline__ f2 limiter2(f2 D, f2 Dp) {
 
 }  // namespace
 
+template <int SCH>
 __global__ void __launch_bounds__(kStepThreads, 2)
     step_kernel_f32(const __grid_constant__ CUtensorMap tmap_in, float* __restrict__ f_out,
                     const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<float> d) {
@@ -338,7 +339,10 @@ __global__ void __launch_bounds__(kStepThreads, 2)
 
   // One velocity of a pair.  sr = +1 if its upwind neighbour in r is at
   // larger r, st the same for theta (rows); fe is its equilibrium.
-  // nar, nkr, nat, nkt: the negated a = |C| and K = |C|(1 - |C|) in r and theta
+  // nar, nkr, nat, nkt: the negated a = |C| and K = |C|(1 - |C|) in r and
+  // theta.  Increments in upwind form (D, Dp the upwind differences):
+  // MWB a D + K h(D, Dp); WB a D + K (D - Dp)/2; LW a D + K (Dd - D)/2 with
+  // Dd the downwind difference; second-order upwind a D + a (D - Dp)/2.
   auto update = [&](int q, int sr, int st, f2 nar, f2 nkr, f2 nat, f2 nkt, f2 fe) {
     const float* w = win + q * kPlaneF;
     const f2 C = ld2(w);
@@ -350,8 +354,22 @@ __global__ void __launch_bounds__(kStepThreads, 2)
     f2 o = fma2(sub2(C, fe), decay, fe);
     o = fma2(nar, Dr, o);
     o = fma2(nat, Dt, o);
-    o = fma2(nkr, limiter2(Dr, sub2(u1, S)), o);
-    o = fma2(nkt, limiter2(Dt, sub2(T1, T2)), o);
+    if constexpr (SCH == PCLB_SCHEME_MWB) {
+      o = fma2(nkr, limiter2(Dr, sub2(u1, S)), o);
+      o = fma2(nkt, limiter2(Dt, sub2(T1, T2)), o);
+    } else if constexpr (SCH == PCLB_SCHEME_WB) {
+      o = fma2(mul2(bc2(0.5f), nkr), sub2(Dr, sub2(u1, S)), o);
+      o = fma2(mul2(bc2(0.5f), nkt), sub2(Dt, sub2(T1, T2)), o);
+    } else if constexpr (SCH == PCLB_SCHEME_UPWIND2) {
+      o = fma2(mul2(bc2(0.5f), nar), sub2(Dr, sub2(u1, S)), o);
+      o = fma2(mul2(bc2(0.5f), nat), sub2(Dt, sub2(T1, T2)), o);
+    } else {
+      const f2 X = ld2(w - 2 * sr);               // the pair on the downwind side
+      const f2 d1 = sr < 0 ? mk2(C.y, X.x) : mk2(X.y, C.x);   // first downwind neighbours
+      const f2 Td = ld2(w - st * kWinR);
+      o = fma2(mul2(bc2(0.5f), nkr), sub2(sub2(d1, C), Dr), o);
+      o = fma2(mul2(bc2(0.5f), nkt), sub2(sub2(Td, C), Dt), o);
+    }
     store(q, o);
   };
 
@@ -383,17 +401,29 @@ __global__ void __launch_bounds__(kStepThreads, 2)
   }
 }
 
-cudaError_t launch_step_f32(const CUtensorMap* tmap_in, float* f_out, const StepParams& p,
-                            const DvmConst<float>& d, cudaStream_t stream) {
+template <int SCH>
+static cudaError_t launch_scheme_f32(const CUtensorMap* tmap_in, float* f_out, const StepParams& p,
+                                     const DvmConst<float>& d, cudaStream_t stream) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemF32);
+    cudaError_t e =
+        cudaFuncSetAttribute(step_kernel_f32<SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemF32);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   dim3 grid((p.n_r + kTileR - 1) / kTileR, (p.n_theta + kTileT - 1) / kTileT);
-  step_kernel_f32<<<grid, kStepThreads, kSmemF32, stream>>>(*tmap_in, f_out, p, d);
+  step_kernel_f32<SCH><<<grid, kStepThreads, kSmemF32, stream>>>(*tmap_in, f_out, p, d);
   return cudaGetLastError();
+}
+
+cudaError_t launch_step_f32(const CUtensorMap* tmap_in, float* f_out, const StepParams& p,
+                            const DvmConst<float>& d, cudaStream_t stream) {
+  switch (p.scheme) {
+    case PCLB_SCHEME_WB: return launch_scheme_f32<PCLB_SCHEME_WB>(tmap_in, f_out, p, d, stream);
+    case PCLB_SCHEME_LW: return launch_scheme_f32<PCLB_SCHEME_LW>(tmap_in, f_out, p, d, stream);
+    case PCLB_SCHEME_UPWIND2: return launch_scheme_f32<PCLB_SCHEME_UPWIND2>(tmap_in, f_out, p, d, stream);
+    default: return launch_scheme_f32<PCLB_SCHEME_MWB>(tmap_in, f_out, p, d, stream);
+  }
 }
 
 }  // namespace pclb

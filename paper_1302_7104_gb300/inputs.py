@@ -51,6 +51,9 @@ BC_WALL = 1       # rho, T extrapolated; u prescribed at the ghost nodes
 BC_DIRICHLET = 2  # rho, u, T prescribed at the ghost nodes
 BC_NEQ = 8        # flag added to a kind: ghosts also carry the wall node's f - f^eq
 
+SCHEME_MWB, SCHEME_WB, SCHEME_LW, SCHEME_UPWIND2 = 0, 1, 2, 3
+RELAX_EXACT, RELAX_EULER = 0, 1
+
 
 @dataclasses.dataclass
 class Workload:
@@ -78,6 +81,8 @@ class Workload:
     bc_values: tuple = (None, None)
     smooth: bool = True
     extra: dict = dataclasses.field(default_factory=dict)
+    scheme: int = 0       # convection: SCHEME_MWB, _WB, _LW, _UPWIND2
+    relaxation: int = 0   # RELAX_EXACT (Eq. 19) or RELAX_EULER
 
     @property
     def q(self) -> int:

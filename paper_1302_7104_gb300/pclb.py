@@ -24,6 +24,10 @@ STATUS = {0: "PCLB_OK", 1: "PCLB_EINVAL", 2: "PCLB_ENOMEM", 3: "PCLB_ECUDA", 4: 
 FLAG_NONPHYS, FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2, 4
 
 
+# convection schemes and relaxations of pclb_set_scheme
+SCHEME_MWB, SCHEME_WB, SCHEME_LW, SCHEME_UPWIND2 = 0, 1, 2, 3
+RELAX_EXACT, RELAX_EULER = 0, 1
+
 # groups of pclb_noneq and the order of its 12 components per group
 NEQ_M, NEQ_DELTA, NEQ_MSTAR, NEQ_DSTAR = 1, 2, 4, 8
 NEQ_COMPONENTS = ("2rr", "2rt", "2tt", "3rrr", "3rrt", "3rtt", "3ttt", "31r", "31t", "42rr", "42rt", "42tt")
@@ -65,6 +69,7 @@ _SIGS = {
     "pclb_step": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "pclb_moments": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "pclb_noneq": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
+    "pclb_set_scheme": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     "pclb_diagnostics": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "pclb_status_flags": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int32]),
     "pclb_sync": (ctypes.c_int, [_vp, ctypes.c_int32]),
@@ -164,6 +169,14 @@ class PCLB:
                                  self.prec, ctypes.byref(bc), _vp(aligned), int(nbytes.value),
                                  _vp(self.stream.cuda_stream), ctypes.byref(ctx)))
         self.ctx = ctx
+        scheme, relaxation = int(getattr(w, "scheme", 0)), int(getattr(w, "relaxation", 0))
+        if scheme or relaxation:
+            self.set_scheme(scheme, relaxation)
+
+    def set_scheme(self, scheme: int = 0, relaxation: int = 0):
+        """Convection scheme (SCHEME_*) and relaxation (RELAX_*) of later steps."""
+        _check(lib().pclb_set_scheme(self.ctx, int(scheme), int(relaxation)), self.ctx)
+        return self
 
     # -- lifetime ----------------------------------------------------------
     def close(self):
