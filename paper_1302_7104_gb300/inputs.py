@@ -300,7 +300,9 @@ def rm(n_r: int = 1024, n_theta: int = 2048, steps: int = 5000, cfl: float = STA
     gas (rho 3 vs 1, equal pressure 1), inward Mach-2 shock starting at r=2.6
     with the Rankine-Hugoniot post-shock state (Eq. 45) behind it.  The
     interface is smoothed over 2 dr (tanh).  Inner wall extrapolated, outer
-    wall held at the post-shock state."""
+    wall held at the post-shock state.  The CFL-based dt is far above tau;
+    runs that follow the shock through the interface need dt of the order
+    of tau (the paper's RM runs use dt = tau = 1e-5)."""
     R, TH = _mesh(n_r, n_theta, r_in, r_out)
     dr = (r_out - r_in) / (n_r - 1)
     r_if = 2.0 + amp * np.cos(mode * TH)
