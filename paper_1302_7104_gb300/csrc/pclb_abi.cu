@@ -248,7 +248,8 @@ pclb_status encode_map(pclb_ctx* ctx, const void* base, int box_rows, CUtensorMa
 int adj_box_rows(const pclb_ctx* ctx) { return (ctx->prec == PCLB_FP64 ? kAdjRows64 : kAdjRows32) + 4; }
 
 pclb_status make_tmap(pclb_ctx* ctx, int which) {
-  return encode_map(ctx, ctx->ws + ctx->lay.f[which], kWinT, &ctx->tmap[which]);
+  return encode_map(ctx, ctx->ws + ctx->lay.f[which], ctx->prec == PCLB_FP32 ? kTileT32 + 4 : kWinT,
+                    &ctx->tmap[which]);
 }
 
 pclb_status bounded_sync(pclb_ctx* ctx, int timeout_ms) {

@@ -22,6 +22,11 @@ constexpr int kQ = 1 + 4 * kNDirs;
 // boundary so the TMA box starts aligned.
 constexpr int kTileR = 32;
 constexpr int kTileT = 16;
+// FP32 step kernel: tile rows, threads (two radially adjacent nodes each) and
+// CTAs per SM
+constexpr int kTileT32 = 16;
+constexpr int kStepThreads32 = 16 * kTileT32;
+constexpr int kCtasPerSm32 = 2;
 constexpr int kWinR = kTileR + 8;   // 40 columns
 constexpr int kWinT = kTileT + 4;   // 20 rows
 constexpr int kLeft = 4;            // column of interior r0 inside the window

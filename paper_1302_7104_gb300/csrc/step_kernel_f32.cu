@@ -3,7 +3,8 @@
 //
 // Work per CTA: a tile of 32 (r) x 16 (theta) nodes, 256 threads.  One thread
 // issues 33 TMA box copies (one per velocity plane) of the window
-// [r0-4, r0+36) x [t0-2, t0+18) into shared memory while the others copy the
+// [r0-4, r0+36) x [t0-2, t0+18) into shared memory, in four groups with a
+// barrier each (rest + shell 1, shells 2, 3, 4), while the others copy the
 // tile's rows of the host-computed Courant table.  Each thread then owns two
 // radially adjacent nodes of one row and processes them together with packed
 // FP32x2 arithmetic:
@@ -30,10 +31,13 @@ namespace pclb {
 namespace {
 
 constexpr int kPairs = 4 * kHalf;                    // 16
-constexpr int kPlaneF = kWinR * kWinT;               // floats per plane window
+constexpr int kPlaneF = kWinR * (kTileT32 + 4);      // floats per plane window
 constexpr int kPlanesBytes = kQ * kPlaneF * 4;       // 105600
-constexpr int kTabBytes = kPairs * kTileT * 16;      // one float4 per (pair, row)
+constexpr int kTabBytes = kPairs * kTileT32 * 16;    // one float4 per (pair, row)
 constexpr int kSmemF32 = kPlanesBytes + kTabBytes + 128;
+constexpr int kGroups = 4;
+__device__ __forceinline__ int group_first(int g) { return g == 0 ? 0 : 1 + g * kNDirs; }
+__device__ __forceinline__ int group_planes(int g) { return g == 0 ? 1 + kNDirs : kNDirs; }
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 // Unit vectors of the first direction of each opposite pair, i = 0..3 of the
@@ -80,8 +84,12 @@ struct State2 {
 
 __device__ __forceinline__ ff2 ffc(float hi, float lo) { return ff2{bc2(hi), bc2(lo)}; }
 
-// Moments (Eqs. 3-5) and temperature recovery of the two nodes.
-__device__ __forceinline__ State2 state2(const float* f, const DvmConst<float>& d) {
+// Moments (Eqs. 3-5) and temperature recovery of the two nodes.  ready(g)
+// is called before plane group g (the rest plane and shell 1, then shells 2,
+// 3, 4) is first read, so the sums start while later groups still land.
+template <class Ready>
+__device__ __forceinline__ State2 state2(const float* f, const DvmConst<float>& d, Ready ready) {
+  ready(0);
   ff2 rho = ff2_of(ld2(f)), jx = ff2_of(bc2(0.f)), jy = jx, e = jx;
   f2 S, X, Xl, Y, Yl;
   // shell 1
@@ -91,6 +99,8 @@ __device__ __forceinline__ State2 state2(const float* f, const DvmConst<float>& 
   jy = ff2_add(jy, ff2_mul(ffc(d.speed[1], d.speed_lo[1]), ff2{Y, Yl}));
   e = ff2_add(e, ff2_mul(ffc(d.half_v2[1], d.half_v2_lo[1]), ff2_of(S)));
   // shells 2 + 3 direction by direction, with the speed and v^2/2 of shell 2
+  ready(1);
+  ready(2);
   shell_sums2<2, 3>(f, S, X, Xl, Y, Yl);
   rho = ff2_add(rho, ff2_of(S));
   jx = ff2_add(jx, ff2_mul(ffc(d.speed[2], d.speed_lo[2]), ff2{X, Xl}));
@@ -102,6 +112,7 @@ __device__ __forceinline__ State2 state2(const float* f, const DvmConst<float>& 
   jy = ff2_add(jy, ff2_mul(ffc(d.dv23, d.dv23_lo), ff2{Y, Yl}));
   e = ff2_add(e, ff2_mul(ffc(d.dh23, d.dh23_lo), ff2_of(S)));
   // shell 4
+  ready(3);
   shell_sums2<4, 0>(f, S, X, Xl, Y, Yl);
   rho = ff2_add(rho, ff2_of(S));
   jx = ff2_add(jx, ff2_mul(ffc(d.speed[4], d.speed_lo[4]), ff2{X, Xl}));
@@ -234,7 +245,7 @@ __device__ __forceinline__ f2 limiter2(f2 D, f2 Dp) {
 }  // namespace
 
 template <int SCH>
-__global__ void __launch_bounds__(kStepThreads, 2)
+__global__ void __launch_bounds__(kStepThreads32, kCtasPerSm32)
     step_kernel_f32(const __grid_constant__ CUtensorMap tmap_in, float* __restrict__ f_out,
                     const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<float> d) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -243,31 +254,31 @@ __global__ void __launch_bounds__(kStepThreads, 2)
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + kPlanesBytes + kTabBytes);
 
   const int r0 = blockIdx.x * kTileR;
-  const int t0 = blockIdx.y * kTileT;
+  const int t0 = blockIdx.y * kTileT32;
   const int tid = threadIdx.x;
 
   if (tid == 0) {
     tma_prefetch_desc(&tmap_in);
-    mbar_init(bar, 1);
+    for (int g = 0; g < kGroups; ++g) mbar_init(&bar[g], 1);
     mbar_fence_init();
   }
   __syncthreads();
   if (tid == 0) {
-    mbar_arrive_expect_tx(bar, (uint32_t)kPlanesBytes);
 #pragma unroll 1
-    for (int q = 0; q < kQ; ++q) tma_load_3d(sm + q * kPlaneF, &tmap_in, r0 - kLeft, t0, q, bar);
+    for (int g = 0; g < kGroups; ++g) {
+      const int q0 = group_first(g), n = group_planes(g);
+      mbar_arrive_expect_tx(&bar[g], (uint32_t)(n * kPlaneF * 4));
+#pragma unroll 1
+      for (int q = q0; q < q0 + n; ++q) tma_load_3d(sm + q * kPlaneF, &tmap_in, r0 - kLeft, t0, q, &bar[g]);
+    }
   }
   {  // Courant entries of the tile rows: table layout [pair][row]
-    const int pair = tid / kTileT, rl = tid % kTileT;
+    const int pair = tid / kTileT32, rl = tid % kTileT32;
     const int t = min(t0 + rl, p.n_theta - 1);
-    tab[pair * kTileT + rl] = p.courant[(size_t)(t + kGhostRows) * kPairs + pair];
+    tab[pair * kTileT32 + rl] = p.courant[(size_t)(t + kGhostRows) * kPairs + pair];
   }
-  if (!mbar_wait_bounded(bar, 0, kWaitNs)) {
-    if (tid == 0) atomicOr(p.status, PCLB_FLAG_TIMEOUT);
-    mbar_wait_bounded(bar, 0, kWaitNs);
-    return;
-  }
-  __syncthreads();   // table visible
+  __syncthreads();   // table visible (while the copies are still landing)
+  bool ok = true;
 
   // ---- per-thread nodes: row rl, radial cells j2 and j2 + 1 -----------------
   const int warp = tid >> 5, lane = tid & 31;
@@ -283,12 +294,15 @@ __global__ void __launch_bounds__(kStepThreads, 2)
 
   Eq2 eq;
   {
-    State2 s = state2(win, d);
+    auto ready = [&](int g) {
+      if (ok) ok = mbar_wait_bounded(&bar[g], 0, kWaitNs);
+    };
+    State2 s = state2(win, d, ready);
     const bool ok0 = s.rho.hi.x > 0.f && s.E.hi.x > 0.f && isfinite(s.E.hi.x) && isfinite(s.ux.hi.x) &&
                      isfinite(s.uy.hi.x);
     const bool ok1 = s.rho.hi.y > 0.f && s.E.hi.y > 0.f && isfinite(s.E.hi.y) && isfinite(s.ux.hi.y) &&
                      isfinite(s.uy.hi.y);
-    if ((v0 && !ok0) || (v1 && !ok1)) atomicOr(p.status, PCLB_FLAG_NONPHYS);
+    if (ok && ((v0 && !ok0) || (v1 && !ok1))) atomicOr(p.status, PCLB_FLAG_NONPHYS);
     // keep lanes without a valid node finite (their results are never stored)
     if (!v0) { s.rho.hi.x = 1.f; s.rho.lo.x = 0.f; s.E.hi.x = 1.f; s.E.lo.x = 0.f;
                s.ux.hi.x = 0.f; s.ux.lo.x = 0.f; s.uy.hi.x = 0.f; s.uy.lo.x = 0.f; }
@@ -297,13 +311,27 @@ __global__ void __launch_bounds__(kStepThreads, 2)
     eq = eq2(s, d);
   }
 
-  // ---- radial ghost columns ------------------------------------------------
-  if (r0 == 0 && warp == 0 && lane < kTileT && t0 + lane < p.n_theta)
-    ghost_columns_f32(sm, 2 + lane, 0, kLeft, t0 + lane, p, d);
+  // ---- radial ghost columns (tiles at a wall only) ----------------------------
   const int cw_out = p.n_r - 1 - r0 + kLeft;
-  if (cw_out <= kLeft + kTileR && warp == 1 && lane < kTileT && t0 + lane < p.n_theta)
-    ghost_columns_f32(sm, 2 + lane, 1, cw_out, t0 + lane, p, d);
-  __syncthreads();
+  if (r0 == 0 || cw_out <= kLeft + kTileR) {
+    if (ok && r0 == 0 && warp == 0 && lane < kTileT32 && t0 + lane < p.n_theta)
+      ghost_columns_f32(sm, 2 + lane, 0, kLeft, t0 + lane, p, d);
+    if (ok && cw_out <= kLeft + kTileR && warp == 1 && lane < kTileT32 && t0 + lane < p.n_theta)
+      ghost_columns_f32(sm, 2 + lane, 1, cw_out, t0 + lane, p, d);
+    if (__syncthreads_or(!ok)) {   // ghost columns visible; a copy that timed out stops the tile
+      if (tid == 0) {
+        atomicOr(p.status, PCLB_FLAG_TIMEOUT);
+        for (int g = 0; g < kGroups; ++g) mbar_wait_bounded(&bar[g], 0, kWaitNs);
+      }
+      return;
+    }
+  } else if (!ok) {
+    // a copy did not land in time: report it, give the copies a bounded time
+    // to finish, and leave (no barrier follows in this tile)
+    atomicOr(p.status, PCLB_FLAG_TIMEOUT);
+    for (int g = 0; g < kGroups; ++g) mbar_wait_bounded(&bar[g], 0, kWaitNs);
+    return;
+  }
 
   // ---- update ----------------------------------------------------------------
   const f2 invr = mk2(v0 ? p.inv_r_f[r] : 1.f, v1 ? p.inv_r_f[r + 1] : 1.f);
@@ -316,7 +344,7 @@ __global__ void __launch_bounds__(kStepThreads, 2)
   float* out_hi = f_out + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r;
 
   // tiles away from the radial walls and the seam take the plain store
-  const bool plain_tile = r0 + kTileR <= p.n_r && t0 >= 2 && t0 + kTileT <= p.n_theta - 2;
+  const bool plain_tile = r0 + kTileR <= p.n_r && t0 >= 2 && t0 + kTileT32 <= p.n_theta - 2;
   auto store = [&](int q, f2 o) {
     if (plain_tile) {
       *reinterpret_cast<float2*>(out_row + (size_t)q * plane_out) = o;
@@ -383,7 +411,7 @@ __global__ void __launch_bounds__(kStepThreads, 2)
 #pragma unroll
     for (int i = 0; i < kHalf; ++i) {
       const int q = qb + i;
-      const float4 tb = tab[((k - 1) * kHalf + i) * kTileT + rl];
+      const float4 tb = tab[((k - 1) * kHalf + i) * kTileT32 + rl];
       const int fl = __float_as_int(tb.w);
       const int sr = (fl & 1) ? 1 : -1;            // v_r < 0: upwind at larger r
       const int st = (fl & 2) ? 1 : -1;            // v_theta < 0: upwind at larger theta
@@ -411,8 +439,8 @@ static cudaError_t launch_scheme_f32(const CUtensorMap* tmap_in, float* f_out, c
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grid((p.n_r + kTileR - 1) / kTileR, (p.n_theta + kTileT - 1) / kTileT);
-  step_kernel_f32<SCH><<<grid, kStepThreads, kSmemF32, stream>>>(*tmap_in, f_out, p, d);
+  dim3 grid((p.n_r + kTileR - 1) / kTileR, (p.n_theta + kTileT32 - 1) / kTileT32);
+  step_kernel_f32<SCH><<<grid, kStepThreads32, kSmemF32, stream>>>(*tmap_in, f_out, p, d);
   return cudaGetLastError();
 }
 
