@@ -11,11 +11,13 @@
 //      shared memory: moments of the two wall nodes, Eq. (39) extrapolation
 //      (or prescribed values), f = f^eq (Sec. II C 1) -- ghosts never touch
 //      global memory;
-//   4. for every velocity: relaxation (Eq. 19) minus the MWB increments
-//      (Eq. 28) in r and theta read from the window, stored straight to the
-//      output; rows next to the azimuthal seam are also written into the
-//      output's ghost rows (Eq. 40, label rotated by N_f) so the next step's
-//      window is one contiguous box.
+//   4. for every pair of opposite velocities (sharing their Courant entry,
+//      staged per tile row in shared memory, and the even and odd parts of
+//      the equilibrium polynomial): relaxation (Eq. 19) minus the convection
+//      increments (Eq. 28 or the compared schemes) in r and theta read from
+//      the window, stored straight to the output; rows next to the azimuthal
+//      seam are also written into the output's ghost rows (Eq. 40, label
+//      rotated by N_f) so the next step's window is one contiguous box.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -28,18 +30,50 @@ namespace pclb {
 constexpr int kPlane = kWinR * kWinT;   // elements per velocity plane in shared memory
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
+constexpr int kPairs64 = 4 * kNDirs / 2;   // pairs of opposite velocities
+
 template <class T>
 constexpr int step_smem_bytes() {
-  return kQ * kPlane * (int)sizeof(T) + 128;   // planes + barrier slot
+  // planes, Courant table [pair][row] of 4 values, barrier slot
+  return kQ * kPlane * (int)sizeof(T) + kPairs64 * kTileT * 4 * (int)sizeof(T) + 128;
+}
+
+// 1/n by the Newton-Raphson iteration r <- r (2 - n r) from the hardware's
+// approximate reciprocal; each step doubles the number of correct bits, two
+// reach full double precision (checked against the division in the parity
+// tests).  n must be a positive normal number.
+__device__ __forceinline__ double recip_newton(double n) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(n));
+  double e = fma(-n, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-n, r, 1.0);
+  return fma(r, e, r);
+}
+
+// Convection increment (upwind form, see convect in device_common.cuh) from
+// a = |C| and K = a (1 - a) given by the Courant table.
+template <int SCH>
+__device__ __forceinline__ double convect_aK(double a, double K, double f0, double u1, double u2, double d1) {
+  const double D = f0 - u1, Dp = u1 - u2;
+  if (SCH == PCLB_SCHEME_MWB) {
+    const double den = fabs(D) + fabs(Dp);
+    const double h = den >= 2.2250738585072014e-308 ? fabs(D) * (D - Dp) * recip_newton(den) : 0.0;
+    return a * D + K * h;
+  }
+  if (SCH == PCLB_SCHEME_WB) return a * D + 0.5 * K * (D - Dp);
+  if (SCH == PCLB_SCHEME_UPWIND2) return a * D + 0.5 * a * (D - Dp);
+  return a * D + 0.5 * K * ((d1 - f0) - D);
 }
 
 template <class T, int SCH>
-__global__ void __launch_bounds__(kStepThreads, (sizeof(T) == 4 ? 2 : 1))
+__global__ void __launch_bounds__(kStepThreads, 1)
     step_kernel(const __grid_constant__ CUtensorMap tmap_in, T* __restrict__ f_out,
                 const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + kQ * kPlane * sizeof(T));
+  T* tab = sm + kQ * kPlane;                           // [pair][row][a_r, k_r, a_w, flags]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tab + kPairs64 * kTileT * 4);
 
   const int r0 = blockIdx.x * kTileR;
   const int t0 = blockIdx.y * kTileT;
@@ -58,6 +92,13 @@ __global__ void __launch_bounds__(kStepThreads, (sizeof(T) == 4 ? 2 : 1))
 #pragma unroll 1
     for (int q = 0; q < kQ; ++q) tma_load_3d(sm + q * kPlane, &tmap_in, r0 - kLeft, t0, q, bar);
   }
+  {  // Courant entries of the tile rows (from the FP64 table of the context)
+    const int pair = threadIdx.x / kTileT, rl = threadIdx.x % kTileT;
+    const int tt = min(t0 + rl, p.n_theta - 1);
+    const double* e = p.courant64 + ((size_t)(tt + kGhostRows) * kPairs64 + pair) * 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tab[(pair * kTileT + rl) * 4 + j] = (T)e[j];
+  }
   if (!mbar_wait_bounded(bar, 0, kWaitLimitNs)) {
     if (threadIdx.x == 0) atomicOr(p.status, PCLB_FLAG_TIMEOUT);
     // give the copies one more bounded chance to land before the CTA exits
@@ -70,7 +111,6 @@ __global__ void __launch_bounds__(kStepThreads, (sizeof(T) == 4 ? 2 : 1))
   const int col = kLeft + lane;
   int row[2], t[2];
   bool valid[2];
-  T cs[2], sn[2];
   EqParams<T> eq[2];
   bool ok = true;
 #pragma unroll
@@ -78,8 +118,6 @@ __global__ void __launch_bounds__(kStepThreads, (sizeof(T) == 4 ? 2 : 1))
     row[c] = 2 + warp + 8 * c;
     t[c] = t0 + warp + 8 * c;
     valid[c] = (r < p.n_r) && (t[c] < p.n_theta);
-    cs[c] = valid[c] ? (T)p.cos_t[t[c]] : T(1);
-    sn[c] = valid[c] ? (T)p.sin_t[t[c]] : T(0);
     NodeState<T> m;
     if (valid[c]) {
       m = node_moments(sm + row[c] * kWinR + col, kPlane, d);
@@ -104,41 +142,60 @@ __global__ void __launch_bounds__(kStepThreads, (sizeof(T) == 4 ? 2 : 1))
   }
   __syncthreads();
 
-  // ---- 4. relaxation minus MWB increments, per velocity -------------------
+  // ---- 4. relaxation minus MWB increments, per pair of opposite velocities --
   const T inv_r = (r < p.n_r) ? (T)p.inv_r[r] : T(1);
-  const T dt_dr = (T)p.dt_dr;
-  const T dt_dth_r = (T)p.dt_dth * inv_r;
   const T decay = (T)p.decay;
   const size_t plane_out = (size_t)p.rows * p.pitch;
-  // Shells are unrolled so that the weight rho F_k is a register, not an
-  // indexed array; directions within a shell run as a loop.
+  auto store = [&](int q, int c, T out) {
+    T* dst = f_out + (size_t)q * plane_out + r;
+    dst[(size_t)(t[c] + kGhostRows) * p.pitch] = out;
+    if (t[c] >= p.n_theta - 2)   // also the low ghost rows (theta <= 0) of the receiving label
+      f_out[(size_t)d.recv_lo[q] * plane_out + (size_t)(t[c] - (p.n_theta - 2)) * p.pitch + r] = out;
+    if (t[c] < 2)                // and the high ghost rows (theta > 2 pi n_f / n_dirs)
+      f_out[(size_t)d.recv_hi[q] * plane_out + (size_t)(p.n_theta + kGhostRows + t[c]) * p.pitch + r] = out;
+  };
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const int q_begin = k == 0 ? 0 : 1 + (k - 1) * kNDirs;
-    const int q_end = k == 0 ? 1 : q_begin + kNDirs;
+  for (int c = 0; c < 2; ++c) {   // rest velocity: no convection
+    if (!valid[c]) continue;
+    const T f0 = sm[row[c] * kWinR + col];
+    const T fe = eq[c].w[0] * eq[c].a0;
+    store(0, c, fe + (f0 - fe) * decay);
+  }
+  // Shells are unrolled so that the weight rho F_k is a register; the four
+  // pairs (q, q + N_i/2) of a shell run as a loop and share their Courant
+  // entry and the even and odd parts of the equilibrium polynomial.
+#pragma unroll
+  for (int k = 1; k <= 4; ++k) {
 #pragma unroll 1
-    for (int q = q_begin; q < q_end; ++q) {
-      const T vx = d.vx[q], vy = d.vy[q];
-      const T* base = sm + q * kPlane + col;
+    for (int i = 0; i < kNDirs / 2; ++i) {
+      const int pair = (k - 1) * (kNDirs / 2) + i;
+      const int q1 = 1 + (k - 1) * kNDirs + i, q2 = q1 + kNDirs / 2;
+      const T vx = d.vx[q1], vy = d.vy[q1];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         if (!valid[c]) continue;
-        const T vr = vx * cs[c] + vy * sn[c];
-        const T vt = vy * cs[c] - vx * sn[c];
-        const int sr = vr >= T(0) ? -1 : 1;            // upwind neighbour in r
-        const int st = vt >= T(0) ? -kWinR : kWinR;    // upwind neighbour in theta
-        const T* fp = base + row[c] * kWinR;
-        const T f0 = fp[0];
-        const T mr = convect<SCH>(vr * dt_dr, f0, fp[sr], fp[2 * sr], SCH == PCLB_SCHEME_LW ? fp[-sr] : T(0));
-        const T mt = convect<SCH>(vt * dt_dth_r, f0, fp[st], fp[2 * st], SCH == PCLB_SCHEME_LW ? fp[-st] : T(0));
-        const T fe = feq_q<T>(eq[c], vx, vy, k);
-        const T out = fe + (f0 - fe) * decay - mr - mt;
-        T* dst = f_out + (size_t)q * plane_out + r;
-        dst[(size_t)(t[c] + kGhostRows) * p.pitch] = out;
-        if (t[c] >= p.n_theta - 2)   // also the low ghost rows (theta <= 0) of the receiving label
-          f_out[(size_t)d.recv_lo[q] * plane_out + (size_t)(t[c] - (p.n_theta - 2)) * p.pitch + r] = out;
-        if (t[c] < 2)                // and the high ghost rows (theta > 2 pi n_f / n_dirs)
-          f_out[(size_t)d.recv_hi[q] * plane_out + (size_t)(p.n_theta + kGhostRows + t[c]) * p.pitch + r] = out;
+        const T* e = tab + (pair * kTileT + warp + 8 * c) * 4;
+        const T ar = e[0], kr = e[1], at = e[2] * inv_r, kt = at - at * at;
+        const int fl = (int)e[3];
+        const int sr = (fl & 1) ? 1 : -1;               // v_r < 0 for q1: upwind at larger r
+        const int st = (fl & 2) ? kWinR : -kWinR;       // v_theta < 0 for q1: upwind at larger theta
+        // equilibrium of the pair: P(+x) = ev + od, P(-x) = ev - od (Eq. 10)
+        const T x = vx * eq[c].uxE + vy * eq[c].uyE, x2 = x * x;
+        const T ev = eq[c].a0 + x2 * (eq[c].a1h + x2 * T(1.0 / 24.0));
+        const T od = x * (eq[c].a1 + x2 * T(1.0 / 6.0));
+        const T fe1 = eq[c].w[k] * (ev + od), fe2 = eq[c].w[k] * (ev - od);
+        const T* fp1 = sm + q1 * kPlane + row[c] * kWinR + col;
+        const T* fp2 = sm + q2 * kPlane + row[c] * kWinR + col;
+        const bool lw = SCH == PCLB_SCHEME_LW;
+        const T a = fp1[0], b = fp2[0];
+        const T o1 = fe1 + (a - fe1) * decay -
+                     convect_aK<SCH>(ar, kr, a, fp1[sr], fp1[2 * sr], lw ? fp1[-sr] : T(0)) -
+                     convect_aK<SCH>(at, kt, a, fp1[st], fp1[2 * st], lw ? fp1[-st] : T(0));
+        const T o2 = fe2 + (b - fe2) * decay -
+                     convect_aK<SCH>(ar, kr, b, fp2[-sr], fp2[-2 * sr], lw ? fp2[sr] : T(0)) -
+                     convect_aK<SCH>(at, kt, b, fp2[-st], fp2[-2 * st], lw ? fp2[st] : T(0));
+        store(q1, c, o1);
+        store(q2, c, o2);
       }
     }
   }
