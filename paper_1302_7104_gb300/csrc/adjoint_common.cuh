@@ -13,13 +13,13 @@ template <class T>
 __device__ __forceinline__ T sgn(T x) { return copysign(x != T(0) ? T(1) : T(0), x); }
 
 // 1/x for the partials below: the hardware approximation in FP32 (relative
-// error ~1 ulp), the correctly rounded quotient in FP64.
+// error ~1 ulp), two Newton steps on it in FP64 (recip_newton).
 __device__ __forceinline__ float recip_fast(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ double recip_fast(double x) { return 1.0 / x; }
+__device__ __forceinline__ double recip_fast(double x) { return recip_newton(x); }
 
 template <class T>
 __device__ __forceinline__ T smallest_normal();
@@ -39,11 +39,12 @@ __device__ __forceinline__ void mwb_partials(T a, T K, T D, T Dp, T& MD, T& MDp)
   const T aD = abs(D), aP = abs(Dp), n = aD + aP;
   const T rn = n >= smallest_normal<T>() ? recip_fast(n) : T(0);
   const T ar = aD * rn, br = aP * rn;
-  const T s = sgn(D) * sgn(Dp);
-  const T hD = ar * (T(1) + br) - s * br * br;
-  const T hP = -(T(1) + s) * ar * ar;
-  MD = a + K * hD;
-  MDp = K * hP;
+  // s: the sign of the product D Dp is exact even where the product
+  // underflows; s = 0 when either factor is 0
+  const T s = min(aD, aP) > T(0) ? copysign(T(1), D * Dp) : T(0);
+  const T Ka = K * ar;
+  MD = fma(K, fma(br, fma(-s, br, ar), ar), a);   // a + K (ar + br (ar - s br))
+  MDp = -(T(1) + s) * (Ka * ar);
 }
 
 // G = sum_q lam(q) d f^eq_q / d(rho, u_x, u_y, E) at the given state (Eq. 10,

@@ -17,14 +17,20 @@
 // sign(x) with sign(0) = 0 (the switch function on its active branch); at
 // D = Dp = 0 the derivative of h is 0.
 //
-// One CTA: 32 (r) x TT (theta) nodes, one node per thread; the windows of f
-// and lam over [r0-4, r0+36) x [t0-2, t0+TT+2) for all 33 labels are staged
-// in shared memory by TMA.  Velocities are processed in pairs of opposite
-// labels, each in two phases: (A) every node whose upwind stencil can reach
-// the tile forms lam(n) dM(n)/dD and lam(n) dM(n)/dDp once, in r and in
-// theta, into shared memory; (B) every tile node gathers the products of the
-// nodes that read it.  One barrier per pair separates the phases; the
-// products live in two alternating buffers.
+// Two kernels:
+//   * adjoint_node_kernel, one thread per node: the moments of f^n, the
+//     cotangent g of the node's equilibrium (a reduction of lam^{n+1} over the
+//     33 labels), and for the nodes at a wall the ghost states and the
+//     cotangent g_wall the ghosts return; written to small global buffers;
+//   * adjoint_pair_kernel, tiles of 32 (r) x TT (theta) nodes: velocities in
+//     pairs of opposite labels, whose f and lam windows over [r0-4, r0+36) x
+//     [t0-2, t0+TT+2) stream through a ring of shared-memory stages filled by
+//     TMA while earlier pairs compute.  Each pair runs in two phases: (A)
+//     every node whose upwind stencil can reach the tile forms
+//     lam(n) dM(n)/dD and lam(n) dM(n)/dDp once, in r and in theta; (B) every
+//     tile node gathers the products of the nodes that read it and adds
+//     d lam + psi . ((1-d) g + g_wall).  One barrier per pair separates the
+//     phases; a stage is refilled as soon as its pair's phase (A) is done.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -56,21 +62,25 @@ struct alignas(4 * sizeof(T)) CourEntry {
   int fl;
 };
 
+constexpr int kAdjStages = 3;   // ring depth of the pair-streaming kernel
+static_assert(sizeof(EqParams<float>) == 10 * sizeof(float) && sizeof(EqParams<double>) == 10 * sizeof(double),
+              "ghost-state scratch holds 10 values per EqParams");
+
 template <class T>
 struct AdjSize {
   static constexpr int TT = AdjTile<T>::TT;
+  static constexpr int threads = 32 * TT;
   static constexpr int plane = kWinR * (TT + 4);
   static constexpr int npairs = 4 * kNDirs / 2;
   // products of one label: radial A, B over TT rows x 36 columns (tile
   // columns -2 .. 33), azimuthal A, B over TT + 4 rows (-2 .. TT + 1) x 32
   static constexpr int rcols = kTileR + 4;
   static constexpr int prod = 2 * TT * rcols + 2 * (TT + 4) * kTileR;
-  static constexpr int win_bytes = 2 * kQ * plane * (int)sizeof(T);
-  static constexpr int prod_bytes = 2 * 2 * prod * (int)sizeof(T);  // 2 buffers x 2 labels
-  static constexpr int gw_bytes = 2 * 2 * TT * 4 * (int)sizeof(T);
+  static constexpr int ring_bytes = kAdjStages * 4 * plane * (int)sizeof(T);   // f, f', lam, lam' per stage
+  static constexpr int prod_bytes = 2 * 2 * prod * (int)sizeof(T);             // 2 buffers x 2 labels
   static constexpr int invr_bytes = kTileR * (int)sizeof(T);
   static constexpr int tab_bytes = (TT + 4) * npairs * (int)sizeof(CourEntry<T>);
-  static constexpr int smem = win_bytes + prod_bytes + gw_bytes + invr_bytes + tab_bytes + 128;
+  static constexpr int smem = ring_bytes + prod_bytes + invr_bytes + tab_bytes + 128;
 };
 
 namespace {
@@ -133,186 +143,316 @@ __device__ __forceinline__ void adj_node_state(const double* f, int plane, const
   rho = m.rho; ux = m.ux; uy = m.uy; E = m.E; ok = m.ok;
 }
 
+
+// ---- the pair-streaming kernel's stencil pieces ------------------------------
+// Products of both labels of a pair at one node in one direction: q1 has its
+// upwind side at offset U, q2 (the opposite velocity) at -U.  sf, sl: the
+// pair's f and lam planes (q2 at +PLANE); o: the node in a plane; pr: its
+// product slot (M_D products; the M_Dp ones at +DB, q2's at +PROD).
+template <class T, int U, int PLANE, int PROD, int DB>
+__device__ __forceinline__ void radial_pair(const T* sf, const T* sl, T* pb, int o, int pr, T a, T K, T lam[2]) {
+  T MD, MP;
+  const T* f1 = sf + o;
+  mwb_partials<T>(a, K, f1[0] - f1[U], f1[U] - f1[2 * U], MD, MP);
+  lam[0] = sl[o];
+  pb[pr] = lam[0] * MD;
+  pb[pr + DB] = lam[0] * MP;
+  const T* f2 = sf + PLANE + o;
+  mwb_partials<T>(a, K, f2[0] - f2[-U], f2[-U] - f2[-2 * U], MD, MP);
+  lam[1] = sl[PLANE + o];
+  pb[PROD + pr] = lam[1] * MD;
+  pb[PROD + pr + DB] = lam[1] * MP;
+}
+
+template <class T, int U, int PLANE, int PROD, int DB>
+__device__ __forceinline__ void azimuthal_pair(const T* sf, const T lam[2], T* pb, int o, int pa, T a, T K) {
+  T MD, MP;
+  const T* f1 = sf + o;
+  mwb_partials<T>(a, K, f1[0] - f1[U], f1[U] - f1[2 * U], MD, MP);
+  pb[pa] = lam[0] * MD;
+  pb[pa + DB] = lam[0] * MP;
+  const T* f2 = sf + PLANE + o;
+  mwb_partials<T>(a, K, f2[0] - f2[-U], f2[-U] - f2[-2 * U], MD, MP);
+  pb[PROD + pa] = lam[1] * MD;
+  pb[PROD + pa + DB] = lam[1] * MP;
+}
+
+// One label at one halo node, upwind side at offset U.
+template <class T, int U>
+__device__ __forceinline__ void azimuthal_one(const T* fw, const T* lw, T* pa, int DB, T a, T K) {
+  T MD, MP;
+  mwb_partials<T>(a, K, fw[0] - fw[U], fw[U] - fw[2 * U], MD, MP);
+  const T lam = lw[0];
+  pa[0] = lam * MD;
+  pa[DB] = lam * MP;
+}
+
+// Gather of the radial products at one node: the node n = c + j u reads f(n),
+// f(n + u), f(n + 2 u), so dM(n)/df(c) collects M_D of n = c, M_Dp - M_D of
+// n = c - u and -M_Dp of n = c - 2u (u = U for q1, -U for q2).
+template <class T, int U, int PROD, int DB>
+__device__ __forceinline__ void gather_radial(const T* pb, int pr, T acc[2]) {
+  acc[0] = pb[pr] - pb[pr - U] + pb[pr + DB - U] - pb[pr + DB - 2 * U];
+  const T* p2 = pb + PROD;
+  acc[1] = p2[pr] - p2[pr + U] + p2[pr + DB + U] - p2[pr + DB + 2 * U];
+}
+
+// Azimuthal gather when the rows -2 .. +2 around the node all have q1's
+// upwind side on the same side: the readers of the node sit at +V, +2V for
+// q1 and at -V, -2V for q2 (V = +-row stride).
+template <class T, int V, int PROD, int DB>
+__device__ __forceinline__ void gather_azimuthal(const T* pb, int pa, T acc[2]) {
+  acc[0] += pb[pa] + pb[pa + DB + V] - pb[pa + V] - pb[pa + DB + 2 * V];
+  const T* p2 = pb + PROD;
+  acc[1] += p2[pa] + p2[pa + DB - V] - p2[pa - V] - p2[pa + DB - 2 * V];
+}
+
+// The same where the upwind side changes within the five rows: bit o of neg
+// set when row o - 2 has v_theta < 0 for q1 (its reader of row 0 is then the
+// row below it).
+template <class T, int PROD, int DB>
+__device__ __forceinline__ void gather_azimuthal_mixed(const T* pb, int pa, int tneg, T acc[2]) {
+#pragma unroll
+  for (int L = 0; L < 2; ++L) {
+    const T* P = pb + L * PROD;
+    const int neg = L ? (tneg ^ 0x1f) : tneg;          // the partner has the opposite velocity
+    T a = P[pa];
+    if (neg & 2) a += P[pa + DB - kTileR] - P[pa - kTileR];
+    if (!(neg & 8)) a += P[pa + DB + kTileR] - P[pa + kTileR];
+    if (neg & 1) a -= P[pa + DB - 2 * kTileR];
+    if (!(neg & 16)) a -= P[pa + DB + 2 * kTileR];
+    acc[L] += a;
+  }
+}
+
+// f^eq_q of a node state (rho and E in double as the step evaluates them).
+template <class T>
+__device__ __forceinline__ T adj_feq(const EqParams<T>& e, const DvmConst<T>& d, int q) {
+  return feq_q<T>(e, d.vx[q], d.vy[q], d.shell[q]);
+}
+
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Node-local part: gsum[n] = (1 - d) g(n), g the moment cotangent of the
+// node's equilibrium, Eq. (10), for lam^{n+1}.  gsum [n_theta][n_r][4].
+// ---------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(AdjTile<T>::TT * 32, 1)
-    adjoint_kernel(const __grid_constant__ CUtensorMap tmap_f, const __grid_constant__ CUtensorMap tmap_l,
-                   T* __restrict__ lam_out, const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
+__global__ void __launch_bounds__(128)
+    adjoint_node_kernel(const T* __restrict__ f, const T* __restrict__ lam, T* __restrict__ gsum,
+                        const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  if (r >= p.n_r) return;
+  const int plane = p.rows * p.pitch;
+  const size_t off = (size_t)(t + kGhostRows) * p.pitch + r;
+  const T* ln = lam + off;
+  T rho, ux, uy, E;
+  bool ok;
+  adj_node_state(f + off, plane, d, rho, ux, uy, E, ok);
+  if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
+  T G[4], g[4];
+  eq_cotangent<T>(rho, ux, uy, E, d, [&](int q) -> T { return ln[(size_t)q * plane]; }, G);
+  to_moment_cotangent<T>(rho, ux, uy, E, G, g);
+  const T keep = T(1) - (T)p.decay;
+  T* o = gsum + ((size_t)t * p.n_r + r) * 4;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) o[j] = keep * g[j];
+}
+
+// ---------------------------------------------------------------------------
+// Walls: for side s (0 inner, 1 outer) and row t, the equilibrium parameters
+// of the two ghost layers (Eq. 39, or the prescribed states) and the
+// cotangent g_wall that the ghosts return to the wall node (node 0) and the
+// next node inward (node 1).  ghost [side][layer][n_theta] EqParams;
+// gwall [side][node][n_theta][4].
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(64)
+    adjoint_wall_kernel(const T* __restrict__ f, const T* __restrict__ lam, EqParams<T>* __restrict__ ghost,
+                        T* __restrict__ gwall, const __grid_constant__ StepParams p,
+                        const __grid_constant__ DvmConst<T> d) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int side = blockIdx.y;
+  if (t >= p.n_theta) return;
+  const int plane = p.rows * p.pitch;
+  const int srow = t + kGhostRows;
+  const int step = side == 0 ? 1 : -1;                // towards the interior
+  const int out = -step;                              // the upwind offset that reads the ghosts
+  const int ra = side == 0 ? 0 : p.n_r - 1;
+  const T* fa = f + (size_t)srow * p.pitch + ra;
+  const T* fb = fa + step;
+  const T* la = lam + (size_t)srow * p.pitch + ra;
+  const T* lb = la + step;
+  const NodeState<T> a = node_moments(fa, plane, d);
+  const NodeState<T> b = node_moments(fb, plane, d);
+  const int kind = p.bc_kind[side] & ~PCLB_BC_NEQ;
+  double grho[2], gE[2];
+  T gux[2], guy[2];
+  grho[0] = 2.0 * a.rho_d - b.rho_d;  grho[1] = 2.0 * grho[0] - a.rho_d;   // Eq. (39), applied twice
+  gE[0] = 2.0 * a.E_d - b.E_d;        gE[1] = 2.0 * gE[0] - a.E_d;
+  gux[0] = T(2) * a.ux - b.ux;        gux[1] = T(2) * gux[0] - a.ux;
+  guy[0] = T(2) * a.uy - b.uy;        guy[1] = T(2) * guy[0] - a.uy;
+  if (kind != PCLB_BC_EXTRAP) {
+    const double c = p.cos_t[t], s = p.sin_t[t];
+    for (int l = 0; l < 2; ++l) {
+      const double* v = p.bc_vals + (size_t)((side * 2 + l) * 4) * p.n_theta + t;
+      gux[l] = (T)(v[1 * p.n_theta] * c - v[2 * p.n_theta] * s);
+      guy[l] = (T)(v[1 * p.n_theta] * s + v[2 * p.n_theta] * c);
+      if (kind == PCLB_BC_DIRICHLET) {
+        grho[l] = v[0];
+        gE[l] = v[3 * p.n_theta];
+      }
+    }
+  }
+  if (!(grho[0] > 0.0 && grho[1] > 0.0 && gE[0] > 0.0 && gE[1] > 0.0)) atomicOr(p.status, PCLB_FLAG_NONPHYS);
+  EqParams<T> e[2];
+  for (int l = 0; l < 2; ++l) {
+    e[l] = eq_params<T>(grho[l], gux[l], guy[l], gE[l], d);
+    ghost[(size_t)(side * 2 + l) * p.n_theta + t] = e[l];
+  }
+  T Gl[2][4];
+  for (int l = 0; l < 2; ++l) {
+    // cotangent of the ghost value f_q(layer l) = -sum_n lam_q(n) dM_q(n)/df_q(ghost l):
+    // the wall node a reads (a, g0, g1), the next node b reads (b, a, g0)
+    auto ghost_lam = [&](int q) -> T {
+      const Cour<T> c = courant<T>(p, d, q, srow);
+      if (c.up_r != out) return T(0);
+      const T f_a = fa[(size_t)q * plane], f_b = fb[(size_t)q * plane];
+      const T g0 = adj_feq<T>(e[0], d, q), g1 = adj_feq<T>(e[1], d, q);
+      T MDa, MPa, MDb, MPb;
+      mwb_partials<T>(c.a_r, c.k_r, f_a - g0, g0 - g1, MDa, MPa);
+      mwb_partials<T>(c.a_r, c.k_r, f_b - f_a, f_a - g0, MDb, MPb);
+      const T lam_a = la[(size_t)q * plane], lam_b = lb[(size_t)q * plane];
+      if (l == 0) return lam_a * (MDa - MPa) + lam_b * MPb;
+      return lam_a * MPa;
+    };
+    eq_cotangent<T>((T)grho[l], gux[l], guy[l], (T)gE[l], d, ghost_lam, Gl[l]);
+  }
+  // back through the extrapolation g0 = 2a - b, g1 = 3a - 2b (extrapolated components only)
+  const bool ext_rho_E = kind != PCLB_BC_DIRICHLET;
+  const bool ext_u = kind == PCLB_BC_EXTRAP;
+  T Ga[4], Gb[4];
+  for (int j = 0; j < 4; ++j) {
+    const bool ext = (j == 0 || j == 3) ? ext_rho_E : ext_u;
+    Ga[j] = ext ? T(2) * Gl[0][j] + T(3) * Gl[1][j] : T(0);
+    Gb[j] = ext ? -Gl[0][j] - T(2) * Gl[1][j] : T(0);
+  }
+  T ga[4], gb[4];
+  to_moment_cotangent<T>(a.rho, a.ux, a.uy, a.E, Ga, ga);
+  to_moment_cotangent<T>(b.rho, b.ux, b.uy, b.E, Gb, gb);
+  for (int j = 0; j < 4; ++j) {
+    gwall[((size_t)(side * 2 + 0) * p.n_theta + t) * 4 + j] = ga[j];
+    gwall[((size_t)(side * 2 + 1) * p.n_theta + t) * 4 + j] = gb[j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pair-streaming part.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(AdjSize<T>::threads)
+    adjoint_pair_kernel(const __grid_constant__ CUtensorMap tmap_f, const __grid_constant__ CUtensorMap tmap_l,
+                        const T* __restrict__ f, const T* __restrict__ lam_in, T* __restrict__ lam_out,
+                        const EqParams<T>* __restrict__ ghost, const T* __restrict__ gwall,
+                        const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
   constexpr int TT = AdjTile<T>::TT;
   constexpr int PLANE = AdjSize<T>::plane;
+  constexpr int NP = AdjSize<T>::npairs, RC = AdjSize<T>::rcols, PROD = AdjSize<T>::prod;
+  constexpr int S = kAdjStages;
+  // offsets inside one label's products
+  constexpr int AR = 0, BR = TT * RC, AT = 2 * TT * RC, BT = 2 * TT * RC + (TT + 4) * kTileR;
+  constexpr uint32_t kStageBytes = (uint32_t)(4 * PLANE * sizeof(T));
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  T* sf = reinterpret_cast<T*>(smem_raw);
-  T* sl = sf + kQ * PLANE;
-  T* prod = sl + kQ * PLANE;                        // [buffer][label][products]
-  T* gw = prod + 2 * 2 * AdjSize<T>::prod;          // [side][node][TT][4]
-  T* invr = gw + 2 * 2 * TT * 4;                    // 1/r of the tile columns
-  CourEntry<T>* ctab = reinterpret_cast<CourEntry<T>*>(invr + kTileR);   // [TT + 4][npairs]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(ctab + (TT + 4) * AdjSize<T>::npairs);   // [0] f, [1] lam
+  T* ring = reinterpret_cast<T*>(smem_raw);                 // [stage][f q1, f q2, lam q1, lam q2][PLANE]
+  T* prod = ring + S * 4 * PLANE;                             // [buffer][label][products]
+  T* invr = prod + 2 * 2 * PROD;                              // 1/r of the tile columns
+  CourEntry<T>* ctab = reinterpret_cast<CourEntry<T>*>(invr + kTileR);   // [TT + 4][NP]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ctab + (TT + 4) * NP);     // [S]
 
   const int r0 = blockIdx.x * kTileR;
   const int t0 = blockIdx.y * TT;
   const int tid = threadIdx.x;
   const int lane = tid & 31, rowl = tid >> 5;
 
+  // the planes of pair pr (labels q1, q1 + N_i/2) into stage s (thread 0)
+  auto issue_pair = [&](int pr, int s) {
+    const int k = 1 + pr / (kNDirs / 2);
+    const int q1 = 1 + (k - 1) * kNDirs + pr % (kNDirs / 2), q2 = q1 + kNDirs / 2;
+    T* st = ring + s * 4 * PLANE;
+    mbar_arrive_expect_tx(&bar[s], kStageBytes);
+    tma_load_3d(st, &tmap_f, r0 - kLeft, t0, q1, &bar[s]);
+    tma_load_3d(st + PLANE, &tmap_f, r0 - kLeft, t0, q2, &bar[s]);
+    tma_load_3d(st + 2 * PLANE, &tmap_l, r0 - kLeft, t0, q1, &bar[s]);
+    tma_load_3d(st + 3 * PLANE, &tmap_l, r0 - kLeft, t0, q2, &bar[s]);
+  };
   if (tid == 0) {
     tma_prefetch_desc(&tmap_f);
     tma_prefetch_desc(&tmap_l);
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
     mbar_fence_init();
   }
-  for (int i = tid; i < 2 * 2 * TT * 4; i += blockDim.x) gw[i] = T(0);
   if (tid < kTileR) invr[tid] = r0 + tid < p.n_r ? (T)p.inv_r[r0 + tid] : T(1);
   // Courant entries of the stored rows t0 .. t0 + TT + 3 (theta rows t0 - 2 .. t0 + TT + 1)
-  for (int i = tid; i < (TT + 4) * AdjSize<T>::npairs; i += blockDim.x) {
-    const int srow = t0 + i / AdjSize<T>::npairs, pair = i % AdjSize<T>::npairs;
+  for (int i = tid; i < (TT + 4) * NP; i += blockDim.x) {
+    const int srow = t0 + i / NP, pr = i % NP;
     CourEntry<T> e{T(0), T(0), T(0), 0};
-    if (srow < p.rows) courant_entry(p, srow, pair, e.a_r, e.k_r, e.a_w, e.fl);
+    if (srow < p.rows) courant_entry(p, srow, pr, e.a_r, e.k_r, e.a_w, e.fl);
     ctab[i] = e;
   }
   __syncthreads();
-  if (tid == 0) {
-    mbar_arrive_expect_tx(&bar[0], (uint32_t)(kQ * PLANE * sizeof(T)));
-    mbar_arrive_expect_tx(&bar[1], (uint32_t)(kQ * PLANE * sizeof(T)));
-#pragma unroll 1
-    for (int q = 0; q < kQ; ++q) tma_load_3d(sf + q * PLANE, &tmap_f, r0 - kLeft, t0, q, &bar[0]);
-#pragma unroll 1
-    for (int q = 0; q < kQ; ++q) tma_load_3d(sl + q * PLANE, &tmap_l, r0 - kLeft, t0, q, &bar[1]);
+  // bits 2..6 of the tile rows' flags: bit 1 (v_theta < 0 for q1) of the rows
+  // -2 .. +2 around them, the rows whose azimuthal stencils reach the node
+  for (int i = tid; i < TT * NP; i += blockDim.x) {
+    const int w = 2 + i / NP, pr = i % NP;
+    int m = 0;
+#pragma unroll
+    for (int o = 0; o < 5; ++o) m |= ((ctab[(w - 2 + o) * NP + pr].fl >> 1) & 1) << o;
+    ctab[w * NP + pr].fl |= m << 2;
   }
-  // f first (moments, ghost columns); lam is awaited before it is first read
-  const bool f_ok = mbar_wait_bounded(&bar[0], 0, kAdjWaitNs);
-  if (__syncthreads_or(!f_ok)) {
-    if (tid == 0) {
-      atomicOr(p.status, PCLB_FLAG_TIMEOUT);
-      mbar_wait_bounded(&bar[0], 0, kAdjWaitNs);
-      mbar_wait_bounded(&bar[1], 0, kAdjWaitNs);
-    }
-    return;
-  }
-
-  // ---- radial ghost columns of f, exactly as the forward step ---------------
-  const int cw_out = p.n_r - 1 - r0 + kLeft;
-  const bool inner = r0 == 0;
-  const bool outer = cw_out <= kLeft + kTileR;
-  if (inner && rowl == 0 && lane < TT && t0 + lane < p.n_theta)
-    fill_ghost_columns<T, PLANE>(sf, 2 + lane, 0, kLeft, t0 + lane, p, d);
-  if (outer && rowl == 1 && lane < TT && t0 + lane < p.n_theta)
-    fill_ghost_columns<T, PLANE>(sf, 2 + lane, 1, cw_out, t0 + lane, p, d);
   __syncthreads();
+  if (tid == 0)
+    for (int s = 0; s < S && s < NP; ++s) issue_pair(s, s);
 
-  // this thread's node moments (f only), while lam is still landing
+  // ---- this thread's node -----------------------------------------------------
   const int row = 2 + rowl;
   const int col = kLeft + lane;
   const int t = t0 + rowl;
   const int r = r0 + lane;
   const bool valid = r < p.n_r && t < p.n_theta;
   const int srow = t + kGhostRows;
-  T n_rho = T(1), n_ux = T(0), n_uy = T(0), n_E = T(1);
-  if (valid) {
-    bool ok;
-    adj_node_state(sf + row * kWinR + col, PLANE, d, n_rho, n_ux, n_uy, n_E, ok);
-    if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
-  }
-  const bool l_ok = mbar_wait_bounded(&bar[1], 0, kAdjWaitNs);
-  if (__syncthreads_or(!l_ok)) {
-    if (tid == 0) {
-      atomicOr(p.status, PCLB_FLAG_TIMEOUT);
-      mbar_wait_bounded(&bar[1], 0, kAdjWaitNs);
-    }
-    return;
-  }
-
-  // ---- cotangent returned by the ghost nodes to the two wall nodes ---------
-  auto wall_feedback = [&](int side, int rl) {
-    const int row = 2 + rl;
-    const int srow = t0 + rl + kGhostRows;             // stored row of this theta node
-    const int t = t0 + rl;
-    const int step = side == 0 ? 1 : -1;
-    const int ca = side == 0 ? kLeft : cw_out;          // wall node column
-    const int cb = ca + step;                           // next node inward
-    const int outward = -step;                          // upwind offset that reads the ghosts
-    const NodeState<T> a = node_moments(sf + row * kWinR + ca, PLANE, d);
-    const NodeState<T> b = node_moments(sf + row * kWinR + cb, PLANE, d);
-    const int kind = p.bc_kind[side] & ~PCLB_BC_NEQ;
-    T st[2][4];   // ghost states (rho, ux, uy, E), layers 0 and 1
-    st[0][0] = T(2) * a.rho - b.rho;  st[1][0] = T(2) * st[0][0] - a.rho;
-    st[0][1] = T(2) * a.ux - b.ux;    st[1][1] = T(2) * st[0][1] - a.ux;
-    st[0][2] = T(2) * a.uy - b.uy;    st[1][2] = T(2) * st[0][2] - a.uy;
-    st[0][3] = T(2) * a.E - b.E;      st[1][3] = T(2) * st[0][3] - a.E;
-    if (kind != PCLB_BC_EXTRAP) {
-      const double c = p.cos_t[t], s = p.sin_t[t];
-      for (int l = 0; l < 2; ++l) {
-        const double* v = p.bc_vals + (size_t)((side * 2 + l) * 4) * p.n_theta + t;
-        st[l][1] = (T)(v[1 * p.n_theta] * c - v[2 * p.n_theta] * s);
-        st[l][2] = (T)(v[1 * p.n_theta] * s + v[2 * p.n_theta] * c);
-        if (kind == PCLB_BC_DIRICHLET) {
-          st[l][0] = (T)v[0];
-          st[l][3] = (T)v[3 * p.n_theta];
-        }
-      }
-    }
-    T Gl[2][4];
-    for (int l = 0; l < 2; ++l) {
-      // cotangent of ghost value f_q(layer l) = -sum_n lam_q(n) dM_q(n)/d f_q(ghost l)
-      auto ghost_lam = [&](int q) -> T {
-        const Cour<T> c = courant<T>(p, d, q, srow);
-        if (c.up_r != outward) return T(0);
-        const T* fp = sf + q * PLANE + row * kWinR;
-        const T* lp = sl + q * PLANE + row * kWinR;
-        T MDa, MPa, MDb, MPb;
-        mwb_partials<T>(c.a_r, c.k_r, fp[ca] - fp[ca + outward], fp[ca + outward] - fp[ca + 2 * outward],
-                        MDa, MPa);
-        mwb_partials<T>(c.a_r, c.k_r, fp[cb] - fp[cb + outward], fp[cb + outward] - fp[cb + 2 * outward],
-                        MDb, MPb);
-        if (l == 0) return lp[ca] * (MDa - MPa) + lp[cb] * MPb;
-        return lp[ca] * MPa;
-      };
-      eq_cotangent<T>(st[l][0], st[l][1], st[l][2], st[l][3], d, ghost_lam, Gl[l]);
-    }
-    // back through the extrapolation g0 = 2a - b, g1 = 3a - 2b (extrapolated components only)
-    const bool ext_rho_E = kind != PCLB_BC_DIRICHLET;
-    const bool ext_u = kind == PCLB_BC_EXTRAP;
-    T Ga[4], Gb[4];
-    for (int j = 0; j < 4; ++j) {
-      const bool ext = (j == 0 || j == 3) ? ext_rho_E : ext_u;
-      Ga[j] = ext ? T(2) * Gl[0][j] + T(3) * Gl[1][j] : T(0);
-      Gb[j] = ext ? -Gl[0][j] - T(2) * Gl[1][j] : T(0);
-    }
-    T ga[4], gb[4];
-    to_moment_cotangent<T>(a.rho, a.ux, a.uy, a.E, Ga, ga);
-    to_moment_cotangent<T>(b.rho, b.ux, b.uy, b.E, Gb, gb);
-    for (int j = 0; j < 4; ++j) {
-      gw[((side * 2 + 0) * TT + rl) * 4 + j] = ga[j];
-      gw[((side * 2 + 1) * TT + rl) * 4 + j] = gb[j];
-    }
-  };
-  if (inner && rowl == 0 && lane < TT && t0 + lane < p.n_theta) wall_feedback(0, lane);
-  if (outer && rowl == 1 && lane < TT && t0 + lane < p.n_theta) wall_feedback(1, lane);
-
-  // ---- this thread's node: cotangent of its equilibrium ----------------------
-  T g[4] = {T(0), T(0), T(0), T(0)};
-  if (valid) {
-    T G[4];
-    eq_cotangent<T>(n_rho, n_ux, n_uy, n_E, d, [&](int q) -> T { return sl[q * PLANE + row * kWinR + col]; }, G);
-    to_moment_cotangent<T>(n_rho, n_ux, n_uy, n_E, G, g);
-  }
-  __syncthreads();   // wall feedback ready
-  // gs = (1 - d) g + g_wall: every label receives psi_q . gs
-  const T decay = (T)p.decay;
-  T gs[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    T w = T(0);
-    if (inner && r == 0) w += gw[((0 * 2 + 0) * TT + rowl) * 4 + j];
-    if (inner && r == 1) w += gw[((0 * 2 + 1) * TT + rowl) * 4 + j];
-    if (outer && r == p.n_r - 1) w += gw[((1 * 2 + 0) * TT + rowl) * 4 + j];
-    if (outer && r == p.n_r - 2) w += gw[((1 * 2 + 1) * TT + rowl) * 4 + j];
-    gs[j] = (T(1) - decay) * g[j] + w;
-  }
-
   const size_t plane_out = (size_t)p.rows * p.pitch;
-  const int win = row * kWinR + col;
+  const T decay = (T)p.decay;
+  T gs[4] = {T(0), T(0), T(0), T(0)};
+  if (valid) {
+    // (1 - d) g of this node, read from global memory while the first pairs'
+    // windows land (the TMA copies then mostly hit L2)
+    const int plane = p.rows * p.pitch;
+    const size_t off = (size_t)srow * p.pitch + r;
+    const T* ln = lam_in + off;
+    T rho, ux, uy, E;
+    bool nok;
+    adj_node_state(f + off, plane, d, rho, ux, uy, E, nok);
+    if (!nok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
+    T G[4], g[4];
+    eq_cotangent<T>(rho, ux, uy, E, d, [&](int q) -> T { return ln[(size_t)q * plane]; }, G);
+    to_moment_cotangent<T>(rho, ux, uy, E, G, g);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) gs[j] = (T(1) - decay) * g[j];
+    // the cotangent the ghost nodes return to the two nodes next to each wall
+    auto add_wall = [&](int side, int node) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) gs[j] += gwall[((size_t)(side * 2 + node) * p.n_theta + t) * 4 + j];
+    };
+    if (r == 0) add_wall(0, 0);
+    if (r == 1) add_wall(0, 1);
+    if (r == p.n_r - 1) add_wall(1, 0);
+    if (r == p.n_r - 2) add_wall(1, 1);
+  }
+  const int o_node = row * kWinR + col;                 // this node in a window plane
+  const int p_rad = AR + rowl * RC + lane + 2;          // its radial product slot
+  const int p_az = AT + row * kTileR + lane;            // its azimuthal product slot
+  const T my_invr = invr[lane];
   auto store = [&](int q, T v) {
     lam_out[(size_t)q * plane_out + (size_t)srow * p.pitch + r] = v;
     if (t >= p.n_theta - 2)
@@ -320,59 +460,81 @@ __global__ void __launch_bounds__(AdjTile<T>::TT * 32, 1)
     if (t < 2) lam_out[(size_t)d.recv_hi[q] * plane_out + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r] = v;
   };
   // rest velocity: no convection
-  if (valid) store(0, decay * sl[win] + gs[0] + gs[3] * d.half_v2[0]);
+  if (valid) store(0, decay * lam_in[(size_t)srow * p.pitch + r] + gs[0] + gs[3] * d.half_v2[0]);
 
-  constexpr int NP = AdjSize<T>::npairs, RC = AdjSize<T>::rcols, PROD = AdjSize<T>::prod;
-  // offsets inside one label's products
-  constexpr int AR = 0, BR = TT * RC, AT = 2 * TT * RC, BT = 2 * TT * RC + (TT + 4) * kTileR;
+  // wall tiles: the ghost states of the rows this thread fills (warp 0: inner, warp 1: outer)
+  const int cw_out = p.n_r - 1 - r0 + kLeft;
+  const bool inner = r0 == 0, outer = cw_out <= kLeft + kTileR;
+  const bool wall_tile = inner || outer;
+  const int gside = rowl == 0 ? 0 : 1;
+  const bool fills = wall_tile && rowl < 2 && lane < TT && t0 + lane < p.n_theta && (gside == 0 ? inner : outer);
+  const EqParams<T>* eg = ghost + (size_t)(gside * 2) * p.n_theta + t0 + lane;   // layer l at + l n_theta
+
+  bool ok = true;
+  int brk = NP;                                         // the pair at which a wait timed out
 #pragma unroll 1
   for (int pair = 0; pair < NP; ++pair) {
     const int k = 1 + pair / (kNDirs / 2);
     const int q1 = 1 + (k - 1) * kNDirs + pair % (kNDirs / 2);
     const int q2 = q1 + kNDirs / 2;                      // opposite velocity
-    T* pb = prod + (pair & 1) * 2 * PROD;                // this pair's buffer: [label][products]
+    const int s = pair % S;
+    const T* st = ring + s * 4 * PLANE;
+    T* pb = prod + (pair & 1) * 2 * PROD;                // this pair's products: [label][...]
+    if (ok) ok = mbar_wait_bounded(&bar[s], (uint32_t)((pair / S) & 1), kAdjWaitNs);
+    if (wall_tile) {
+      // radial ghost columns of this pair's f planes (f = f^eq of the ghost states)
+      if (fills && ok) {
+        T* fw = const_cast<T*>(st) + (2 + lane) * kWinR;
+        const int c0 = gside == 0 ? kLeft : cw_out, stp = gside == 0 ? 1 : -1;
+        for (int l = 0; l < 2; ++l) {
+          const int c = c0 - stp * (1 + l);
+          if (c < 0 || c >= kWinR) continue;
+          const EqParams<T> e = eg[(size_t)l * p.n_theta];
+          fw[c] = adj_feq<T>(e, d, q1);
+          fw[PLANE + c] = adj_feq<T>(e, d, q2);
+        }
+      }
+      __syncthreads();
+    }
 
     // (A) products lam(n) M_D(n), lam(n) M_Dp(n) of every node that can reach the
     // tile.  Warp w forms those of tile row w at its 32 columns (both labels),
-    // lanes 0..3 the two halo columns of each label on its upwind side, and
     // warps 0..3 the halo rows -2, -1, TT, TT + 1 for the label whose upwind
-    // side points into the tile.
+    // side points into the tile, and the next warps the halo columns.  The
+    // upwind sides are uniform across a warp (one row), so each warp takes a
+    // branch in which the stencil offsets are constants.
+    const T* sfp = st;                                    // f q1, f q2 at +PLANE
+    const T* slp = st + 2 * PLANE;                        // lam q1, lam q2 at +PLANE
+    const CourEntry<T> e = ctab[row * NP + pair];
+    const int fl_c = e.fl;                                // flags of this node's row
+    T lam_c[2];                                           // lam^{n+1} of both labels at this node
+    if (fl_c & 1)
+      radial_pair<T, 1, PLANE, PROD, BR - AR>(sfp, slp, pb, o_node, p_rad, e.a_r, e.k_r, lam_c);
+    else
+      radial_pair<T, -1, PLANE, PROD, BR - AR>(sfp, slp, pb, o_node, p_rad, e.a_r, e.k_r, lam_c);
     {
-      const CourEntry<T> e = ctab[row * NP + pair];
-      auto radial = [&](int L, int uL, int c) {
-        const int o = row * kWinR + c + kLeft;
-        const T* fw = sf + (L ? q2 : q1) * PLANE + o;
-        T MD, MP;
-        mwb_partials<T>(e.a_r, e.k_r, fw[0] - fw[uL], fw[uL] - fw[2 * uL], MD, MP);
-        const T lam = sl[(L ? q2 : q1) * PLANE + o];
-        pb[L * PROD + AR + rowl * RC + c + 2] = lam * MD;
-        pb[L * PROD + BR + rowl * RC + c + 2] = lam * MP;
-      };
-      auto azimuthal = [&](int L, int uL, int rr, T at, T kt) {
-        const int o = rr * kWinR + lane + kLeft;
-        const T* fw = sf + (L ? q2 : q1) * PLANE + o;
-        T MD, MP;
-        mwb_partials<T>(at, kt, fw[0] - fw[uL * kWinR], fw[uL * kWinR] - fw[2 * uL * kWinR], MD, MP);
-        const T lam = sl[(L ? q2 : q1) * PLANE + o];
-        pb[L * PROD + AT + rr * kTileR + lane] = lam * MD;
-        pb[L * PROD + BT + rr * kTileR + lane] = lam * MP;
-      };
-      const int u = (e.fl & 1) ? 1 : -1;                 // radial upwind offset of q1 in this row
-      const int un = (e.fl & 2) ? 1 : -1;                // azimuthal upwind offset of q1 in this row
-      radial(0, u, lane);
-      radial(1, -u, lane);
-      const T at = e.a_w * invr[lane], kt = at - at * at;
-      azimuthal(0, un, row, at, kt);
-      azimuthal(1, -un, row, at, kt);
-      if (rowl < 4) {
-        // halo rows: warps 0..3 take window rows 0, 1, TT + 2, TT + 3
-        const int rr = rowl < 2 ? rowl : TT + rowl;
-        const CourEntry<T> eh = ctab[rr * NP + pair];
-        const int unh = (eh.fl & 2) ? 1 : -1;
-        const int need = rr < 2 ? 1 : -1;
-        const T ath = eh.a_w * invr[lane], kth = ath - ath * ath;
-        azimuthal(unh == need ? 0 : 1, need, rr, ath, kth);
-      }
+      const T at = e.a_w * my_invr, kt = at - at * at;
+      if (fl_c & 2)
+        azimuthal_pair<T, kWinR, PLANE, PROD, BT - AT>(sfp, lam_c, pb, o_node, p_az, at, kt);
+      else
+        azimuthal_pair<T, -kWinR, PLANE, PROD, BT - AT>(sfp, lam_c, pb, o_node, p_az, at, kt);
+    }
+    if (rowl < 4) {
+      // halo rows: warps 0..3 take window rows 0, 1, TT + 2, TT + 3; rows
+      // above the tile are read by labels whose upwind side is +theta
+      const int rr = rowl < 2 ? rowl : TT + rowl;
+      const CourEntry<T> eh = ctab[rr * NP + pair];
+      const bool q1_up_pos = (eh.fl & 2) != 0;
+      const T ath = eh.a_w * my_invr, kth = ath - ath * ath;
+      const int o = rr * kWinR + col;
+      if (rowl < 2)
+        azimuthal_one<T, kWinR>(sfp + (q1_up_pos ? 0 : PLANE) + o, slp + (q1_up_pos ? 0 : PLANE) + o,
+                                pb + (q1_up_pos ? 0 : PROD) + AT + rr * kTileR + lane, BT - AT, ath, kth);
+      else
+        azimuthal_one<T, -kWinR>(sfp + (q1_up_pos ? PLANE : 0) + o, slp + (q1_up_pos ? PLANE : 0) + o,
+                                 pb + (q1_up_pos ? PROD : 0) + AT + rr * kTileR + lane, BT - AT, ath, kth);
+    }
+    {
       // halo columns: 4 per tile row (label, column); the warps after the first
       // four take them, or warp 0 as well when the tile has too few rows.
       // Upwind at larger r (+1) reads the tile from columns -2, -1, at
@@ -387,68 +549,101 @@ __global__ void __launch_bounds__(AdjTile<T>::TT * 32, 1)
           const int uh = (eh.fl & 1) ? 1 : -1, uL = L ? -uh : uh;
           const int c = uL == 1 ? j - 2 : kTileR + j;
           const int o = (hr + 2) * kWinR + c + kLeft;
-          const T* fw = sf + (L ? q2 : q1) * PLANE + o;
+          const T* fw = sfp + L * PLANE + o;
           T MD, MP;
           mwb_partials<T>(eh.a_r, eh.k_r, fw[0] - fw[uL], fw[uL] - fw[2 * uL], MD, MP);
-          const T lam = sl[(L ? q2 : q1) * PLANE + o];
+          const T lam = slp[L * PLANE + o];
           pb[L * PROD + AR + hr * RC + c + 2] = lam * MD;
           pb[L * PROD + BR + hr * RC + c + 2] = lam * MP;
         }
       }
     }
-    __syncthreads();
+    if (__syncthreads_or(!ok)) {
+      brk = pair;
+      break;
+    }
+    // the stage of this pair is free: the planes of pair + S start now
+    if (tid == 0 && pair + S < NP) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_pair(pair + S, s);
+    }
 
     // (B) gather at this node: node n = c + j u_n reads f(n), f(n + u_n),
     // f(n + 2 u_n), so dM(n)/df(n) = M_D, dM(n)/df(n + u_n) = M_Dp - M_D,
     // dM(n)/df(n + 2 u_n) = -M_Dp.
     if (valid) {
-      const CourEntry<T>* cr = ctab + rowl * NP + pair;  // rows rowl - 2 .. rowl + 2 at stride NP
-      const int u = (cr[2 * NP].fl & 1) ? 1 : -1;
-      int tneg = 0;                                       // bit o: row o - 2 has v_theta < 0 for q1
-#pragma unroll
-      for (int o = 0; o < 5; ++o) tneg |= ((cr[o * NP].fl >> 1) & 1) << o;
+      T acc[2];
+      if (fl_c & 1)
+        gather_radial<T, 1, PROD, BR - AR>(pb, p_rad, acc);
+      else
+        gather_radial<T, -1, PROD, BR - AR>(pb, p_rad, acc);
+      const int tneg = fl_c >> 2;                        // bit o: row o - 2 has v_theta < 0 for q1
+      if (tneg == 0)
+        gather_azimuthal<T, kTileR, PROD, BT - AT>(pb, p_az, acc);
+      else if (tneg == 31)
+        gather_azimuthal<T, -kTileR, PROD, BT - AT>(pb, p_az, acc);
+      else
+        gather_azimuthal_mixed<T, PROD, BT - AT>(pb, p_az, tneg, acc);
       const T A = gs[0] + gs[3] * d.half_v2[k];
       const T B = gs[1] * d.vx[q1] + gs[2] * d.vy[q1];
-#pragma unroll
-      for (int L = 0; L < 2; ++L) {
-        const T* P = pb + L * PROD;
-        const int uL = L ? -u : u;
-        const int neg = L ? (tneg ^ 0x1f) : tneg;        // the partner has the opposite velocity
-        const int cc = lane + 2;
-        T acc = P[AR + rowl * RC + cc] - P[AR + rowl * RC + cc - uL] + P[BR + rowl * RC + cc - uL] -
-                P[BR + rowl * RC + cc - 2 * uL];
-        const int rr = rowl + 2;
-        acc += P[AT + rr * kTileR + lane];
-        if (neg & 2) acc += P[BT + (rr - 1) * kTileR + lane] - P[AT + (rr - 1) * kTileR + lane];
-        if (!(neg & 8)) acc += P[BT + (rr + 1) * kTileR + lane] - P[AT + (rr + 1) * kTileR + lane];
-        if (neg & 1) acc -= P[BT + (rr - 2) * kTileR + lane];
-        if (!(neg & 16)) acc -= P[BT + (rr + 2) * kTileR + lane];
-        const int q = L ? q2 : q1;
-        store(q, decay * sl[q * PLANE + win] + (L ? A - B : A + B) - acc);
-      }
+      store(q1, decay * lam_c[0] + (A + B) - acc[0]);
+      store(q2, decay * lam_c[1] + (A - B) - acc[1]);
+    }
+  }
+  if (brk < NP && tid == 0) {
+    // a copy did not land in time: report it, give the copies still in
+    // flight (the last one issued into each stage) a bounded time to finish
+    atomicOr(p.status, PCLB_FLAG_TIMEOUT);
+    const int issued = brk + S < NP ? brk + S : NP;
+    for (int s = 0; s < S && s < issued; ++s) {
+      const int last = s + ((issued - 1 - s) / S) * S;
+      mbar_wait_bounded(&bar[s], (uint32_t)((last / S) & 1), kAdjWaitNs);
     }
   }
 }
 
 template <class T>
-cudaError_t launch_adjoint(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, T* lam_out, const StepParams& p,
-                           const DvmConst<T>& d, cudaStream_t stream) {
+cudaError_t launch_adjoint(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, const T* f, const T* lam_in,
+                           T* lam_out, const AdjScratch& ws, const StepParams& p, const DvmConst<T>& d,
+                           cudaStream_t stream) {
   static bool configured = false;
   constexpr int smem = AdjSize<T>::smem;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(adjoint_pair_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
+  EqParams<T>* ghost = reinterpret_cast<EqParams<T>*>(ws.ghost);
+  T* gwall = reinterpret_cast<T*>(ws.gwall);
+  adjoint_wall_kernel<T><<<dim3((p.n_theta + 63) / 64, 2), 64, 0, stream>>>(f, lam_in, ghost, gwall, p, d);
   constexpr int TT = AdjTile<T>::TT;
-  dim3 grid((p.n_r + kTileR - 1) / kTileR, (p.n_theta + TT - 1) / TT);
-  adjoint_kernel<T><<<grid, TT * 32, smem, stream>>>(*tmap_f, *tmap_l, lam_out, p, d);
+  dim3 g((p.n_r + kTileR - 1) / kTileR, (p.n_theta + TT - 1) / TT);
+  adjoint_pair_kernel<T><<<g, AdjSize<T>::threads, smem, stream>>>(*tmap_f, *tmap_l, f, lam_in, lam_out, ghost,
+                                                                   gwall, p, d);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_adjoint<float>(const CUtensorMap*, const CUtensorMap*, float*, const StepParams&,
-                                           const DvmConst<float>&, cudaStream_t);
-template cudaError_t launch_adjoint<double>(const CUtensorMap*, const CUtensorMap*, double*, const StepParams&,
-                                            const DvmConst<double>&, cudaStream_t);
+size_t adjoint_scratch_bytes(int n_r, int n_theta, int elem) {
+  // gsum: 4 per node; ghost: 2 x 2 EqParams (10 values) per row; gwall: 2 x 2 x 4 per row
+  const size_t a = (size_t)n_r * n_theta * 4 * elem, b = (size_t)4 * n_theta * 10 * elem, c = (size_t)16 * n_theta * elem;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  return up(a) + up(b) + up(c);
+}
+
+AdjScratch adjoint_scratch(unsigned char* base, int n_r, int n_theta, int elem) {
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  AdjScratch s;
+  s.gsum = base;
+  s.ghost = base + up((size_t)n_r * n_theta * 4 * elem);
+  s.gwall = s.ghost + up((size_t)4 * n_theta * 10 * elem);
+  return s;
+}
+
+template cudaError_t launch_adjoint<float>(const CUtensorMap*, const CUtensorMap*, const float*, const float*, float*,
+                                           const AdjScratch&, const StepParams&, const DvmConst<float>&, cudaStream_t);
+template cudaError_t launch_adjoint<double>(const CUtensorMap*, const CUtensorMap*, const double*, const double*,
+                                            double*, const AdjScratch&, const StepParams&, const DvmConst<double>&,
+                                            cudaStream_t);
 
 }  // namespace pclb

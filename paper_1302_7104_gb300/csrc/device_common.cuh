@@ -109,6 +109,19 @@ struct NodeState {
 // T = (e - |j|^2 / (2 rho)) / rho is recovered in double.
 // FP64: plain double sums.
 // ---------------------------------------------------------------------------
+// 1/n by the Newton-Raphson iteration r <- r (2 - n r) from the hardware's
+// approximate reciprocal; each step doubles the number of correct bits, two
+// reach full double precision (checked against the division in the parity
+// tests).  n must be a positive normal number.
+__device__ __forceinline__ double recip_newton(double n) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(n));
+  double e = fma(-n, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-n, r, 1.0);
+  return fma(r, e, r);
+}
+
 __device__ __forceinline__ double recip_refined(double x) {
   // Newton-Raphson step y1 = y0 (2 - x y0) on a single-precision seed.
   double y0 = (double)__frcp_rn((float)x);

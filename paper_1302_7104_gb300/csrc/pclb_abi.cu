@@ -36,8 +36,8 @@ cudaError_t launch_diagnostics(const T*, double*, double*, const StepParams&, co
 template <class T>
 cudaError_t launch_noneq(const T*, T*, int, const StepParams&, const DvmConst<T>&, cudaStream_t);
 template <class T>
-cudaError_t launch_adjoint(const CUtensorMap*, const CUtensorMap*, T*, const StepParams&, const DvmConst<T>&,
-                           cudaStream_t);
+cudaError_t launch_adjoint(const CUtensorMap*, const CUtensorMap*, const T*, const T*, T*, const AdjScratch&,
+                           const StepParams&, const DvmConst<T>&, cudaStream_t);
 template <class T>
 cudaError_t launch_moments_vjp(const T*, const T*, const T*, const T*, const T*, T*, const StepParams&,
                                const DvmConst<T>&, cudaStream_t);
@@ -132,6 +132,7 @@ Layout make_layout(const pclb_grid* g, pclb_precision prec) {
   L.partials = off; off = align_up(off + (size_t)kDiagBlocks * 8 * 8, 256);
   L.diag_out = off; off = align_up(off + 8 * 8, 256);
   L.stage = off; off = align_up(off + (size_t)8 * g->n_r * g->n_theta * es, 256);
+  L.adj_scratch = off; off = align_up(off + adjoint_scratch_bytes(g->n_r, g->n_theta, (int)es), 256);
   L.total = off;
   return L;
 }
@@ -313,10 +314,14 @@ pclb_status do_step(pclb_ctx* ctx, int n) {
 }
 
 template <class T>
-pclb_status do_adjoint(pclb_ctx* ctx, const CUtensorMap* tmap_f) {
+pclb_status do_adjoint(pclb_ctx* ctx, const CUtensorMap* tmap_f, const void* f) {
   const int src = ctx->cur_lam, dst = 1 - ctx->cur_lam;
-  cudaError_t e = launch_adjoint<T>(tmap_f, &ctx->tmap_adj[3 + src], reinterpret_cast<T*>(ctx->ws + ctx->lay.lam[dst]),
-                                    ctx->sp, dvm_of<T>(ctx), ctx->stream);
+  const AdjScratch ws = adjoint_scratch(ctx->ws + ctx->lay.adj_scratch, ctx->grid.n_r, ctx->grid.n_theta,
+                                        (int)sizeof(T));
+  cudaError_t e = launch_adjoint<T>(tmap_f, &ctx->tmap_adj[3 + src], reinterpret_cast<const T*>(f),
+                                    reinterpret_cast<const T*>(ctx->ws + ctx->lay.lam[src]),
+                                    reinterpret_cast<T*>(ctx->ws + ctx->lay.lam[dst]), ws, ctx->sp, dvm_of<T>(ctx),
+                                    ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint kernel launch");
   ctx->cur_lam = dst;
   return PCLB_OK;
@@ -739,15 +744,17 @@ pclb_status pclb_adjoint_state(pclb_ctx* ctx, const void* f_state) {
   if (!ctx->has_lam) return fail(ctx, PCLB_ESTATE, "no adjoint variable: call pclb_lambda_set or pclb_moments_vjp");
   const CUtensorMap* map;
   CUtensorMap local;
+  const void* f = f_state;
   if (f_state == nullptr) {
     if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
     map = &ctx->tmap_adj[ctx->cur];
+    f = ctx->ws + ctx->lay.f[ctx->cur];
   } else {
     pclb_status st = encode_map(ctx, f_state, adj_box_rows(ctx), &local);
     if (st != PCLB_OK) return st;
     map = &local;
   }
-  return ctx->prec == PCLB_FP32 ? do_adjoint<float>(ctx, map) : do_adjoint<double>(ctx, map);
+  return ctx->prec == PCLB_FP32 ? do_adjoint<float>(ctx, map, f) : do_adjoint<double>(ctx, map, f);
 }
 
 pclb_status pclb_adjoint_step(pclb_ctx* ctx, const void* f_n, const void* lam_np1, void* lam_n) {
@@ -761,7 +768,8 @@ pclb_status pclb_adjoint_step(pclb_ctx* ctx, const void* f_n, const void* lam_np
   if (e != cudaSuccess) return cuda_fail(ctx, e, "state unpack launch");
   pclb_status st = pclb_lambda_set(ctx, lam_np1);
   if (st != PCLB_OK) return st;
-  st = ctx->prec == PCLB_FP32 ? do_adjoint<float>(ctx, &ctx->tmap_adj[2]) : do_adjoint<double>(ctx, &ctx->tmap_adj[2]);
+  st = ctx->prec == PCLB_FP32 ? do_adjoint<float>(ctx, &ctx->tmap_adj[2], adj)
+                               : do_adjoint<double>(ctx, &ctx->tmap_adj[2], adj);
   if (st != PCLB_OK) return st;
   return pclb_lambda_get(ctx, lam_n);
 }

@@ -34,8 +34,8 @@ constexpr int kStepThreads = 256;   // 8 warps; each thread owns 2 nodes (rows w
 constexpr int kPitchAlign = 32;     // row pitch in elements (128 B for float)
 constexpr int kGhostRows = 2;       // azimuthal ghost rows stored on each side
 // Tile rows of the adjoint kernel (its window holds f and lam for all labels).
-constexpr int kAdjRows32 = 12;
-constexpr int kAdjRows64 = 4;
+constexpr int kAdjRows32 = 8;
+constexpr int kAdjRows64 = 8;
 
 // Per-velocity constants, in the arithmetic type T of the kernel, plus the
 // double-precision ones the moment / temperature recovery uses.
@@ -94,8 +94,18 @@ struct Layout {
   size_t partials;            // double [kDiagBlocks][8] reduction partials
   size_t diag_out;            // double [8]
   size_t stage;               // host-I/O staging: 8 fields [n_theta][n_r]
+  size_t adj_scratch;         // adjoint node cotangents, ghost states, wall cotangents
   size_t total;
 };
+
+// Scratch of one adjoint step (device pointers inside the workspace).
+struct AdjScratch {
+  unsigned char* gsum;        // [n_theta][n_r][4]  (1 - d) g of every node
+  unsigned char* ghost;       // [side][layer][n_theta] EqParams of the radial ghost layers
+  unsigned char* gwall;       // [side][node][n_theta][4] cotangent the ghosts return
+};
+size_t adjoint_scratch_bytes(int n_r, int n_theta, int elem);
+AdjScratch adjoint_scratch(unsigned char* base, int n_r, int n_theta, int elem);
 
 constexpr int kDiagBlocks = 304;    // 2 x 152 SMs
 

@@ -38,19 +38,6 @@ constexpr int step_smem_bytes() {
   return kQ * kPlane * (int)sizeof(T) + kPairs64 * kTileT * 4 * (int)sizeof(T) + 128;
 }
 
-// 1/n by the Newton-Raphson iteration r <- r (2 - n r) from the hardware's
-// approximate reciprocal; each step doubles the number of correct bits, two
-// reach full double precision (checked against the division in the parity
-// tests).  n must be a positive normal number.
-__device__ __forceinline__ double recip_newton(double n) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(n));
-  double e = fma(-n, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-n, r, 1.0);
-  return fma(r, e, r);
-}
-
 // Convection increment (upwind form, see convect in device_common.cuh) from
 // a = |C| and K = a (1 - a) given by the Courant table.
 template <int SCH>
