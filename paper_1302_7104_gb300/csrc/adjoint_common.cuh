@@ -47,6 +47,28 @@ __device__ __forceinline__ void mwb_partials(T a, T K, T D, T Dp, T& MD, T& MDp)
   MDp = -(T(1) + s) * (Ka * ar);
 }
 
+// The terms of one pair of opposite velocities (v, -v) of a shell in the sums
+// of eq_cotangent below, added to Ak, Bxk, Byk, Ck, Dk; lp, lm: the
+// cotangents of f^eq at v and -v.
+template <class T>
+__device__ __forceinline__ void pair_terms(T vx, T vy, T uxE, T uyE, T s, T a0, T a1, T lp, T lm, T& Ak, T& Bxk,
+                                           T& Byk, T& Ck, T& Dk) {
+  const T x = vx * uxE + vy * uyE;
+  const T x2 = x * x;
+  const T Pe = a0 + x2 * (T(0.5) * a1 + x2 * T(1.0 / 24.0));   // P(+-x) = Pe +- Po
+  const T Po = x * (a1 + x2 * T(1.0 / 6.0));
+  const T Xe = a1 + x2 * T(0.5);                                // P_x(+-x) = Xe +- Xo
+  const T Xo = x * (a1 + x2 * T(1.0 / 6.0));
+  const T Se = T(-0.5) + T(0.25) * s - T(0.25) * x2;           // P_s(+-x) = Se -+ x/2
+  const T ls = lp + lm, ld = lp - lm;
+  Ak += ls * Pe + ld * Po;
+  const T lpx = ld * Xe + ls * Xo;        // lp Px(x) - lm Px(-x)
+  Bxk += lpx * vx;
+  Byk += lpx * vy;
+  Ck += ls * Se - ld * T(0.5) * x;
+  Dk += x * (ls * Xo + ld * Xe);          // lp x Px(x) + lm (-x) Px(-x)
+}
+
 // G = sum_q lam(q) d f^eq_q / d(rho, u_x, u_y, E) at the given state (Eq. 10,
 // weights Eq. 11).  With P(x) the polynomial of Eq. (10), P_x, P_s its
 // derivatives in x = v.u/E and s = u^2/E:
@@ -85,22 +107,7 @@ __device__ __forceinline__ void eq_cotangent(T rho, T ux, T uy, T E, const DvmCo
 #pragma unroll
     for (int i = 0; i < half; ++i) {
       const int q = 1 + (k - 1) * kNDirs + i;
-      const T vx = d.vx[q], vy = d.vy[q];
-      const T x = vx * uxE + vy * uyE;
-      const T x2 = x * x;
-      const T Pe = a0 + x2 * (T(0.5) * a1 + x2 * T(1.0 / 24.0));   // P(+-x) = Pe +- Po
-      const T Po = x * (a1 + x2 * T(1.0 / 6.0));
-      const T Xe = a1 + x2 * T(0.5);                                // P_x(+-x) = Xe +- Xo
-      const T Xo = x * (a1 + x2 * T(1.0 / 6.0));
-      const T Se = T(-0.5) + T(0.25) * s - T(0.25) * x2;           // P_s(+-x) = Se -+ x/2
-      const T lp = lam(q), lm = lam(q + half);
-      const T ls = lp + lm, ld = lp - lm;
-      Ak += ls * Pe + ld * Po;
-      const T lpx = ld * Xe + ls * Xo;        // lp Px(x) - lm Px(-x)
-      Bxk += lpx * vx;
-      Byk += lpx * vy;
-      Ck += ls * Se - ld * T(0.5) * x;
-      Dk += x * (ls * Xo + ld * Xe);          // lp x Px(x) + lm (-x) Px(-x)
+      pair_terms<T>(d.vx[q], d.vy[q], uxE, uyE, s, a0, a1, lam(q), lam(q + half), Ak, Bxk, Byk, Ck, Dk);
     }
     A += F[k] * Ak;
     Bx += F[k] * Bxk;

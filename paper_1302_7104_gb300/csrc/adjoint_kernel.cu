@@ -18,15 +18,16 @@
 // D = Dp = 0 the derivative of h is 0.
 //
 // Two kernels:
-//   * adjoint_node_kernel, one thread per node: the moments of f^n, the
-//     cotangent g of the node's equilibrium (a reduction of lam^{n+1} over the
-//     33 labels), and for the nodes at a wall the ghost states and the
-//     cotangent g_wall the ghosts return; written to small global buffers;
-//   * adjoint_pair_kernel, tiles of 32 (r) x TT (theta) nodes: velocities in
-//     pairs of opposite labels, whose f and lam windows over [r0-4, r0+36) x
-//     [t0-2, t0+TT+2) stream through a ring of shared-memory stages filled by
-//     TMA while earlier pairs compute.  Each pair runs in two phases: (A)
-//     every node whose upwind stencil can reach the tile forms
+//   * adjoint_wall_kernel, one warp per wall and row: the ghost states
+//     (Eq. 39 or prescribed) and the cotangent g_wall they return, written to
+//     small global buffers;
+//   * adjoint_pair_kernel, tiles of 32 (r) x TT (theta) nodes, one node per
+//     thread.  Each thread first forms g of its node from f^n and lam^{n+1}
+//     read from global memory (a reduction over the 33 labels).  Then the
+//     velocities, in pairs of opposite labels, stream their f and lam windows
+//     over [r0-4, r0+36) x [t0-2, t0+TT+2) through a ring of shared-memory
+//     stages filled by TMA while earlier pairs compute.  Each pair runs in two
+//     phases: (A) every node whose upwind stencil can reach the tile forms
 //     lam(n) dM(n)/dD and lam(n) dM(n)/dDp once, in r and in theta; (B) every
 //     tile node gathers the products of the nodes that read it and adds
 //     d lam + psi . ((1-d) g + g_wall).  One barrier per pair separates the
@@ -47,10 +48,12 @@ struct AdjTile;
 template <>
 struct AdjTile<float> {
   static constexpr int TT = kAdjRows32;
+  static constexpr int min_blocks = 5;   // 5 CTAs of 256 threads per SM: at most 51 registers
 };
 template <>
 struct AdjTile<double> {
   static constexpr int TT = kAdjRows64;
+  static constexpr int min_blocks = 3;   // at most 85 registers
 };
 
 // Courant entry of one pair of opposite velocities at one theta row:
@@ -62,7 +65,7 @@ struct alignas(4 * sizeof(T)) CourEntry {
   int fl;
 };
 
-constexpr int kAdjStages = 3;   // ring depth of the pair-streaming kernel
+constexpr int kAdjStages = 2;   // ring depth of the pair-streaming kernel (2 measured best of 1..4)
 static_assert(sizeof(EqParams<float>) == 10 * sizeof(float) && sizeof(EqParams<double>) == 10 * sizeof(double),
               "ghost-state scratch holds 10 values per EqParams");
 
@@ -234,47 +237,22 @@ __device__ __forceinline__ T adj_feq(const EqParams<T>& e, const DvmConst<T>& d,
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Node-local part: gsum[n] = (1 - d) g(n), g the moment cotangent of the
-// node's equilibrium, Eq. (10), for lam^{n+1}.  gsum [n_theta][n_r][4].
+// Walls: one warp per side s (0 inner, 1 outer) and row t.  It forms the
+// equilibrium parameters of the two ghost layers (Eq. 39, or the prescribed
+// states) and the cotangent g_wall that the ghosts return to the wall node
+// (node 0) and the next node inward (node 1); lanes 0..15 take one pair of
+// opposite velocities each, a warp reduction sums them.
+// ghost [side][layer][n_theta] EqParams; gwall [side][node][n_theta][4].
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(128)
-    adjoint_node_kernel(const T* __restrict__ f, const T* __restrict__ lam, T* __restrict__ gsum,
-                        const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  const int t = blockIdx.y;
-  if (r >= p.n_r) return;
-  const int plane = p.rows * p.pitch;
-  const size_t off = (size_t)(t + kGhostRows) * p.pitch + r;
-  const T* ln = lam + off;
-  T rho, ux, uy, E;
-  bool ok;
-  adj_node_state(f + off, plane, d, rho, ux, uy, E, ok);
-  if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
-  T G[4], g[4];
-  eq_cotangent<T>(rho, ux, uy, E, d, [&](int q) -> T { return ln[(size_t)q * plane]; }, G);
-  to_moment_cotangent<T>(rho, ux, uy, E, G, g);
-  const T keep = T(1) - (T)p.decay;
-  T* o = gsum + ((size_t)t * p.n_r + r) * 4;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) o[j] = keep * g[j];
-}
-
-// ---------------------------------------------------------------------------
-// Walls: for side s (0 inner, 1 outer) and row t, the equilibrium parameters
-// of the two ghost layers (Eq. 39, or the prescribed states) and the
-// cotangent g_wall that the ghosts return to the wall node (node 0) and the
-// next node inward (node 1).  ghost [side][layer][n_theta] EqParams;
-// gwall [side][node][n_theta][4].
-// ---------------------------------------------------------------------------
-template <class T>
-__global__ void __launch_bounds__(64)
     adjoint_wall_kernel(const T* __restrict__ f, const T* __restrict__ lam, EqParams<T>* __restrict__ ghost,
                         T* __restrict__ gwall, const __grid_constant__ StepParams p,
                         const __grid_constant__ DvmConst<T> d) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int side = blockIdx.y;
-  if (t >= p.n_theta) return;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int side = warp & 1, t = warp >> 1;
+  if (t >= p.n_theta) return;                          // uniform across the warp
   const int plane = p.rows * p.pitch;
   const int srow = t + kGhostRows;
   const int step = side == 0 ? 1 : -1;                // towards the interior
@@ -305,29 +283,75 @@ __global__ void __launch_bounds__(64)
       }
     }
   }
-  if (!(grho[0] > 0.0 && grho[1] > 0.0 && gE[0] > 0.0 && gE[1] > 0.0)) atomicOr(p.status, PCLB_FLAG_NONPHYS);
-  EqParams<T> e[2];
-  for (int l = 0; l < 2; ++l) {
-    e[l] = eq_params<T>(grho[l], gux[l], guy[l], gE[l], d);
-    ghost[(size_t)(side * 2 + l) * p.n_theta + t] = e[l];
+  const EqParams<T> e0 = eq_params<T>(grho[0], gux[0], guy[0], gE[0], d);
+  const EqParams<T> e1 = eq_params<T>(grho[1], gux[1], guy[1], gE[1], d);
+  if (lane == 0) {
+    if (!(grho[0] > 0.0 && grho[1] > 0.0 && gE[0] > 0.0 && gE[1] > 0.0)) atomicOr(p.status, PCLB_FLAG_NONPHYS);
+    ghost[(size_t)(side * 2 + 0) * p.n_theta + t] = e0;
+    ghost[(size_t)(side * 2 + 1) * p.n_theta + t] = e1;
   }
-  T Gl[2][4];
-  for (int l = 0; l < 2; ++l) {
-    // cotangent of the ghost value f_q(layer l) = -sum_n lam_q(n) dM_q(n)/df_q(ghost l):
+  // per layer: the sums A, Bx, By, Cs, Dx, Fq of eq_cotangent over this lane's pair
+  T c[2][6];
+#pragma unroll
+  for (int l = 0; l < 2; ++l)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) c[l][j] = T(0);
+  constexpr int half = kNDirs / 2;
+  if (lane < 4 * half) {
+    const int k = 1 + lane / half;
+    const int q1 = 1 + (k - 1) * kNDirs + lane % half;
+    // cotangent of the ghost values f_q(layer l) = -sum_n lam_q(n) dM_q(n)/df_q(ghost l):
     // the wall node a reads (a, g0, g1), the next node b reads (b, a, g0)
-    auto ghost_lam = [&](int q) -> T {
-      const Cour<T> c = courant<T>(p, d, q, srow);
-      if (c.up_r != out) return T(0);
-      const T f_a = fa[(size_t)q * plane], f_b = fb[(size_t)q * plane];
-      const T g0 = adj_feq<T>(e[0], d, q), g1 = adj_feq<T>(e[1], d, q);
-      T MDa, MPa, MDb, MPb;
-      mwb_partials<T>(c.a_r, c.k_r, f_a - g0, g0 - g1, MDa, MPa);
-      mwb_partials<T>(c.a_r, c.k_r, f_b - f_a, f_a - g0, MDb, MPb);
-      const T lam_a = la[(size_t)q * plane], lam_b = lb[(size_t)q * plane];
-      if (l == 0) return lam_a * (MDa - MPa) + lam_b * MPb;
-      return lam_a * MPa;
-    };
-    eq_cotangent<T>((T)grho[l], gux[l], guy[l], (T)gE[l], d, ghost_lam, Gl[l]);
+    T lg[2][2];                                        // [label][layer]
+#pragma unroll
+    for (int L = 0; L < 2; ++L) {
+      const int q = q1 + L * half;
+      const Cour<T> cr = courant<T>(p, d, q, srow);
+      lg[L][0] = lg[L][1] = T(0);
+      if (cr.up_r == out) {
+        const T f_a = fa[(size_t)q * plane], f_b = fb[(size_t)q * plane];
+        const T g0 = adj_feq<T>(e0, d, q), g1 = adj_feq<T>(e1, d, q);
+        T MDa, MPa, MDb, MPb;
+        mwb_partials<T>(cr.a_r, cr.k_r, f_a - g0, g0 - g1, MDa, MPa);
+        mwb_partials<T>(cr.a_r, cr.k_r, f_b - f_a, f_a - g0, MDb, MPb);
+        const T lam_a = la[(size_t)q * plane], lam_b = lb[(size_t)q * plane];
+        lg[L][0] = lam_a * (MDa - MPa) + lam_b * MPb;
+        lg[L][1] = lam_a * MPa;
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      const T E = (T)gE[l], ux = gux[l], uy = guy[l];
+      const T* cf = d.Fc[k];
+      const T F = E * (cf[0] + E * (cf[1] + E * (cf[2] + E * cf[3])));
+      const T Fd = cf[0] + E * (T(2) * cf[1] + E * (T(3) * cf[2] + E * T(4) * cf[3]));
+      const T invE = T(1) / E;
+      const T s = (ux * ux + uy * uy) * invE;
+      const T a1 = T(1) - T(0.5) * s;
+      const T a0 = a1 + T(0.125) * s * s;
+      T Ak = 0, Bxk = 0, Byk = 0, Ck = 0, Dk = 0;
+      pair_terms<T>(d.vx[q1], d.vy[q1], ux * invE, uy * invE, s, a0, a1, lg[0][l], lg[1][l], Ak, Bxk, Byk, Ck, Dk);
+      c[l][0] = F * Ak; c[l][1] = F * Bxk; c[l][2] = F * Byk; c[l][3] = F * Ck; c[l][4] = F * Dk; c[l][5] = Fd * Ak;
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < 2; ++l)
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c[l][j] += __shfl_xor_sync(0xffffffffu, c[l][j], o);
+  if (lane != 0) return;
+  T Gl[2][4];
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    // G of eq_cotangent at the ghost state (the rest velocity returns nothing)
+    const T rho = (T)grho[l], E = (T)gE[l], ux = gux[l], uy = guy[l];
+    const T invE = T(1) / E;
+    const T s = (ux * ux + uy * uy) * invE;
+    Gl[l][0] = c[l][0];
+    Gl[l][1] = rho * (c[l][1] + T(2) * ux * c[l][3]) * invE;
+    Gl[l][2] = rho * (c[l][2] + T(2) * uy * c[l][3]) * invE;
+    Gl[l][3] = rho * (c[l][5] - (c[l][4] + s * c[l][3]) * invE);
   }
   // back through the extrapolation g0 = 2a - b, g1 = 3a - 2b (extrapolated components only)
   const bool ext_rho_E = kind != PCLB_BC_DIRICHLET;
@@ -351,11 +375,11 @@ __global__ void __launch_bounds__(64)
 // Pair-streaming part.
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(AdjSize<T>::threads)
+__global__ void __launch_bounds__(AdjSize<T>::threads, AdjTile<T>::min_blocks)
     adjoint_pair_kernel(const __grid_constant__ CUtensorMap tmap_f, const __grid_constant__ CUtensorMap tmap_l,
                         const T* __restrict__ f, const T* __restrict__ lam_in, T* __restrict__ lam_out,
-                        const EqParams<T>* __restrict__ ghost, const T* __restrict__ gwall,
-                        const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
+                        const EqParams<T>* __restrict__ ghost, const T* __restrict__ gwall, int a0, int na,
+                        int b0, const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
   constexpr int TT = AdjTile<T>::TT;
   constexpr int PLANE = AdjSize<T>::plane;
   constexpr int NP = AdjSize<T>::npairs, RC = AdjSize<T>::rcols, PROD = AdjSize<T>::prod;
@@ -370,7 +394,9 @@ __global__ void __launch_bounds__(AdjSize<T>::threads)
   CourEntry<T>* ctab = reinterpret_cast<CourEntry<T>*>(invr + kTileR);   // [TT + 4][NP]
   uint64_t* bar = reinterpret_cast<uint64_t*>(ctab + (TT + 4) * NP);     // [S]
 
-  const int r0 = blockIdx.x * kTileR;
+  // radial tile: blocks 0 .. na - 1 take tiles a0 .., the rest tiles b0 ..
+  const int tx = (int)blockIdx.x < na ? a0 + (int)blockIdx.x : b0 + (int)blockIdx.x - na;
+  const int r0 = tx * kTileR;
   const int t0 = blockIdx.y * TT;
   const int tid = threadIdx.x;
   const int lane = tid & 31, rowl = tid >> 5;
@@ -602,10 +628,13 @@ __global__ void __launch_bounds__(AdjSize<T>::threads)
   }
 }
 
+// The tiles that read the wall kernel's output (ghost columns, g_wall) are
+// tile 0 and the tiles with r0 >= n_r - 33; they run on the side stream after
+// the wall kernel while the interior tiles run on the main stream.
 template <class T>
 cudaError_t launch_adjoint(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, const T* f, const T* lam_in,
                            T* lam_out, const AdjScratch& ws, const StepParams& p, const DvmConst<T>& d,
-                           cudaStream_t stream) {
+                           cudaStream_t stream, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
   static bool configured = false;
   constexpr int smem = AdjSize<T>::smem;
   if (!configured) {
@@ -616,34 +645,47 @@ cudaError_t launch_adjoint(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l,
   }
   EqParams<T>* ghost = reinterpret_cast<EqParams<T>*>(ws.ghost);
   T* gwall = reinterpret_cast<T*>(ws.gwall);
-  adjoint_wall_kernel<T><<<dim3((p.n_theta + 63) / 64, 2), 64, 0, stream>>>(f, lam_in, ghost, gwall, p, d);
   constexpr int TT = AdjTile<T>::TT;
-  dim3 g((p.n_r + kTileR - 1) / kTileR, (p.n_theta + TT - 1) / TT);
-  adjoint_pair_kernel<T><<<g, AdjSize<T>::threads, smem, stream>>>(*tmap_f, *tmap_l, f, lam_in, lam_out, ghost,
-                                                                   gwall, p, d);
-  return cudaGetLastError();
+  const int nt = (p.n_r + kTileR - 1) / kTileR;
+  const int t_hi = p.n_r - 33 > 0 ? (p.n_r - 33 + kTileR - 1) / kTileR : 0;   // first tile with r0 >= n_r - 33
+  const int b0 = t_hi > 1 ? t_hi : 1;
+  const int n_interior = t_hi > 1 ? t_hi - 1 : 0;                              // tiles 1 .. t_hi - 1
+  const unsigned gy = (unsigned)((p.n_theta + TT - 1) / TT);
+  cudaError_t e = cudaEventRecord(ev_fork, stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_fork, 0);
+  if (e != cudaSuccess) return e;
+  adjoint_wall_kernel<T><<<(2 * p.n_theta + 3) / 4, 128, 0, side>>>(f, lam_in, ghost, gwall, p, d);
+  adjoint_pair_kernel<T><<<dim3(1 + (nt - b0), gy), AdjSize<T>::threads, smem, side>>>(
+      *tmap_f, *tmap_l, f, lam_in, lam_out, ghost, gwall, 0, 1, b0, p, d);
+  if (n_interior > 0)
+    adjoint_pair_kernel<T><<<dim3(n_interior, gy), AdjSize<T>::threads, smem, stream>>>(
+        *tmap_f, *tmap_l, f, lam_in, lam_out, ghost, gwall, 1, n_interior, 0, p, d);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(ev_join, side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev_join, 0);
+  return e;
 }
 
-size_t adjoint_scratch_bytes(int n_r, int n_theta, int elem) {
-  // gsum: 4 per node; ghost: 2 x 2 EqParams (10 values) per row; gwall: 2 x 2 x 4 per row
-  const size_t a = (size_t)n_r * n_theta * 4 * elem, b = (size_t)4 * n_theta * 10 * elem, c = (size_t)16 * n_theta * elem;
+size_t adjoint_scratch_bytes(int n_theta, int elem) {
+  // ghost: 2 x 2 EqParams (10 values) per row; gwall: 2 x 2 x 4 per row
+  const size_t b = (size_t)4 * n_theta * 10 * elem, c = (size_t)16 * n_theta * elem;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  return up(a) + up(b) + up(c);
+  return up(b) + up(c);
 }
 
-AdjScratch adjoint_scratch(unsigned char* base, int n_r, int n_theta, int elem) {
-  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+AdjScratch adjoint_scratch(unsigned char* base, int n_theta, int elem) {
   AdjScratch s;
-  s.gsum = base;
-  s.ghost = base + up((size_t)n_r * n_theta * 4 * elem);
-  s.gwall = s.ghost + up((size_t)4 * n_theta * 10 * elem);
+  s.ghost = base;
+  s.gwall = base + (((size_t)4 * n_theta * 10 * elem + 255) & ~(size_t)255);
   return s;
 }
 
 template cudaError_t launch_adjoint<float>(const CUtensorMap*, const CUtensorMap*, const float*, const float*, float*,
-                                           const AdjScratch&, const StepParams&, const DvmConst<float>&, cudaStream_t);
+                                           const AdjScratch&, const StepParams&, const DvmConst<float>&, cudaStream_t,
+                                           cudaStream_t, cudaEvent_t, cudaEvent_t);
 template cudaError_t launch_adjoint<double>(const CUtensorMap*, const CUtensorMap*, const double*, const double*,
                                             double*, const AdjScratch&, const StepParams&, const DvmConst<double>&,
-                                            cudaStream_t);
+                                            cudaStream_t, cudaStream_t, cudaEvent_t, cudaEvent_t);
 
 }  // namespace pclb

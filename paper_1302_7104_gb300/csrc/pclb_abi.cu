@@ -37,7 +37,8 @@ template <class T>
 cudaError_t launch_noneq(const T*, T*, int, const StepParams&, const DvmConst<T>&, cudaStream_t);
 template <class T>
 cudaError_t launch_adjoint(const CUtensorMap*, const CUtensorMap*, const T*, const T*, T*, const AdjScratch&,
-                           const StepParams&, const DvmConst<T>&, cudaStream_t);
+                           const StepParams&, const DvmConst<T>&, cudaStream_t, cudaStream_t, cudaEvent_t,
+                           cudaEvent_t);
 template <class T>
 cudaError_t launch_moments_vjp(const T*, const T*, const T*, const T*, const T*, T*, const StepParams&,
                                const DvmConst<T>&, cudaStream_t);
@@ -132,7 +133,7 @@ Layout make_layout(const pclb_grid* g, pclb_precision prec) {
   L.partials = off; off = align_up(off + (size_t)kDiagBlocks * 8 * 8, 256);
   L.diag_out = off; off = align_up(off + 8 * 8, 256);
   L.stage = off; off = align_up(off + (size_t)8 * g->n_r * g->n_theta * es, 256);
-  L.adj_scratch = off; off = align_up(off + adjoint_scratch_bytes(g->n_r, g->n_theta, (int)es), 256);
+  L.adj_scratch = off; off = align_up(off + adjoint_scratch_bytes(g->n_theta, (int)es), 256);
   L.total = off;
   return L;
 }
@@ -315,13 +316,23 @@ pclb_status do_step(pclb_ctx* ctx, int n) {
 
 template <class T>
 pclb_status do_adjoint(pclb_ctx* ctx, const CUtensorMap* tmap_f, const void* f) {
+  if (!ctx->side) {
+    // created on first use: the side stream (highest priority, so that the
+    // wall tiles are scheduled as soon as their inputs are ready) and the
+    // fork / join events
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint side stream");
+  }
   const int src = ctx->cur_lam, dst = 1 - ctx->cur_lam;
-  const AdjScratch ws = adjoint_scratch(ctx->ws + ctx->lay.adj_scratch, ctx->grid.n_r, ctx->grid.n_theta,
-                                        (int)sizeof(T));
+  const AdjScratch ws = adjoint_scratch(ctx->ws + ctx->lay.adj_scratch, ctx->grid.n_theta, (int)sizeof(T));
   cudaError_t e = launch_adjoint<T>(tmap_f, &ctx->tmap_adj[3 + src], reinterpret_cast<const T*>(f),
                                     reinterpret_cast<const T*>(ctx->ws + ctx->lay.lam[src]),
                                     reinterpret_cast<T*>(ctx->ws + ctx->lay.lam[dst]), ws, ctx->sp, dvm_of<T>(ctx),
-                                    ctx->stream);
+                                    ctx->stream, ctx->side, ctx->ev_fork, ctx->ev_join);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint kernel launch");
   ctx->cur_lam = dst;
   return PCLB_OK;
@@ -513,6 +524,9 @@ pclb_status pclb_destroy(pclb_ctx* ctx) {
   if (!ctx) return PCLB_OK;
   pclb_status st = bounded_sync(ctx, kDefaultTimeoutMs);
   if (st != PCLB_OK) std::snprintf(g_err, sizeof(g_err), "%s", ctx->err);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   delete static_cast<HostCtx*>(ctx);
   return st;
 }

@@ -94,18 +94,17 @@ struct Layout {
   size_t partials;            // double [kDiagBlocks][8] reduction partials
   size_t diag_out;            // double [8]
   size_t stage;               // host-I/O staging: 8 fields [n_theta][n_r]
-  size_t adj_scratch;         // adjoint node cotangents, ghost states, wall cotangents
+  size_t adj_scratch;         // adjoint ghost states and wall cotangents
   size_t total;
 };
 
 // Scratch of one adjoint step (device pointers inside the workspace).
 struct AdjScratch {
-  unsigned char* gsum;        // [n_theta][n_r][4]  (1 - d) g of every node
   unsigned char* ghost;       // [side][layer][n_theta] EqParams of the radial ghost layers
   unsigned char* gwall;       // [side][node][n_theta][4] cotangent the ghosts return
 };
-size_t adjoint_scratch_bytes(int n_r, int n_theta, int elem);
-AdjScratch adjoint_scratch(unsigned char* base, int n_r, int n_theta, int elem);
+size_t adjoint_scratch_bytes(int n_theta, int elem);
+AdjScratch adjoint_scratch(unsigned char* base, int n_theta, int elem);
 
 constexpr int kDiagBlocks = 304;    // 2 x 152 SMs
 
@@ -130,6 +129,8 @@ struct pclb_ctx {
   int32_t scheme = 0;       // pclb_scheme
   int32_t relaxation = 0;   // pclb_relaxation
   cudaStream_t stream;
+  cudaStream_t side = nullptr;        // high-priority stream for the adjoint's wall work
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   unsigned char* ws;
   pclb::Layout lay;
   int cur;                    // which of the two f buffers holds the state
