@@ -71,7 +71,7 @@ typedef enum {
   PCLB_ETIMEOUT = 5,     /* a bounded wait for the stream (or a device-side wait) ran out */
   PCLB_ECFL = 6,         /* max over velocities and nodes of |C_r| + |C_theta| exceeds 1 */
   PCLB_ESTATE = 7,       /* call out of order, e.g. pclb_step before any state was set */
-  PCLB_EUNSUPPORTED = 8  /* configuration this build does not implement (e.g. n_dirs != 8) */
+  PCLB_EUNSUPPORTED = 8  /* configuration this build does not implement (e.g. n_dirs not 8, 16, 24) */
 } pclb_status;
 
 typedef enum { PCLB_FP32 = 0, PCLB_FP64 = 1 } pclb_precision;
@@ -118,9 +118,15 @@ typedef struct {
 } pclb_grid;
 
 /* Discrete velocity model (Sec. II A): N_k = 4 shells of n_dirs directions
- * plus the rest velocity. */
+ * plus the rest velocity, Q = 1 + 4 n_dirs labels.  n_dirs = 8 (the octagon)
+ * runs the tuned kernels and every entry point.  n_dirs = 16 and 24 (Table I,
+ * rows 2-3; B from that table) run generic kernels for the forward path only:
+ * pclb_set_state, pclb_set_f, pclb_get_f, pclb_step (every scheme and
+ * relaxation), pclb_moments, pclb_diagnostics, pclb_run_host and the state
+ * save / load calls; the reverse-mode entry points, pclb_noneq and
+ * pclb_diagnostics_noalloc return PCLB_EUNSUPPORTED for them. */
 typedef struct {
-  int32_t n_dirs;    /* N_i; this build implements 8 */
+  int32_t n_dirs;    /* N_i: 8, 16 or 24 */
   double speeds[5];  /* v_0 .. v_4; the paper uses 0, 1, 2.92, 2.99, 4.49 */
   double B[5];       /* B[n] = B_n of Table I (octagon: 8, -1/4, 1, -6, 48) */
 } pclb_dvm;

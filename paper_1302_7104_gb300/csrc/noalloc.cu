@@ -169,6 +169,10 @@ extern "C" pclb_status pclb_diagnostics_noalloc(const pclb_grid* grid, const pcl
   char err[256];
   pclb_status st = validate_problem(grid, dvm, prec);
   if (st != PCLB_OK) return st;
+  if (dvm->n_dirs != kNDirs) {
+    set_thread_error("pclb_diagnostics_noalloc implements n_dirs = 8 only");
+    return PCLB_EUNSUPPORTED;
+  }
   if (!f || !out) {
     set_thread_error("f and out must not be NULL");
     return PCLB_EINVAL;

@@ -40,6 +40,20 @@ cudaError_t launch_adjoint(const CUtensorMap*, const CUtensorMap*, const T*, con
                            const StepParams&, const DvmConst<T>&, cudaStream_t, cudaStream_t, cudaEvent_t,
                            cudaEvent_t);
 template <class T>
+cudaError_t gen_launch_set_state(T*, const T*, const T*, const T*, const T*, const StepParams&, const DvmG&,
+                                 cudaStream_t);
+template <class T>
+cudaError_t gen_launch_moments(const T*, T*, T*, T*, T*, const StepParams&, const DvmG&, cudaStream_t);
+template <class T>
+cudaError_t gen_launch_pack(const T*, T*, const StepParams&, const DvmG&, cudaStream_t);
+template <class T>
+cudaError_t gen_launch_unpack(const T*, T*, const StepParams&, const DvmG&, cudaStream_t);
+template <class T>
+cudaError_t gen_launch_step(const T*, T*, T*, const StepParams&, const DvmG&, cudaStream_t);
+template <class T>
+cudaError_t gen_launch_diagnostics(const T*, double*, double*, const StepParams&, const DvmG&, double, double,
+                                   double, cudaStream_t);
+template <class T>
 cudaError_t launch_moments_vjp(const T*, const T*, const T*, const T*, const T*, T*, const StepParams&,
                                const DvmConst<T>&, cudaStream_t);
 template <class T>
@@ -87,8 +101,8 @@ pclb_status validate_problem(const pclb_grid* g, const pclb_dvm* d, pclb_precisi
     return fail(nullptr, PCLB_EINVAL, "grid %d x %d beyond the supported 2^20 per direction", g->n_r, g->n_theta);
   if (!(g->r_in > 0.0) || !(g->r_out > g->r_in) || !std::isfinite(g->r_out))
     return fail(nullptr, PCLB_EINVAL, "need 0 < r_in < r_out (got %g, %g)", g->r_in, g->r_out);
-  if (d->n_dirs != kNDirs)
-    return fail(nullptr, PCLB_EUNSUPPORTED, "n_dirs = %d; this build implements %d directions", d->n_dirs, kNDirs);
+  if (d->n_dirs != kNDirs && d->n_dirs != 16 && d->n_dirs != 24)
+    return fail(nullptr, PCLB_EUNSUPPORTED, "n_dirs = %d; this build implements 8, 16 and 24 directions", d->n_dirs);
   if (g->n_f < 1 || g->n_f > d->n_dirs)
     return fail(nullptr, PCLB_EINVAL, "n_f = %d must be in [1, n_dirs]", g->n_f);
   if (d->speeds[0] != 0.0) return fail(nullptr, PCLB_EINVAL, "speeds[0] must be 0 (rest velocity)");
@@ -110,12 +124,13 @@ pclb_status validate(const pclb_grid* g, const pclb_dvm* d, pclb_precision prec)
   return validate_problem(g, d, prec);
 }
 
-Layout make_layout(const pclb_grid* g, pclb_precision prec) {
+Layout make_layout(const pclb_grid* g, const pclb_dvm* d, pclb_precision prec) {
   Layout L{};
   const size_t es = elem_size(prec);
+  const size_t Q = 1 + 4 * (size_t)d->n_dirs, npairs = 2 * (size_t)d->n_dirs;
   const size_t pitch = align_up((size_t)g->n_r, kPitchAlign);
   const size_t rows = (size_t)g->n_theta + 2 * kGhostRows;
-  L.f_bytes = align_up((size_t)kQ * rows * pitch * es, 256);
+  L.f_bytes = align_up(Q * rows * pitch * es, 256);
   size_t off = 0;
   L.f[0] = off; off += L.f_bytes;
   L.f[1] = off; off += L.f_bytes;
@@ -126,14 +141,16 @@ Layout make_layout(const pclb_grid* g, pclb_precision prec) {
   L.sin_t = off; off = align_up(off + (size_t)g->n_theta * 8, 256);
   L.inv_r = off; off = align_up(off + (size_t)g->n_r * 8, 256);
   L.bc_vals = off; off = align_up(off + (size_t)2 * 2 * 4 * g->n_theta * 8, 256);
-  L.courant = off; off = align_up(off + (size_t)(g->n_theta + 2 * kGhostRows) * (4 * kNDirs / 2) * 16, 256);
-  L.courant64 = off; off = align_up(off + (size_t)(g->n_theta + 2 * kGhostRows) * (4 * kNDirs / 2) * 32, 256);
+  L.courant = off; off = align_up(off + (size_t)(g->n_theta + 2 * kGhostRows) * npairs * 16, 256);
+  L.courant64 = off; off = align_up(off + (size_t)(g->n_theta + 2 * kGhostRows) * npairs * 32, 256);
   L.inv_r_f = off; off = align_up(off + (size_t)g->n_r * 4, 256);
   L.status = off; off = align_up(off + 256, 256);
   L.partials = off; off = align_up(off + (size_t)kDiagBlocks * 8 * 8, 256);
   L.diag_out = off; off = align_up(off + 8 * 8, 256);
   L.stage = off; off = align_up(off + (size_t)8 * g->n_r * g->n_theta * es, 256);
   L.adj_scratch = off; off = align_up(off + adjoint_scratch_bytes(g->n_theta, (int)es), 256);
+  L.gen_ghost = off;
+  if (d->n_dirs != kNDirs) off = align_up(off + 4 * (size_t)g->n_theta * Q * es, 256);
   L.total = off;
   return L;
 }
@@ -210,6 +227,37 @@ void fill_dvm(DvmConst<T>& c, const pclb_dvm& d, const pclb_grid& g) {
     }
 }
 template void fill_dvm<float>(DvmConst<float>&, const pclb_dvm&, const pclb_grid&);
+
+// The same constants in double for N_i = 16, 24 (the generic kernels).
+void fill_dvm_generic(DvmG& c, const pclb_dvm& d, const pclb_grid& g) {
+  DvmConst<double> base;   // shell-level constants (speeds, weights) as for N_i = 8
+  pclb_dvm d8 = d;
+  d8.n_dirs = kNDirs;
+  pclb_grid g8 = g;
+  g8.n_f = kNDirs;
+  fill_dvm(base, d8, g8);
+  std::memset(&c, 0, sizeof(c));
+  for (int k = 0; k < 5; ++k) c.half_v2[k] = base.half_v2[k];
+  for (int k = 0; k < 5; ++k)
+    for (int n = 0; n < 4; ++n) c.Fc[k][n] = base.Fc[k][n];
+  c.B0 = base.B0;
+  const int nd = d.n_dirs;
+  c.n_dirs = nd;
+  c.q = 1 + 4 * nd;
+  for (int k = 1; k <= 4; ++k)
+    for (int i = 0; i < nd; ++i) {
+      const int q = 1 + (k - 1) * nd + i;
+      // exactly antisymmetric opposite directions (i and i + n_dirs/2)
+      const int ib = i % (nd / 2);
+      const double phi = 2.0 * M_PI * ib / nd;
+      const double sgn = i < nd / 2 ? 1.0 : -1.0;
+      c.vx[q] = d.speeds[k] * sgn * std::cos(phi);
+      c.vy[q] = d.speeds[k] * sgn * std::sin(phi);
+      c.shell[q] = k;
+      c.recv_lo[q] = 1 + (k - 1) * nd + ((i - g.n_f) % nd + nd) % nd;
+      c.recv_hi[q] = 1 + (k - 1) * nd + (i + g.n_f) % nd;
+    }
+}
 template void fill_dvm<double>(DvmConst<double>&, const pclb_dvm&, const pclb_grid&);
 void set_thread_error(const char* msg) { std::snprintf(g_err, sizeof(g_err), "%s", msg); }
 }  // namespace pclb
@@ -299,12 +347,18 @@ pclb_status check_launch(pclb_ctx* ctx, cudaError_t e, const char* what) {
   return e == cudaSuccess ? PCLB_OK : cuda_fail(ctx, e, what);
 }
 
+// N_i = 16 or 24: the generic kernels
+bool generic(const pclb_ctx* c) { return c->dvm.n_dirs != kNDirs; }
+
 template <class T>
 pclb_status do_step(pclb_ctx* ctx, int n) {
   for (int i = 0; i < n; ++i) {
     const int src = ctx->cur, dst = 1 - ctx->cur;
     cudaError_t e;
-    if constexpr (sizeof(T) == 4)
+    if (generic(ctx))
+      e = gen_launch_step<T>(fbuf<T>(ctx, src), fbuf<T>(ctx, dst), reinterpret_cast<T*>(ctx->ws + ctx->lay.gen_ghost),
+                             ctx->sp, ctx->dvmg, ctx->stream);
+    else if constexpr (sizeof(T) == 4)
       e = launch_step_f32(&ctx->tmap[src], fbuf<float>(ctx, dst), ctx->sp, ctx->dvm32, ctx->stream);
     else
       e = launch_step<T>(&ctx->tmap[src], fbuf<T>(ctx, dst), ctx->sp, dvm_of<T>(ctx), ctx->stream);
@@ -351,7 +405,7 @@ pclb_status pclb_workspace_size(const pclb_grid* grid, const pclb_dvm* dvm, pclb
   if (!bytes) return fail(nullptr, PCLB_EINVAL, "bytes must not be NULL");
   pclb_status st = validate(grid, dvm, prec);
   if (st != PCLB_OK) return st;
-  *bytes = make_layout(grid, prec).total;
+  *bytes = make_layout(grid, dvm, prec).total;
   return PCLB_OK;
 }
 
@@ -375,7 +429,7 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
   if (!workspace) return fail(nullptr, PCLB_EINVAL, "workspace must not be NULL");
   if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
     return fail(nullptr, PCLB_EINVAL, "workspace must be 256-byte aligned");
-  const Layout lay = make_layout(grid, prec);
+  const Layout lay = make_layout(grid, dvm, prec);
   if (workspace_bytes < lay.total)
     return fail(nullptr, PCLB_ENOMEM, "workspace has %zu bytes, %zu needed", workspace_bytes, lay.total);
 
@@ -482,8 +536,12 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
   sp.courant64 = reinterpret_cast<const double*>(ctx->ws + lay.courant64);
   sp.inv_r_f = reinterpret_cast<const float*>(ctx->ws + lay.inv_r_f);
   sp.status = reinterpret_cast<uint32_t*>(ctx->ws + lay.status);
-  fill_dvm(ctx->dvm32, *dvm, *grid);
-  fill_dvm(ctx->dvm64, *dvm, *grid);
+  if (dvm->n_dirs == kNDirs) {
+    fill_dvm(ctx->dvm32, *dvm, *grid);
+    fill_dvm(ctx->dvm64, *dvm, *grid);
+  } else {
+    fill_dvm_generic(ctx->dvmg, *dvm, *grid);
+  }
 
   struct Up { size_t off; const void* src; size_t n; } ups[] = {
       {lay.cos_t, ctx->cos_t.data(), NT * 8ul}, {lay.sin_t, ctx->sin_t.data(), NT * 8ul},
@@ -542,7 +600,13 @@ pclb_status pclb_set_state(pclb_ctx* ctx, const void* rho, const void* u_r, cons
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
   if (!rho || !u_r || !u_theta || !T) return fail(ctx, PCLB_EINVAL, "field pointers must not be NULL");
   cudaError_t e;
-  if (ctx->prec == PCLB_FP32)
+  if (generic(ctx) && ctx->prec == PCLB_FP32)
+    e = gen_launch_set_state<float>(fbuf<float>(ctx, ctx->cur), (const float*)rho, (const float*)u_r,
+                                    (const float*)u_theta, (const float*)T, ctx->sp, ctx->dvmg, ctx->stream);
+  else if (generic(ctx))
+    e = gen_launch_set_state<double>(fbuf<double>(ctx, ctx->cur), (const double*)rho, (const double*)u_r,
+                                     (const double*)u_theta, (const double*)T, ctx->sp, ctx->dvmg, ctx->stream);
+  else if (ctx->prec == PCLB_FP32)
     e = launch_set_state<float>(fbuf<float>(ctx, ctx->cur), (const float*)rho, (const float*)u_r,
                                 (const float*)u_theta, (const float*)T, ctx->sp, ctx->dvm32, ctx->stream);
   else
@@ -556,9 +620,15 @@ pclb_status pclb_set_state(pclb_ctx* ctx, const void* rho, const void* u_r, cons
 pclb_status pclb_set_f(pclb_ctx* ctx, const void* f) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
   if (!f) return fail(ctx, PCLB_EINVAL, "f must not be NULL");
-  cudaError_t e = ctx->prec == PCLB_FP32
-                      ? launch_unpack<float>((const float*)f, fbuf<float>(ctx, ctx->cur), ctx->sp, ctx->dvm32, ctx->stream)
-                      : launch_unpack<double>((const double*)f, fbuf<double>(ctx, ctx->cur), ctx->sp, ctx->dvm64, ctx->stream);
+  cudaError_t e;
+  if (generic(ctx))
+    e = ctx->prec == PCLB_FP32
+            ? gen_launch_unpack<float>((const float*)f, fbuf<float>(ctx, ctx->cur), ctx->sp, ctx->dvmg, ctx->stream)
+            : gen_launch_unpack<double>((const double*)f, fbuf<double>(ctx, ctx->cur), ctx->sp, ctx->dvmg, ctx->stream);
+  else
+    e = ctx->prec == PCLB_FP32
+            ? launch_unpack<float>((const float*)f, fbuf<float>(ctx, ctx->cur), ctx->sp, ctx->dvm32, ctx->stream)
+            : launch_unpack<double>((const double*)f, fbuf<double>(ctx, ctx->cur), ctx->sp, ctx->dvm64, ctx->stream);
   pclb_status st = check_launch(ctx, e, "set_f kernel launch");
   if (st == PCLB_OK) ctx->has_state = true;
   return st;
@@ -568,9 +638,15 @@ pclb_status pclb_get_f(pclb_ctx* ctx, void* f) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
   if (!f) return fail(ctx, PCLB_EINVAL, "f must not be NULL");
   if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
-  cudaError_t e = ctx->prec == PCLB_FP32
-                      ? launch_pack<float>(fbuf<float>(ctx, ctx->cur), (float*)f, ctx->sp, ctx->stream)
-                      : launch_pack<double>(fbuf<double>(ctx, ctx->cur), (double*)f, ctx->sp, ctx->stream);
+  cudaError_t e;
+  if (generic(ctx))
+    e = ctx->prec == PCLB_FP32
+            ? gen_launch_pack<float>(fbuf<float>(ctx, ctx->cur), (float*)f, ctx->sp, ctx->dvmg, ctx->stream)
+            : gen_launch_pack<double>(fbuf<double>(ctx, ctx->cur), (double*)f, ctx->sp, ctx->dvmg, ctx->stream);
+  else
+    e = ctx->prec == PCLB_FP32
+            ? launch_pack<float>(fbuf<float>(ctx, ctx->cur), (float*)f, ctx->sp, ctx->stream)
+            : launch_pack<double>(fbuf<double>(ctx, ctx->cur), (double*)f, ctx->sp, ctx->stream);
   return check_launch(ctx, e, "get_f kernel launch");
 }
 
@@ -586,7 +662,13 @@ pclb_status pclb_moments(pclb_ctx* ctx, void* rho, void* u_r, void* u_theta, voi
   if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
   if (!rho && !u_r && !u_theta && !T) return PCLB_OK;
   cudaError_t e;
-  if (ctx->prec == PCLB_FP32)
+  if (generic(ctx) && ctx->prec == PCLB_FP32)
+    e = gen_launch_moments<float>(fbuf<float>(ctx, ctx->cur), (float*)rho, (float*)u_r, (float*)u_theta,
+                                  (float*)T, ctx->sp, ctx->dvmg, ctx->stream);
+  else if (generic(ctx))
+    e = gen_launch_moments<double>(fbuf<double>(ctx, ctx->cur), (double*)rho, (double*)u_r, (double*)u_theta,
+                                   (double*)T, ctx->sp, ctx->dvmg, ctx->stream);
+  else if (ctx->prec == PCLB_FP32)
     e = launch_moments<float>(fbuf<float>(ctx, ctx->cur), (float*)rho, (float*)u_r, (float*)u_theta,
                               (float*)T, ctx->sp, ctx->dvm32, ctx->stream);
   else
@@ -597,6 +679,7 @@ pclb_status pclb_moments(pclb_ctx* ctx, void* rho, void* u_r, void* u_theta, voi
 
 pclb_status pclb_noneq(pclb_ctx* ctx, int32_t groups, void* out) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (generic(ctx)) return fail(ctx, PCLB_EUNSUPPORTED, "pclb_noneq implements n_dirs = 8 only");
   if (groups < 1 || groups > 15) return fail(ctx, PCLB_EINVAL, "groups = %d must be in 1..15", (int)groups);
   if (!out) return fail(ctx, PCLB_EINVAL, "out must not be NULL");
   if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
@@ -617,11 +700,18 @@ pclb_status pclb_diagnostics(pclb_ctx* ctx, double* out) {
   const double dth = 2.0 * M_PI * ctx->grid.n_f / ((double)ctx->dvm.n_dirs * ctx->grid.n_theta);
   double* partials = reinterpret_cast<double*>(ctx->ws + ctx->lay.partials);
   double* dout = reinterpret_cast<double*>(ctx->ws + ctx->lay.diag_out);
-  cudaError_t e = ctx->prec == PCLB_FP32
-                      ? launch_diagnostics<float>(fbuf<float>(ctx, ctx->cur), partials, dout, ctx->sp,
-                                                  ctx->dvm32, dr, dth, ctx->grid.r_in, ctx->stream)
-                      : launch_diagnostics<double>(fbuf<double>(ctx, ctx->cur), partials, dout, ctx->sp,
-                                                   ctx->dvm64, dr, dth, ctx->grid.r_in, ctx->stream);
+  cudaError_t e;
+  if (generic(ctx))
+    e = ctx->prec == PCLB_FP32 ? gen_launch_diagnostics<float>(fbuf<float>(ctx, ctx->cur), partials, dout, ctx->sp,
+                                                               ctx->dvmg, dr, dth, ctx->grid.r_in, ctx->stream)
+                               : gen_launch_diagnostics<double>(fbuf<double>(ctx, ctx->cur), partials, dout,
+                                                                ctx->sp, ctx->dvmg, dr, dth, ctx->grid.r_in,
+                                                                ctx->stream);
+  else
+    e = ctx->prec == PCLB_FP32 ? launch_diagnostics<float>(fbuf<float>(ctx, ctx->cur), partials, dout, ctx->sp,
+                                                           ctx->dvm32, dr, dth, ctx->grid.r_in, ctx->stream)
+                               : launch_diagnostics<double>(fbuf<double>(ctx, ctx->cur), partials, dout, ctx->sp,
+                                                            ctx->dvm64, dr, dth, ctx->grid.r_in, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "diagnostics kernel launch");
   pclb_status st = bounded_sync(ctx, kDefaultTimeoutMs);
   if (st != PCLB_OK) return st;
@@ -707,6 +797,7 @@ pclb_status pclb_load_state(pclb_ctx* ctx, const void* state) {
 
 pclb_status pclb_lambda_set(pclb_ctx* ctx, const void* lam) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (generic(ctx)) return fail(ctx, PCLB_EUNSUPPORTED, "reverse mode implements n_dirs = 8 only");
   if (!lam) return fail(ctx, PCLB_EINVAL, "lam must not be NULL");
   void* dst = ctx->ws + ctx->lay.lam[ctx->cur_lam];
   cudaError_t e = ctx->prec == PCLB_FP32
@@ -719,6 +810,7 @@ pclb_status pclb_lambda_set(pclb_ctx* ctx, const void* lam) {
 
 pclb_status pclb_lambda_get(pclb_ctx* ctx, void* lam) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (generic(ctx)) return fail(ctx, PCLB_EUNSUPPORTED, "reverse mode implements n_dirs = 8 only");
   if (!lam) return fail(ctx, PCLB_EINVAL, "lam must not be NULL");
   if (!ctx->has_lam) return fail(ctx, PCLB_ESTATE, "no adjoint variable: call pclb_lambda_set or pclb_moments_vjp");
   const void* src = ctx->ws + ctx->lay.lam[ctx->cur_lam];
@@ -730,6 +822,7 @@ pclb_status pclb_lambda_get(pclb_ctx* ctx, void* lam) {
 // The adjoint differentiates the ghost nodes as f = f^eq of their state and
 // the MWB increments.
 static pclb_status adjoint_supported(pclb_ctx* ctx) {
+  if (generic(ctx)) return fail(ctx, PCLB_EUNSUPPORTED, "reverse mode implements n_dirs = 8 only");
   if ((ctx->bc_kind[0] | ctx->bc_kind[1]) & PCLB_BC_NEQ)
     return fail(ctx, PCLB_EUNSUPPORTED, "the adjoint does not support PCLB_BC_NEQ boundaries");
   if (ctx->scheme != PCLB_SCHEME_MWB)
@@ -790,6 +883,7 @@ pclb_status pclb_adjoint_step(pclb_ctx* ctx, const void* f_n, const void* lam_np
 
 pclb_status pclb_moments_vjp(pclb_ctx* ctx, const void* g_rho, const void* g_ur, const void* g_ut, const void* g_T) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (generic(ctx)) return fail(ctx, PCLB_EUNSUPPORTED, "reverse mode implements n_dirs = 8 only");
   if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
   void* lam = ctx->ws + ctx->lay.lam[ctx->cur_lam];
   const void* f = ctx->ws + ctx->lay.f[ctx->cur];
@@ -809,6 +903,7 @@ pclb_status pclb_moments_vjp(pclb_ctx* ctx, const void* g_rho, const void* g_ur,
 pclb_status pclb_set_state_vjp(pclb_ctx* ctx, const void* rho, const void* u_r, const void* u_theta, const void* T,
                                void* g_rho, void* g_ur, void* g_ut, void* g_T) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (generic(ctx)) return fail(ctx, PCLB_EUNSUPPORTED, "reverse mode implements n_dirs = 8 only");
   if (!rho || !u_r || !u_theta || !T) return fail(ctx, PCLB_EINVAL, "field pointers must not be NULL");
   if (!ctx->has_lam) return fail(ctx, PCLB_ESTATE, "no adjoint variable: call pclb_lambda_set first");
   const void* lam = ctx->ws + ctx->lay.lam[ctx->cur_lam];

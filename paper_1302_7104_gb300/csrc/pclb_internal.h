@@ -61,6 +61,19 @@ struct DvmConst {
   int8_t recv_hi[kQ];         // label whose high ghost rows copy rows 0, 1 of label q
 };
 
+// Velocity sets with N_i = 16 or 24 (Table I), for the generic kernels; all
+// constants in double.
+constexpr int kMaxQ = 1 + 4 * 24;
+struct DvmG {
+  double vx[kMaxQ], vy[kMaxQ];
+  double half_v2[5];          // v_k^2 / 2
+  double Fc[5][4];            // F_k(E) = sum_{n=1..4} Fc[k][n-1] E^n, k = 1..4 (Eq. 11a)
+  double B0;                  // F_0 = 1 - B0 (F_1 + .. + F_4) (Eq. 11b)
+  int shell[kMaxQ];
+  int recv_lo[kMaxQ], recv_hi[kMaxQ];   // as in DvmConst
+  int n_dirs, q;
+};
+
 struct StepParams {
   int n_r, n_theta;           // interior nodes
   int pitch;                  // elements per stored row (multiple of kPitchAlign)
@@ -95,6 +108,7 @@ struct Layout {
   size_t diag_out;            // double [8]
   size_t stage;               // host-I/O staging: 8 fields [n_theta][n_r]
   size_t adj_scratch;         // adjoint ghost states and wall cotangents
+  size_t gen_ghost;           // N_i = 16, 24: radial ghost values [side][layer][n_theta][Q]
   size_t total;
 };
 
@@ -142,5 +156,6 @@ struct pclb_ctx {
   pclb::StepParams sp;
   pclb::DvmConst<float> dvm32;
   pclb::DvmConst<double> dvm64;
+  pclb::DvmG dvmg;            // N_i = 16, 24 (the generic kernels)
   char err[512];
 };

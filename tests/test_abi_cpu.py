@@ -64,8 +64,8 @@ def test_create_rejects_invalid_arguments_without_a_device():
     w = I.uniform(8, 8)
     assert _create(w, dt=-1.0)[0] == 1                      # PCLB_EINVAL
     assert _create(w, dt=10.0)[0] == 6                      # PCLB_ECFL
-    code, msg = _create(w, n_dirs=16)
-    assert code == 8 and "n_dirs" in msg                    # PCLB_EUNSUPPORTED
+    code, msg = _create(w, n_dirs=12)
+    assert code == 8 and "n_dirs" in msg                    # PCLB_EUNSUPPORTED (8, 16, 24 only)
     assert _create(w, ws_bytes=1024)[0] == 2                # PCLB_ENOMEM
     assert _create(w, workspace=100)[0] == 1                # misaligned workspace
     bad = I.uniform(8, 8)
