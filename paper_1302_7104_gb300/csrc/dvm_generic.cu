@@ -1,8 +1,10 @@
 // The step and its field kernels for the larger velocity sets of Table I,
 // N_i = 16 and 24 directions per shell (Q = 65, 97): the same model (Eqs. 2-5,
-// 10-11, 19 or 18, 28 or the other convection schemes, 38-40), evaluated in
-// double for both storage precisions, one thread per node, stencil values read
-// from global memory (L1/L2).  These sets serve the paper's velocity-set
+// 10-11, 19 or 18, 28 or the other convection schemes, 38-40), one thread per
+// node, stencil values read from global memory (L1/L2).  Moments, temperature
+// recovery and the equilibrium factors are formed in double; the per-velocity
+// work (equilibrium polynomial, relaxation, convection) runs in the storage
+// type.  These sets serve the paper's velocity-set
 // comparison; the tuned TMA kernels cover N_i = 8.
 //
 // Radial ghost nodes (Sec. II C 1) are formed once per wall row by
@@ -12,6 +14,7 @@
 // are stored rows, written by the producer of the seam rows with the label
 // rotation, as in the rest of the library.
 #include <cfloat>
+#include <cstddef>
 #include <cuda_runtime.h>
 
 #include "pclb_internal.h"
@@ -76,19 +79,52 @@ __device__ __forceinline__ double gen_feq(const GenEq& e, const DvmG& d, int q) 
   return e.w[d.shell[q]] * (e.a0 + x * (e.a1 + x * (e.a1h + x * (1.0 / 6.0 + x * (1.0 / 24.0)))));
 }
 
+// The equilibrium factors in the arithmetic type C of the per-velocity work
+// (float for FP32 storage, double for FP64), rounded from the double ones.
+template <class C>
+struct GenEqC {
+  C w[5], a0, a1, a1h, uxE, uyE;
+};
+
+template <class C>
+__device__ __forceinline__ GenEqC<C> gen_eq_c(const GenEq& e) {
+  GenEqC<C> c;
+  for (int k = 0; k < 5; ++k) c.w[k] = (C)e.w[k];
+  c.a0 = (C)e.a0; c.a1 = (C)e.a1; c.a1h = (C)e.a1h; c.uxE = (C)e.uxE; c.uyE = (C)e.uyE;
+  return c;
+}
+
+// f^eq of velocity (vx, vy) of shell k, Eq. (10), as even and odd parts in x
+// = v.u/E: P(x) = ev + od, P(-x) = ev - od (the opposite velocity).
+template <class C>
+__device__ __forceinline__ void gen_feq_pair(const GenEqC<C>& e, C vx, C vy, int k, C& fp, C& fm) {
+  const C x = vx * e.uxE + vy * e.uyE, x2 = x * x;
+  const C ev = e.a0 + x2 * (e.a1h + x2 * C(1.0 / 24.0));
+  const C od = x * (e.a1 + x2 * C(1.0 / 6.0));
+  fp = e.w[k] * (ev + od);
+  fm = e.w[k] * (ev - od);
+}
+
+template <class C>
+__device__ __forceinline__ C smallest_normal_c();
+template <>
+__device__ __forceinline__ float smallest_normal_c<float>() { return FLT_MIN; }
+template <>
+__device__ __forceinline__ double smallest_normal_c<double>() { return DBL_MIN; }
+
 // Convection increment in upwind form from a = |C|, K = a (1 - a), the node
 // value f0, its upwind neighbours u1, u2 and (Lax-Wendroff) the downwind one d1.
-template <int SCH>
-__device__ __forceinline__ double gen_convect(double a, double K, double f0, double u1, double u2, double d1) {
-  const double D = f0 - u1, Dp = u1 - u2;
+template <int SCH, class C>
+__device__ __forceinline__ C gen_convect(C a, C K, C f0, C u1, C u2, C d1) {
+  const C D = f0 - u1, Dp = u1 - u2;
   if (SCH == PCLB_SCHEME_MWB) {
-    const double den = fabs(D) + fabs(Dp);
-    const double h = den >= DBL_MIN ? fabs(D) * (D - Dp) / den : 0.0;
+    const C den = fabs(D) + fabs(Dp);
+    const C h = den >= smallest_normal_c<C>() ? fabs(D) * (D - Dp) / den : C(0);
     return a * D + K * h;
   }
-  if (SCH == PCLB_SCHEME_WB) return a * D + 0.5 * K * (D - Dp);
-  if (SCH == PCLB_SCHEME_UPWIND2) return a * D + 0.5 * a * (D - Dp);
-  return a * D + 0.5 * K * ((d1 - f0) - D);
+  if (SCH == PCLB_SCHEME_WB) return a * D + C(0.5) * K * (D - Dp);
+  if (SCH == PCLB_SCHEME_UPWIND2) return a * D + C(0.5) * a * (D - Dp);
+  return a * D + C(0.5) * K * ((d1 - f0) - D);
 }
 
 // Store of label q at interior node (t, r), and of the azimuthal ghost rows
@@ -206,9 +242,11 @@ __global__ void __launch_bounds__(kGenThreads)
   if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
 }
 
-// One step (Eq. 38) at node (t, r): moments, equilibrium, relaxation (decay
+// One step (Eq. 38) at node (t, r): moments and equilibrium factors in
+// double, then per pair of opposite velocities (sharing the Courant entry and
+// the even and odd parts of the equilibrium polynomial) the relaxation (decay
 // d = exp(-dt/tau) or 1 - dt/tau) minus the convection increments in r and
-// theta, per pair of opposite velocities sharing the Courant entry.
+// theta, in the storage type T.
 template <class T, int SCH>
 __global__ void __launch_bounds__(kGenThreads)
     gen_step_kernel(const T* __restrict__ f, T* __restrict__ f_out, const T* __restrict__ ghost,
@@ -221,39 +259,41 @@ __global__ void __launch_bounds__(kGenThreads)
   const T* fn = f + (size_t)srow * p.pitch + r;
   const GenState m = gen_moments_node(fn, plane, d);
   if (!m.ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
-  const GenEq e = gen_eq(m.rho, m.ux, m.uy, m.E, d);
-  const double decay = p.decay;
+  const GenEq ed = gen_eq(m.rho, m.ux, m.uy, m.E, d);
+  const GenEqC<T> e = gen_eq_c<T>(ed);
+  const T decay = (T)p.decay;
   // value of label q at radial index rr of row t (a ghost layer outside the grid)
-  auto fr = [&](int q, int rr) -> double {
-    if (rr < 0) return (double)ghost[((size_t)(0 * 2 + (-1 - rr)) * p.n_theta + t) * d.q + q];
-    if (rr >= p.n_r) return (double)ghost[((size_t)(1 * 2 + (rr - p.n_r)) * p.n_theta + t) * d.q + q];
-    return (double)fn[(size_t)q * plane + (rr - r)];
+  auto fr = [&](int q, int rr) -> T {
+    if (rr < 0) return ghost[((size_t)(0 * 2 + (-1 - rr)) * p.n_theta + t) * d.q + q];
+    if (rr >= p.n_r) return ghost[((size_t)(1 * 2 + (rr - p.n_r)) * p.n_theta + t) * d.q + q];
+    return fn[(size_t)q * plane + (rr - r)];
   };
   // value of label q at stored row srow + dt_rows of column r
-  auto ft = [&](int q, int dt_rows) -> double { return (double)fn[(size_t)q * plane + (ptrdiff_t)dt_rows * p.pitch]; };
+  auto ft = [&](int q, int dt_rows) -> T { return fn[(size_t)q * plane + (ptrdiff_t)dt_rows * p.pitch]; };
   {
-    const double f0 = (double)fn[0];
-    const double fe = gen_feq(e, d, 0);
+    const T f0 = fn[0];
+    const T fe = e.w[0] * e.a0;
     gen_store<T>(f_out, p, d, 0, t, r, fe + (f0 - fe) * decay);
   }
   const int half = d.n_dirs / 2, npairs = 2 * d.n_dirs;
-  const double inv_r = p.inv_r[r];
+  const T inv_r = (T)p.inv_r[r];
   const bool lw = SCH == PCLB_SCHEME_LW;
   for (int k = 1; k <= 4; ++k)
     for (int i = 0; i < half; ++i) {
       const int q1 = 1 + (k - 1) * d.n_dirs + i, q2 = q1 + half;
       const double* ce = p.courant64 + ((size_t)srow * npairs + (k - 1) * half + i) * 4;
-      const double ar = ce[0], kr = ce[1], at = ce[2] * inv_r, kt = at - at * at;
+      const T ar = (T)ce[0], kr = (T)ce[1], at = (T)ce[2] * inv_r, kt = at - at * at;
       const int fl = (int)ce[3];
       const int sr = (fl & 1) ? 1 : -1;   // v_r < 0 for q1: upwind at larger r
       const int st = (fl & 2) ? 1 : -1;   // v_theta < 0 for q1: upwind at larger theta
+      T fe[2];
+      gen_feq_pair<T>(e, (T)d.vx[q1], (T)d.vy[q1], k, fe[0], fe[1]);
       for (int L = 0; L < 2; ++L) {
         const int q = L ? q2 : q1, s_r = L ? -sr : sr, s_t = L ? -st : st;
-        const double a = (double)fn[(size_t)q * plane];
-        const double fe = gen_feq(e, d, q);
-        const double cr = gen_convect<SCH>(ar, kr, a, fr(q, r + s_r), fr(q, r + 2 * s_r), lw ? fr(q, r - s_r) : 0.0);
-        const double ct = gen_convect<SCH>(at, kt, a, ft(q, s_t), ft(q, 2 * s_t), lw ? ft(q, -s_t) : 0.0);
-        gen_store<T>(f_out, p, d, q, t, r, fe + (a - fe) * decay - cr - ct);
+        const T a = fn[(size_t)q * plane];
+        const T cr = gen_convect<SCH, T>(ar, kr, a, fr(q, r + s_r), fr(q, r + 2 * s_r), lw ? fr(q, r - s_r) : T(0));
+        const T ct = gen_convect<SCH, T>(at, kt, a, ft(q, s_t), ft(q, 2 * s_t), lw ? ft(q, -s_t) : T(0));
+        gen_store<T>(f_out, p, d, q, t, r, (double)(fe[L] + (a - fe[L]) * decay - cr - ct));
       }
     }
 }
