@@ -2,14 +2,28 @@
 //
 // For the weights w_q = f_q (moments) or w_q = f_q - f^eq_q (departures) and
 // the velocities c_q = v_q (plain) or c_q = v_q - u (central), in polar
-// components at the node, the kernel forms
+// components at the node, the groups are
 //   M_2 = sum w c c (rr, r theta, theta theta),
 //   M_3 = sum w c c c (rrr, rr theta, r theta theta, theta theta theta),
 //   M_{3,1} = sum w (c.c/2) c (r, theta),
 //   M_{4,2} = sum w (c.c/2) c c (rr, r theta, theta theta),
 // for each requested group: M_m(f), Delta_m = M_m(f - f^eq), M*_m(f) and
-// Delta*_m = M*_m(f - f^eq).  f^eq is the equilibrium of Eq. (10) at the
-// node's own moments (Eqs. 3-5), evaluated exactly as the step kernels do.
+// Delta*_m = M*_m(f - f^eq).
+//
+// One pass accumulates the 12 central moments M*_m(f) of the node.  The
+// others follow per node:
+//   * Delta*_m = M*_m(f) - M*_m(f^eq), and the central moments of the model's
+//     equilibrium are those of the Maxwellian, (rho E I, 0, 0, 2 rho E^2 I)
+//     (the relations the velocity set is built to satisfy, Eqs. 6-9);
+//   * the plain moments from the central ones with v = u + c: with
+//     S = M*_2, T = M*_3, V = M*_{3,1}, Q = M*_{4,2} and sum w c = 0,
+//       M_2 = S + rho u u,
+//       M_3 = T + (u S + S u + ...: the three placements of u) + rho u u u,
+//       M_{3,1} = V + S u + u tr(S)/2 + rho u |u|^2/2,
+//       M_{4,2} = Q + u V + V u + u.T + u u tr(S)/2 + u (S u) + (S u) u
+//                 + |u|^2/2 S + rho |u|^2/2 u u;
+//     the departures the same way from Delta*_m with rho replaced by
+//     sum (f - f^eq) = 0 (f and f^eq share mass, momentum and energy).
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -22,46 +36,56 @@ namespace {
 
 constexpr int kNeqThreads = 128;
 
-// Node state and equilibrium factors in the precision of the step kernels.
+// rho, u and E of the node in the precision of the step kernels (float-float
+// moments in FP32), and rho E, 2 rho E^2 in double.
 __device__ __forceinline__ void neq_state(const float* f, size_t plane, const DvmConst<float>& d, float& rho,
-                                          float& ux, float& uy, bool& ok, Eq32& e) {
+                                          float& ux, float& uy, bool& ok, double& rE, double& rE2) {
   const State32 s = state32(f, plane, d);
-  e = eq32(s, d);
-  rho = s.rho.hi + s.rho.lo;
+  const double R = (double)s.rho.hi + s.rho.lo, E = (double)s.E.hi + s.E.lo;
+  rho = (float)R;
   ux = s.ux.hi + s.ux.lo;
   uy = s.uy.hi + s.uy.lo;
   ok = s.ok;
-}
-// label q = 1 + (k - 1) N_i + i: shell k, direction i (q = 0: rest)
-__device__ __forceinline__ float neq_feq(const Eq32& e, const DvmConst<float>& d, int q) {
-  if (q == 0) return feq32(e, d, 0, 0, 1.f);
-  const int k = 1 + (q - 1) / kNDirs, i = (q - 1) % kNDirs;
-  return i < kHalf ? feq32(e, d, k, i, 1.f) : feq32(e, d, k, i - kHalf, -1.f);
+  rE = R * E;
+  rE2 = 2.0 * R * E * E;
 }
 
 __device__ __forceinline__ void neq_state(const double* f, size_t plane, const DvmConst<double>& d, double& rho,
-                                          double& ux, double& uy, bool& ok, EqParams<double>& e) {
+                                          double& ux, double& uy, bool& ok, double& rE, double& rE2) {
   const NodeState<double> m = node_moments(f, plane, d);
-  e = eq_params<double>(m.rho_d, m.ux, m.uy, m.E_d, d);
   rho = m.rho;
   ux = m.ux;
   uy = m.uy;
   ok = m.ok;
-}
-__device__ __forceinline__ double neq_feq(const EqParams<double>& e, const DvmConst<double>& d, int q) {
-  return feq_q<double>(e, d.vx[q], d.vy[q], q == 0 ? 0 : 1 + (q - 1) / kNDirs);
+  rE = m.rho_d * m.E_d;
+  rE2 = 2.0 * m.rho_d * m.E_d * m.E_d;
 }
 
+// Plain moments (12 components, order as above) from central ones C with
+// density R (0 for departures) and velocity (ur, ut), polar components.
 template <class T>
-struct NeqEq;
-template <>
-struct NeqEq<float> {
-  using type = Eq32;
-};
-template <>
-struct NeqEq<double> {
-  using type = EqParams<double>;
-};
+__device__ __forceinline__ void plain_from_central(T R, T ur, T ut, const T* C, T* M) {
+  const T Srr = C[0], Srt = C[1], Stt = C[2];
+  const T Trrr = C[3], Trrt = C[4], Trtt = C[5], Tttt = C[6];
+  const T Vr = C[7], Vt = C[8];
+  const T trS2 = T(0.5) * (Srr + Stt);
+  const T u2 = T(0.5) * (ur * ur + ut * ut);
+  const T Sur = Srr * ur + Srt * ut, Sut = Srt * ur + Stt * ut;   // S u
+  M[0] = Srr + R * ur * ur;
+  M[1] = Srt + R * ur * ut;
+  M[2] = Stt + R * ut * ut;
+  M[3] = Trrr + T(3) * ur * Srr + R * ur * ur * ur;
+  M[4] = Trrt + T(2) * ur * Srt + ut * Srr + R * ur * ur * ut;
+  M[5] = Trtt + ur * Stt + T(2) * ut * Srt + R * ur * ut * ut;
+  M[6] = Tttt + T(3) * ut * Stt + R * ut * ut * ut;
+  M[7] = Vr + Sur + ur * trS2 + R * ur * u2;
+  M[8] = Vt + Sut + ut * trS2 + R * ut * u2;
+  // u.T for the pairs (rr, rt, tt): u_r T_r.. + u_t T_t..
+  const T uTrr = ur * Trrr + ut * Trrt, uTrt = ur * Trrt + ut * Trtt, uTtt = ur * Trtt + ut * Tttt;
+  M[9] = C[9] + T(2) * ur * Vr + uTrr + ur * ur * trS2 + T(2) * ur * Sur + u2 * Srr + R * u2 * ur * ur;
+  M[10] = C[10] + ur * Vt + ut * Vr + uTrt + ur * ut * trS2 + ur * Sut + ut * Sur + u2 * Srt + R * u2 * ur * ut;
+  M[11] = C[11] + T(2) * ut * Vt + uTtt + ut * ut * trS2 + T(2) * ut * Sut + u2 * Stt + R * u2 * ut * ut;
+}
 
 }  // namespace
 
@@ -76,50 +100,59 @@ __global__ void __launch_bounds__(kNeqThreads)
   const T* fn = f + (size_t)(t + kGhostRows) * p.pitch + r;
   T rho, ux, uy;
   bool ok;
-  typename NeqEq<T>::type e;
-  neq_state(fn, plane, d, rho, ux, uy, ok, e);
+  double rE, rE2;
+  neq_state(fn, plane, d, rho, ux, uy, ok, rE, rE2);
   if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
   const T cs = (T)p.cos_t[t], sn = (T)p.sin_t[t];
   const T u_r = ux * cs + uy * sn, u_t = uy * cs - ux * sn;
 
-  T m[4][12];
+  // central moments of f
+  T A[12];
 #pragma unroll
-  for (int g = 0; g < 4; ++g)
-#pragma unroll
-    for (int c = 0; c < 12; ++c) m[g][c] = T(0);
+  for (int c = 0; c < 12; ++c) A[c] = T(0);
 #pragma unroll
   for (int q = 0; q < kQ; ++q) {
-    const T fq = fn[(size_t)q * plane];
-    const T dq = fq - neq_feq(e, d, q);
-    const T vr = d.vx[q] * cs + d.vy[q] * sn, vt = d.vy[q] * cs - d.vx[q] * sn;
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      if (!(groups & (1 << g))) continue;
-      const T w = (g == 1 || g == 3) ? dq : fq;
-      const T cr = g >= 2 ? vr - u_r : vr, ct = g >= 2 ? vt - u_t : vt;
-      const T h = T(0.5) * (cr * cr + ct * ct);
-      const T wr = w * cr, wt = w * ct;
-      m[g][0] += wr * cr;
-      m[g][1] += wr * ct;
-      m[g][2] += wt * ct;
-      m[g][3] += wr * cr * cr;
-      m[g][4] += wr * cr * ct;
-      m[g][5] += wr * ct * ct;
-      m[g][6] += wt * ct * ct;
-      m[g][7] += h * wr;
-      m[g][8] += h * wt;
-      m[g][9] += h * wr * cr;
-      m[g][10] += h * wr * ct;
-      m[g][11] += h * wt * ct;
-    }
+    const T w = fn[(size_t)q * plane];
+    const T cr = d.vx[q] * cs + d.vy[q] * sn - u_r, ct = d.vy[q] * cs - d.vx[q] * sn - u_t;
+    const T h = T(0.5) * (cr * cr + ct * ct);
+    const T wr = w * cr, wt = w * ct;
+    const T wrr = wr * cr, wrt = wr * ct, wtt = wt * ct;
+    A[0] += wrr;
+    A[1] += wrt;
+    A[2] += wtt;
+    A[3] += wrr * cr;
+    A[4] += wrr * ct;
+    A[5] += wrt * ct;
+    A[6] += wtt * ct;
+    A[7] += h * wr;
+    A[8] += h * wt;
+    A[9] += h * wrr;
+    A[10] += h * wrt;
+    A[11] += h * wtt;
   }
+  // central departures: minus the equilibrium's (rho E I, 0, 0, 2 rho E^2 I)
+  T D[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) D[c] = A[c];
+  D[0] = (T)((double)A[0] - rE);
+  D[2] = (T)((double)A[2] - rE);
+  D[9] = (T)((double)A[9] - rE2);
+  D[11] = (T)((double)A[11] - rE2);
+
   const size_t nodes = (size_t)p.n_theta * p.n_r, n = (size_t)t * p.n_r + r;
   int slot = 0;
-#pragma unroll
+  T out_g[12];
+#pragma unroll 1
   for (int g = 0; g < 4; ++g) {
     if (!(groups & (1 << g))) continue;
+    if (g == 0) plain_from_central<T>(rho, u_r, u_t, A, out_g);
+    else if (g == 1) plain_from_central<T>(T(0), u_r, u_t, D, out_g);
+    else if (g == 2)
+      for (int c = 0; c < 12; ++c) out_g[c] = A[c];
+    else
+      for (int c = 0; c < 12; ++c) out_g[c] = D[c];
 #pragma unroll
-    for (int c = 0; c < 12; ++c) out[(size_t)(slot * 12 + c) * nodes + n] = m[g][c];
+    for (int c = 0; c < 12; ++c) out[(size_t)(slot * 12 + c) * nodes + n] = out_g[c];
     ++slot;
   }
 }
