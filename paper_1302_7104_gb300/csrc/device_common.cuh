@@ -110,9 +110,11 @@ struct NodeState {
 // FP64: plain double sums.
 // ---------------------------------------------------------------------------
 // 1/n by the Newton-Raphson iteration r <- r (2 - n r) from the hardware's
-// approximate reciprocal; each step doubles the number of correct bits, two
-// reach full double precision (checked against the division in the parity
-// tests).  n must be a positive normal number.
+// approximate reciprocal (rcp.approx.ftz.f64: relative error <= 1e-6,
+// measured 9.9e-7 over 6.7e7 arguments); each step squares the relative
+// error.  Two steps reach the correctly rounded quotient in every argument
+// measured; one step leaves <= 1e-12 (measured 9.9e-13).  n must be a
+// positive normal number.
 __device__ __forceinline__ double recip_newton(double n) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(n));
@@ -120,6 +122,11 @@ __device__ __forceinline__ double recip_newton(double n) {
   r = fma(r, e, r);
   e = fma(-n, r, 1.0);
   return fma(r, e, r);
+}
+__device__ __forceinline__ double recip_newton1(double n) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(n));
+  return fma(r, fma(-n, r, 1.0), r);
 }
 
 __device__ __forceinline__ double recip_refined(double x) {

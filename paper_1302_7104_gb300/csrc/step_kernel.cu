@@ -5,7 +5,7 @@
 //   1. one thread issues 33 TMA box copies (one per velocity plane) of the
 //      window [r0-4, r0+36) x [t0-2, t0+18) into shared memory, completing on
 //      one mbarrier (bounded wait);
-//   2. every thread computes the moments (Eqs. 3-5) of its two nodes and
+//   2. every thread computes the moments (Eqs. 3-5) of its node(s) and
 //      factors their equilibrium (Eqs. 10-11);
 //   3. CTAs whose window covers a wall compute the radial ghost columns in
 //      shared memory: moments of the two wall nodes, Eq. (39) extrapolation
@@ -31,6 +31,10 @@ constexpr int kPlane = kWinR * kWinT;   // elements per velocity plane in shared
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
 constexpr int kPairs64 = 4 * kNDirs / 2;   // pairs of opposite velocities
+constexpr int kThreads64 = 512;            // 16 warps: one node per thread
+constexpr int kWarps64 = kThreads64 / 32;
+constexpr int kNodes64 = kTileT / kWarps64;   // nodes per thread (rows w, w + kWarps64, ..)
+static_assert(kTileT % kWarps64 == 0 && kPairs64 * kTileT <= 2 * kThreads64, "tile / thread mapping");
 
 template <class T>
 constexpr int step_smem_bytes() {
@@ -40,21 +44,25 @@ constexpr int step_smem_bytes() {
 
 // Convection increment (upwind form, see convect in device_common.cuh) from
 // a = |C| and K = a (1 - a) given by the Courant table.
+// Limiter part of the MWB increment, h = |D| (D - Dp) / (|D| + |Dp|), 0 when
+// D = Dp = 0.  One Newton step on the reciprocal: h then carries a relative
+// error <= 1e-12, i.e. K h <= 2.5e-13 |D| (K <= 1/4) in the update.
+__device__ __forceinline__ double mwb_h(double D, double Dp) {
+  const double den = fabs(D) + fabs(Dp);
+  return den >= 2.2250738585072014e-308 ? fabs(D) * (D - Dp) * recip_newton1(den) : 0.0;
+}
+
 template <int SCH>
 __device__ __forceinline__ double convect_aK(double a, double K, double f0, double u1, double u2, double d1) {
   const double D = f0 - u1, Dp = u1 - u2;
-  if (SCH == PCLB_SCHEME_MWB) {
-    const double den = fabs(D) + fabs(Dp);
-    const double h = den >= 2.2250738585072014e-308 ? fabs(D) * (D - Dp) * recip_newton(den) : 0.0;
-    return a * D + K * h;
-  }
+  if (SCH == PCLB_SCHEME_MWB) return a * D + K * mwb_h(D, Dp);
   if (SCH == PCLB_SCHEME_WB) return a * D + 0.5 * K * (D - Dp);
   if (SCH == PCLB_SCHEME_UPWIND2) return a * D + 0.5 * a * (D - Dp);
   return a * D + 0.5 * K * ((d1 - f0) - D);
 }
 
 template <class T, int SCH>
-__global__ void __launch_bounds__(kStepThreads, 1)
+__global__ void __launch_bounds__(kThreads64, 1)
     step_kernel(const __grid_constant__ CUtensorMap tmap_in, T* __restrict__ f_out,
                 const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -79,8 +87,9 @@ __global__ void __launch_bounds__(kStepThreads, 1)
 #pragma unroll 1
     for (int q = 0; q < kQ; ++q) tma_load_3d(sm + q * kPlane, &tmap_in, r0 - kLeft, t0, q, bar);
   }
-  {  // Courant entries of the tile rows (from the FP64 table of the context)
-    const int pair = threadIdx.x / kTileT, rl = threadIdx.x % kTileT;
+  // Courant entries of the tile rows (from the FP64 table of the context)
+  for (int i = threadIdx.x; i < kPairs64 * kTileT; i += kThreads64) {
+    const int pair = i / kTileT, rl = i % kTileT;
     const int tt = min(t0 + rl, p.n_theta - 1);
     const double* e = p.courant64 + ((size_t)(tt + kGhostRows) * kPairs64 + pair) * 4;
 #pragma unroll
@@ -96,14 +105,14 @@ __global__ void __launch_bounds__(kStepThreads, 1)
   // ---- 2. moments and equilibrium factors of this thread's two nodes ------
   const int r = r0 + lane;
   const int col = kLeft + lane;
-  int row[2], t[2];
-  bool valid[2];
-  EqParams<T> eq[2];
+  int row[kNodes64], t[kNodes64];
+  bool valid[kNodes64];
+  EqParams<T> eq[kNodes64];
   bool ok = true;
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    row[c] = 2 + warp + 8 * c;
-    t[c] = t0 + warp + 8 * c;
+  for (int c = 0; c < kNodes64; ++c) {
+    row[c] = 2 + warp + kWarps64 * c;
+    t[c] = t0 + warp + kWarps64 * c;
     valid[c] = (r < p.n_r) && (t[c] < p.n_theta);
     NodeState<T> m;
     if (valid[c]) {
@@ -131,7 +140,7 @@ __global__ void __launch_bounds__(kStepThreads, 1)
 
   // ---- 4. relaxation minus MWB increments, per pair of opposite velocities --
   const T inv_r = (r < p.n_r) ? (T)p.inv_r[r] : T(1);
-  const T decay = (T)p.decay;
+  const T decay = (T)p.decay, omd = T(1) - decay;
   const size_t plane_out = (size_t)p.rows * p.pitch;
   auto store = [&](int q, int c, T out) {
     T* dst = f_out + (size_t)q * plane_out + r;
@@ -142,7 +151,7 @@ __global__ void __launch_bounds__(kStepThreads, 1)
       f_out[(size_t)d.recv_hi[q] * plane_out + (size_t)(p.n_theta + kGhostRows + t[c]) * p.pitch + r] = out;
   };
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {   // rest velocity: no convection
+  for (int c = 0; c < kNodes64; ++c) {   // rest velocity: no convection
     if (!valid[c]) continue;
     const T f0 = sm[row[c] * kWinR + col];
     const T fe = eq[c].w[0] * eq[c].a0;
@@ -159,9 +168,9 @@ __global__ void __launch_bounds__(kStepThreads, 1)
       const int q1 = 1 + (k - 1) * kNDirs + i, q2 = q1 + kNDirs / 2;
       const T vx = d.vx[q1], vy = d.vy[q1];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
+      for (int c = 0; c < kNodes64; ++c) {
         if (!valid[c]) continue;
-        const T* e = tab + (pair * kTileT + warp + 8 * c) * 4;
+        const T* e = tab + (pair * kTileT + warp + kWarps64 * c) * 4;
         const T ar = e[0], kr = e[1], at = e[2] * inv_r, kt = at - at * at;
         const int fl = (int)e[3];
         const int sr = (fl & 1) ? 1 : -1;               // v_r < 0 for q1: upwind at larger r
@@ -170,17 +179,37 @@ __global__ void __launch_bounds__(kStepThreads, 1)
         const T x = vx * eq[c].uxE + vy * eq[c].uyE, x2 = x * x;
         const T ev = eq[c].a0 + x2 * (eq[c].a1h + x2 * T(1.0 / 24.0));
         const T od = x * (eq[c].a1 + x2 * T(1.0 / 6.0));
-        const T fe1 = eq[c].w[k] * (ev + od), fe2 = eq[c].w[k] * (ev - od);
+        const T fe1 = SCH == PCLB_SCHEME_MWB ? T(0) : eq[c].w[k] * (ev + od);
+        const T fe2 = SCH == PCLB_SCHEME_MWB ? T(0) : eq[c].w[k] * (ev - od);
         const T* fp1 = sm + q1 * kPlane + row[c] * kWinR + col;
         const T* fp2 = sm + q2 * kPlane + row[c] * kWinR + col;
         const bool lw = SCH == PCLB_SCHEME_LW;
         const T a = fp1[0], b = fp2[0];
-        const T o1 = fe1 + (a - fe1) * decay -
-                     convect_aK<SCH>(ar, kr, a, fp1[sr], fp1[2 * sr], lw ? fp1[-sr] : T(0)) -
-                     convect_aK<SCH>(at, kt, a, fp1[st], fp1[2 * st], lw ? fp1[-st] : T(0));
-        const T o2 = fe2 + (b - fe2) * decay -
-                     convect_aK<SCH>(ar, kr, b, fp2[-sr], fp2[-2 * sr], lw ? fp2[sr] : T(0)) -
-                     convect_aK<SCH>(at, kt, b, fp2[-st], fp2[-2 * st], lw ? fp2[st] : T(0));
+        T o1, o2;
+        if constexpr (SCH == PCLB_SCHEME_MWB) {
+          // relaxation minus a D + K h in r and theta, as one chain of fused
+          // multiply-adds
+          // (1 - d) f^eq + d f0 = (1 - d) rho F_k P + d f0
+          const T wd = omd * eq[c].w[k];
+          auto mwb = [&](T f0, T P, const T* fp, int s_r, int s_t) {
+            const T u1 = fp[s_r], v1 = fp[s_t];
+            const T Dr = f0 - u1, Dt = f0 - v1;
+            T o = fma(wd, P, decay * f0);
+            o = fma(-ar, Dr, o);
+            o = fma(-kr, mwb_h(Dr, u1 - fp[2 * s_r]), o);
+            o = fma(-at, Dt, o);
+            return fma(-kt, mwb_h(Dt, v1 - fp[2 * s_t]), o);
+          };
+          o1 = mwb(a, ev + od, fp1, sr, st);
+          o2 = mwb(b, ev - od, fp2, -sr, -st);
+        } else {
+          o1 = fe1 + (a - fe1) * decay -
+               convect_aK<SCH>(ar, kr, a, fp1[sr], fp1[2 * sr], lw ? fp1[-sr] : T(0)) -
+               convect_aK<SCH>(at, kt, a, fp1[st], fp1[2 * st], lw ? fp1[-st] : T(0));
+          o2 = fe2 + (b - fe2) * decay -
+               convect_aK<SCH>(ar, kr, b, fp2[-sr], fp2[-2 * sr], lw ? fp2[sr] : T(0)) -
+               convect_aK<SCH>(at, kt, b, fp2[-st], fp2[-2 * st], lw ? fp2[st] : T(0));
+        }
         store(q1, c, o1);
         store(q2, c, o2);
       }
@@ -199,7 +228,7 @@ static cudaError_t launch_scheme(const CUtensorMap* tmap_in, T* f_out, const Ste
     configured = true;
   }
   dim3 grid((p.n_r + kTileR - 1) / kTileR, (p.n_theta + kTileT - 1) / kTileT);
-  step_kernel<T, SCH><<<grid, kStepThreads, smem, stream>>>(*tmap_in, f_out, p, d);
+  step_kernel<T, SCH><<<grid, kThreads64, smem, stream>>>(*tmap_in, f_out, p, d);
   return cudaGetLastError();
 }
 
