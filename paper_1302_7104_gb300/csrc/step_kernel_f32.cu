@@ -257,13 +257,13 @@ __global__ void __launch_bounds__(kStepThreads32, kCtasPerSm32)
   const int t0 = blockIdx.y * kTileT32;
   const int tid = threadIdx.x;
 
+  // Thread 0 initialises the barriers and issues the copies at once; the
+  // block barrier below (after the table fill) makes the initialised
+  // barriers visible to the other threads before their first wait.
   if (tid == 0) {
     tma_prefetch_desc(&tmap_in);
     for (int g = 0; g < kGroups; ++g) mbar_init(&bar[g], 1);
     mbar_fence_init();
-  }
-  __syncthreads();
-  if (tid == 0) {
 #pragma unroll 1
     for (int g = 0; g < kGroups; ++g) {
       const int q0 = group_first(g), n = group_planes(g);
