@@ -240,13 +240,15 @@ pclb_status pclb_status_flags(pclb_ctx* ctx, uint32_t* flags, int32_t clear);
  * timeout_ms milliseconds (PCLB_ETIMEOUT when it runs out). */
 pclb_status pclb_sync(pclb_ctx* ctx, int32_t timeout_ms);
 
-/* End-to-end call with host buffers: copy rho, u_r, u_theta, T (host,
+/* End-to-end call with host buffers: bring rho, u_r, u_theta, T (host,
  * [n_theta][n_r], context precision) to the device, set f = f^eq, advance n
- * steps, compute the moments and copy them back to the host arrays
- * out_rho .. out_T (any may be NULL).  Staging lives in the workspace tail
- * (pclb_workspace_size reserves it).  For page-locked host memory the copies
- * are asynchronous DMA; the call returns after the results are on the host
- * (bounded wait). */
+ * steps, compute the moments and bring them back to the host arrays
+ * out_rho .. out_T (any may be NULL).  When every buffer is page-locked
+ * (cudaHostAlloc / cudaHostRegister, e.g. torch's pin_memory) the set-state
+ * and moment kernels read and write them through their device mapping, so the
+ * transfers overlap the kernels; otherwise the fields are staged through the
+ * workspace tail (pclb_workspace_size reserves it) with stream-ordered copies.
+ * The call returns after the results are on the host (bounded wait). */
 pclb_status pclb_run_host(pclb_ctx* ctx, const void* rho, const void* u_r, const void* u_theta,
                           const void* T, int32_t n, void* out_rho, void* out_u_r,
                           void* out_u_theta, void* out_T);

@@ -327,7 +327,7 @@ pclb_status bounded_sync(pclb_ctx* ctx, int timeout_ms) {
       break;
     }
     std::this_thread::sleep_for(std::chrono::microseconds(sleep_us));
-    if (sleep_us < 200) sleep_us *= 2;
+    if (sleep_us < 20) sleep_us *= 2;
   }
   cudaEventDestroy(ev);
   return st;
@@ -747,6 +747,33 @@ pclb_status pclb_run_host(pclb_ctx* ctx, const void* rho, const void* u_r, const
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
   if (!rho || !u_r || !u_theta || !T) return fail(ctx, PCLB_EINVAL, "input pointers must not be NULL");
   if (n < 0) return fail(ctx, PCLB_EINVAL, "n = %d must be >= 0", n);
+  // Page-locked host buffers are read and written by the kernels themselves
+  // through their device mapping (the transfers overlap the set-state and
+  // moment kernels); other host memory goes through staging copies.
+  {
+    const void* ptrs[8] = {rho, u_r, u_theta, T, out_rho, out_u_r, out_u_theta, out_T};
+    void* mapped[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool direct = true;
+    for (int i = 0; i < 8 && direct; ++i) {
+      if (!ptrs[i]) continue;
+      cudaPointerAttributes a;
+      if (cudaPointerGetAttributes(&a, ptrs[i]) != cudaSuccess) {
+        cudaGetLastError();
+        direct = false;
+      } else if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) {
+        direct = false;
+      } else {
+        mapped[i] = a.devicePointer;
+      }
+    }
+    if (direct) {
+      pclb_status st = pclb_set_state(ctx, mapped[0], mapped[1], mapped[2], mapped[3]);
+      if (st != PCLB_OK) return st;
+      if ((st = pclb_step(ctx, n)) != PCLB_OK) return st;
+      if ((st = pclb_moments(ctx, mapped[4], mapped[5], mapped[6], mapped[7])) != PCLB_OK) return st;
+      return bounded_sync(ctx, kDefaultTimeoutMs);
+    }
+  }
   const size_t bytes = (size_t)ctx->grid.n_r * ctx->grid.n_theta * elem_size(ctx->prec);
   unsigned char* stage = ctx->ws + ctx->lay.stage;
   const void* in[4] = {rho, u_r, u_theta, T};
@@ -761,7 +788,6 @@ pclb_status pclb_run_host(pclb_ctx* ctx, const void* rho, const void* u_r, const
   void* dev[4];
   for (int i = 0; i < 4; ++i) dev[i] = outs[i] ? stage + (4 + i) * bytes : nullptr;
   if ((st = pclb_moments(ctx, dev[0], dev[1], dev[2], dev[3])) != PCLB_OK) return st;
-  if ((st = bounded_sync(ctx, kDefaultTimeoutMs)) != PCLB_OK) return st;
   for (int i = 0; i < 4; ++i) {
     if (!outs[i]) continue;
     cudaError_t e = cudaMemcpyAsync(outs[i], dev[i], bytes, cudaMemcpyDeviceToHost, ctx->stream);

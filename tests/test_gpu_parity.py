@@ -185,10 +185,19 @@ def test_step_before_state_is_refused():
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_run_host_equals_device_path(prec):
+@pytest.mark.parametrize("pinned_in,pinned_out", [(True, False), (False, False), (True, True)])
+def test_run_host_equals_device_path(prec, pinned_in, pinned_out):
+    """pclb_run_host gives the device path's fields bit for bit, whether the
+    kernels access page-locked buffers directly (all pinned) or the fields are
+    staged through the workspace (any pageable buffer)."""
     w = I.random_smooth(50, 30, seed=17)
+    dtype = torch.float32 if prec == "fp32" else torch.float64
     with P.PCLB(w, precision=prec) as g:
         dev = [x.cpu() for x in g.set_state().step(4).moments()]
-        host = g.run_host(*[torch.as_tensor(x).pin_memory() for x in w.fields()], 4)
+        ins = [torch.as_tensor(x, dtype=dtype) for x in w.fields()]
+        ins = [x.pin_memory() if pinned_in else x for x in ins]
+        outs = [torch.full((w.n_theta, w.n_r), float("nan"), dtype=dtype) for _ in range(4)]
+        outs = [x.pin_memory() if pinned_out else x for x in outs]
+        host = g.run_host(*ins, 4, outs)
     for a, b in zip(host, dev):
         assert torch.equal(a, b)
