@@ -49,7 +49,9 @@ constexpr int step_smem_bytes() {
 // error <= 1e-12, i.e. K h <= 2.5e-13 |D| (K <= 1/4) in the update.
 __device__ __forceinline__ double mwb_h(double D, double Dp) {
   const double den = fabs(D) + fabs(Dp);
-  return den >= 2.2250738585072014e-308 ? fabs(D) * (D - Dp) * recip_newton1(den) : 0.0;
+  // den >= 2^-1022 (the smallest normal number), tested on the high word of
+  // the non-negative den with an integer compare (keeps the FP64 pipe free)
+  return __double2hiint(den) >= 0x00100000 ? fabs(D) * (D - Dp) * recip_newton1(den) : 0.0;
 }
 
 template <int SCH>
