@@ -84,6 +84,8 @@ struct AdjSize {
   static constexpr int invr_bytes = kTileR * (int)sizeof(T);
   static constexpr int tab_bytes = (TT + 4) * npairs * (int)sizeof(CourEntry<T>);
   static constexpr int smem = ring_bytes + prod_bytes + invr_bytes + tab_bytes + 128;
+  // the ring's planes are TMA destinations: 128-byte aligned
+  static_assert((plane * (int)sizeof(T)) % 128 == 0, "TMA destinations must stay 128-byte aligned");
 };
 
 namespace {

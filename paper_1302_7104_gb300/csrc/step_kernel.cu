@@ -36,6 +36,9 @@ constexpr int kWarps64 = kThreads64 / 32;
 constexpr int kNodes64 = kTileT / kWarps64;   // nodes per thread (rows w, w + kWarps64, ..)
 static_assert(kTileT % kWarps64 == 0 && kPairs64 * kTileT <= 2 * kThreads64, "tile / thread mapping");
 
+// every plane window is a TMA destination: 128-byte aligned
+static_assert((kPlane * 4) % 128 == 0, "TMA destinations must stay 128-byte aligned");
+
 template <class T>
 constexpr int step_smem_bytes() {
   // planes, Courant table [pair][row] of 4 values, barrier slot

@@ -35,6 +35,9 @@ constexpr int kPlaneF = kWinR * (kTileT32 + 4);      // floats per plane window
 constexpr int kPlanesBytes = kQ * kPlaneF * 4;       // 105600
 constexpr int kTabBytes = kPairs * kTileT32 * 16;    // one float4 per (pair, row)
 constexpr int kSmemF32 = kPlanesBytes + kTabBytes + 128;
+// every plane window is a TMA destination: 128-byte aligned (a tile height
+// whose window breaks this faults with a misaligned address)
+static_assert((kPlaneF * 4) % 128 == 0 && kPlanesBytes % 16 == 0, "TMA destinations must stay 128-byte aligned");
 constexpr int kGroups = 4;
 __device__ __forceinline__ int group_first(int g) { return g == 0 ? 0 : 1 + g * kNDirs; }
 __device__ __forceinline__ int group_planes(int g) { return g == 0 ? 1 + kNDirs : kNDirs; }
