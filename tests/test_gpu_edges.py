@@ -1,0 +1,115 @@
+"""Edge cases of the CUDA path through the C ABI: zero steps, interleaved
+contexts on one stream, a large grid ragged in both directions (sampled nodes
+against the oracle), a sector of one period with walls on a ragged grid, and
+forward and adjoint steps interleaved on the caller's stream (the adjoint's
+wall work runs on a side stream joined back before the next launch)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1302_7104_gb300 import inputs as I
+from paper_1302_7104_gb300 import pclb as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _noisy(w, seed=11, scale=0.01):
+    f = O.set_state(w)
+    return np.ascontiguousarray(f * (1.0 + scale * np.random.default_rng(seed).normal(size=f.shape)))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_zero_steps_change_nothing(prec):
+    w = I.random_smooth(37, 19, seed=31)
+    dtype = torch.float32 if prec == "fp32" else torch.float64
+    f0 = torch.as_tensor(_noisy(w), dtype=dtype, device="cuda")
+    with P.PCLB(w, precision=prec) as g:
+        a = g.set_f(f0).step(0).get_f()
+        assert torch.equal(a, f0)
+        host = g.run_host(*[torch.as_tensor(x, dtype=dtype) for x in w.fields()], 0)
+        dev = [x.cpu() for x in g.set_state().moments()]
+    for x, y in zip(host, dev):
+        assert torch.equal(x, y)
+
+
+def test_interleaved_contexts_are_independent():
+    wa = I.random_smooth(40, 24, seed=32, bc_kind=(I.BC_DIRICHLET, I.BC_WALL))
+    wb = I.random_smooth(33, 17, seed=33, n_f=3)
+    fa, fb = _noisy(wa, 1), _noisy(wb, 2)
+    with P.PCLB(wa, precision="fp64") as ga, P.PCLB(wb, precision="fp64") as gb:
+        ga.set_f(torch.as_tensor(fa, device="cuda"))
+        gb.set_f(torch.as_tensor(fb, device="cuda"))
+        for _ in range(3):
+            ga.step(1)
+            gb.step(1)
+        got_a, got_b = ga.get_f().cpu().numpy(), gb.get_f().cpu().numpy()
+    for w, f, got in ((wa, fa, got_a), (wb, fb, got_b)):
+        want = O.run(w, f, 3)
+        assert np.max(np.abs(got - want)) / np.max(np.abs(want)) <= 1e-12
+
+
+def _sample(w, seed=5):
+    nt, nr = w.n_theta, w.n_r
+    rng = np.random.default_rng(seed)
+    it, ir = [], []
+    for c in (0, 1, 2, 3, nr - 4, nr - 3, nr - 2, nr - 1):   # walls
+        rows = rng.integers(0, nt, 24)
+        it += list(rows) + [0, 1, nt - 2, nt - 1]
+        ir += [c] * (len(rows) + 4)
+    for t in (0, 1, 2, 3, nt - 4, nt - 3, nt - 2, nt - 1):   # seam rows
+        cols = rng.integers(0, nr, 24)
+        it += [t] * len(cols)
+        ir += list(cols)
+    # the ragged last tile in r (columns past the last multiple of 32) and in theta
+    it += list(rng.integers(0, nt, 128))
+    ir += list(rng.integers(32 * (nr // 32) - 2, nr, 128))
+    it += list(rng.integers(16 * (nt // 16) - 2, nt, 128))
+    ir += list(rng.integers(0, nr, 128))
+    it += list(rng.integers(0, nt, 512))
+    ir += list(rng.integers(0, nr, 512))
+    return np.asarray(it, dtype=np.int64), np.asarray(ir, dtype=np.int64)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp64", 1e-12)])
+def test_large_ragged_grid_sampled_nodes_match_oracle(prec, tol):
+    # 1999 x 1013: 63 tiles in r with a 15-node tail, 64 tiles in theta with a 5-row tail
+    w = I.random_smooth(1999, 1013, seed=34, bc_kind=(I.BC_WALL, I.BC_DIRICHLET))
+    f = _noisy(w, 3)
+    if prec == "fp32":
+        f = f.astype(np.float32).astype(np.float64)
+    dtype = torch.float32 if prec == "fp32" else torch.float64
+    it, ir = _sample(w)
+    with P.PCLB(w, precision=prec) as g:
+        got_f = g.set_f(torch.as_tensor(f, dtype=dtype, device="cuda")).step(1).get_f()
+        assert g.status_flags() == 0
+        got = got_f[:, torch.as_tensor(it, device="cuda"), torch.as_tensor(ir, device="cuda")].double().cpu().numpy().T
+    want = O.step_nodes(w, f, it, ir)
+    assert np.max(np.abs(got - want)) / np.max(np.abs(f)) <= tol
+
+
+def test_forward_and_adjoint_interleave_on_the_stream():
+    """Alternating steps and adjoint steps on one stream equal the same calls
+    made one by one with a synchronisation after each."""
+    w = I.random_smooth(70, 36, seed=35, bc_kind=(I.BC_WALL, I.BC_EXTRAP))
+    f0 = torch.as_tensor(_noisy(w), device="cuda")
+    lam0 = torch.as_tensor(np.random.default_rng(4).normal(size=(w.q, w.n_theta, w.n_r)), device="cuda")
+
+    def run(sync):
+        with P.PCLB(w, precision="fp64") as g:
+            g.set_f(f0)
+            g.lambda_set(lam0)
+            for _ in range(3):
+                st = g.save_state()
+                g.step(1)
+                if sync:
+                    g.sync()
+                g.adjoint_state(st)
+                if sync:
+                    g.sync()
+            return g.get_f().cpu(), g.lambda_get().cpu()
+
+    a_f, a_l = run(False)
+    b_f, b_l = run(True)
+    assert torch.equal(a_f, b_f) and torch.equal(a_l, b_l)
