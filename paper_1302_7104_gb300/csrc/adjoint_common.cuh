@@ -8,10 +8,6 @@
 
 namespace pclb {
 
-// sign(x) in {-1, 0, 1}
-template <class T>
-__device__ __forceinline__ T sgn(T x) { return copysign(x != T(0) ? T(1) : T(0), x); }
-
 // 1/x for the partials below: the hardware approximation in FP32 (relative
 // error ~1 ulp), two Newton steps on it in FP64 (recip_newton).
 __device__ __forceinline__ float recip_fast(float x) {

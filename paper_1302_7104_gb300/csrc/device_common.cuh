@@ -331,45 +331,18 @@ __device__ __forceinline__ T feq_q(const EqParams<T>& p, T vx, T vy, int k) {
 }
 
 // ---------------------------------------------------------------------------
-// Modified Warming-Beam increment, Eq. (28), in upwind form.  With the
-// upstream values u1 = psi_{j-s}, u2 = psi_{j-2s} (s = sign of C, s = +1 for
-// C >= 0), D = psi_j - u1 and Dp = u1 - u2:
-//   [C + C(1-|C|)(1-S(eta))(1-eta)/2] delta = |C| D + |C|(1-|C|) h,
-//   h = |D| (D - Dp) / (|D| + |Dp|)   (h = 0 when D = Dp = 0),
-// which equals the paper's bracket wherever eta = Dp / D is defined and is its
-// continuous extension elsewhere.
+// Convection increments in upwind form, as the step kernels evaluate them.
+// With the upstream values u1 = psi_{j-s}, u2 = psi_{j-2s} (s = sign of C,
+// s = +1 for C >= 0), D = psi_j - u1, Dp = u1 - u2, the downwind neighbour
+// d1 = psi_{j+s}, a = |C| and K = a (1 - a):
+//   MWB (Eq. 28)          a D + K h,  h = |D| (D - Dp) / (|D| + |Dp|)
+//                         (h = 0 when D = Dp = 0): the paper's bracket
+//                         [C + C(1-|C|)(1-S(eta))(1-eta)/2] delta wherever
+//                         eta = Dp / D is defined, its continuous extension
+//                         elsewhere;
+//   Warming-Beam (Eq. 25) a D + K (D - Dp) / 2;
+//   Lax-Wendroff          a D + K (Dd - D) / 2,   Dd = d1 - psi_j;
+//   2nd-order upwind      a D + a (D - Dp) / 2   (forward Euler with Eq. 23).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float mwb_increment(float C, float f0, float u1, float u2) {
-  const float a = fabsf(C);
-  const float D = f0 - u1, Dp = u1 - u2;
-  const float den = fmaxf(fabsf(D) + fabsf(Dp), 1e-30f);
-  const float h = __fdividef(fabsf(D) * (D - Dp), den);
-  return a * D + (a - a * a) * h;
-}
-
-__device__ __forceinline__ double mwb_increment(double C, double f0, double u1, double u2) {
-  const double a = fabs(C);
-  const double D = f0 - u1, Dp = u1 - u2;
-  const double den = fabs(D) + fabs(Dp);
-  const double h = den > 0.0 ? fabs(D) * (D - Dp) / den : 0.0;
-  return a * D + (a - a * a) * h;
-}
-
-// Convection increment of one node for the scheme SCH (pclb_scheme), in
-// upwind form: D = psi_j - psi_{j+u}, Dp = psi_{j+u} - psi_{j+2u} with u the
-// upwind side, d1 = psi_{j-u} the downwind neighbour, a = |C|, K = a(1 - a):
-//   MWB (Eq. 28)          a D + K h(D, Dp)
-//   Warming-Beam (Eq. 25) a D + K (D - Dp) / 2
-//   Lax-Wendroff          a D + K (Dd - D) / 2,   Dd = d1 - psi_j
-//   2nd-order upwind      a D + a (D - Dp) / 2   (forward Euler with Eq. 23)
-template <int SCH, class T>
-__device__ __forceinline__ T convect(T C, T f0, T u1, T u2, T d1) {
-  if (SCH == PCLB_SCHEME_MWB) return mwb_increment(C, f0, u1, u2);
-  const T a = C < T(0) ? -C : C, K = a - a * a;
-  const T D = f0 - u1, Dp = u1 - u2;
-  if (SCH == PCLB_SCHEME_WB) return a * D + T(0.5) * K * (D - Dp);
-  if (SCH == PCLB_SCHEME_UPWIND2) return a * D + T(0.5) * a * (D - Dp);
-  return a * D + T(0.5) * K * ((d1 - f0) - D);
-}
 
 }  // namespace pclb

@@ -45,7 +45,7 @@ constexpr int step_smem_bytes() {
   return kQ * kPlane * (int)sizeof(T) + kPairs64 * kTileT * 4 * (int)sizeof(T) + 128;
 }
 
-// Convection increment (upwind form, see convect in device_common.cuh) from
+// Convection increment (upwind form, see device_common.cuh) from
 // a = |C| and K = a (1 - a) given by the Courant table.
 // Limiter part of the MWB increment, h = |D| (D - Dp) / (|D| + |Dp|), 0 when
 // D = Dp = 0.  One Newton step on the reciprocal: h then carries a relative
