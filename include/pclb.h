@@ -193,6 +193,15 @@ pclb_status pclb_get_f(pclb_ctx* ctx, void* f);
  * device are reported by pclb_status_flags. */
 pclb_status pclb_step(pclb_ctx* ctx, int32_t n);
 
+/* The same n steps as pclb_step, launched as one CUDA graph: the first call
+ * for a given (n, current state buffer) captures the n launches on a private
+ * stream and instantiates the graph (cached per context, up to four, dropped
+ * by pclb_set_scheme and pclb_destroy); later calls replay it on the
+ * context's stream.  Results are bitwise those of pclb_step.  For grids
+ * small enough that launch overhead matters (no paper section: an execution
+ * detail). */
+pclb_status pclb_step_graph(pclb_ctx* ctx, int32_t n);
+
 /* Macroscopic fields of the current state (Eqs. 3-5): device,
  * [n_theta][n_r], context precision; any pointer may be NULL. */
 pclb_status pclb_moments(pclb_ctx* ctx, void* rho, void* u_r, void* u_theta, void* T);

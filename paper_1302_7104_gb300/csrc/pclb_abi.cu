@@ -350,6 +350,13 @@ pclb_status check_launch(pclb_ctx* ctx, cudaError_t e, const char* what) {
 // N_i = 16 or 24: the generic kernels
 bool generic(const pclb_ctx* c) { return c->dvm.n_dirs != kNDirs; }
 
+// Captured step graphs depend on the scheme and relaxation (kernel choice and
+// parameters): dropped when those change and when the context goes.
+void drop_graphs(pclb_ctx* ctx) {
+  for (int i = 0; i < ctx->n_graphs; ++i) cudaGraphExecDestroy(ctx->graphs[i].exec);
+  ctx->n_graphs = 0;
+}
+
 template <class T>
 pclb_status do_step(pclb_ctx* ctx, int n) {
   for (int i = 0; i < n; ++i) {
@@ -582,6 +589,8 @@ pclb_status pclb_destroy(pclb_ctx* ctx) {
   if (!ctx) return PCLB_OK;
   pclb_status st = bounded_sync(ctx, kDefaultTimeoutMs);
   if (st != PCLB_OK) std::snprintf(g_err, sizeof(g_err), "%s", ctx->err);
+  drop_graphs(ctx);
+  if (ctx->capture) cudaStreamDestroy(ctx->capture);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->side) cudaStreamDestroy(ctx->side);
@@ -655,6 +664,51 @@ pclb_status pclb_step(pclb_ctx* ctx, int32_t n) {
   if (n < 0) return fail(ctx, PCLB_EINVAL, "n = %d must be >= 0", n);
   if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
   return ctx->prec == PCLB_FP32 ? do_step<float>(ctx, n) : do_step<double>(ctx, n);
+}
+
+pclb_status pclb_step_graph(pclb_ctx* ctx, int32_t n) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (n < 0) return fail(ctx, PCLB_EINVAL, "n = %d must be >= 0", n);
+  if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
+  if (n == 0) return PCLB_OK;
+  const int cur = ctx->cur;
+  cudaGraphExec_t exec = nullptr;
+  for (int i = 0; i < ctx->n_graphs; ++i)
+    if (ctx->graphs[i].n == n && ctx->graphs[i].cur == cur) exec = ctx->graphs[i].exec;
+  if (!exec) {
+    // capture the n launches on a private stream (nothing runs), then keep
+    // the instantiated graph for this (n, starting buffer)
+    cudaError_t e = cudaSuccess;
+    if (!ctx->capture) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "capture stream");
+    cudaStream_t user = ctx->stream;
+    ctx->stream = ctx->capture;
+    e = cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeRelaxed);
+    pclb_status st = PCLB_OK;
+    if (e == cudaSuccess) st = ctx->prec == PCLB_FP32 ? do_step<float>(ctx, n) : do_step<double>(ctx, n);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e_end = e == cudaSuccess ? cudaStreamEndCapture(ctx->capture, &graph) : e;
+    ctx->stream = user;
+    ctx->cur = cur;
+    if (e != cudaSuccess || e_end != cudaSuccess || st != PCLB_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return st != PCLB_OK ? st : cuda_fail(ctx, e != cudaSuccess ? e : e_end, "step graph capture");
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "step graph instantiation");
+    if (ctx->n_graphs == 4) {   // drop the oldest
+      cudaGraphExecDestroy(ctx->graphs[0].exec);
+      for (int i = 1; i < 4; ++i) ctx->graphs[i - 1] = ctx->graphs[i];
+      ctx->n_graphs = 3;
+    }
+    ctx->graphs[ctx->n_graphs++] = {n, cur, exec};
+  }
+  cudaError_t e = cudaGraphLaunch(exec, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "step graph launch");
+  ctx->cur = (cur + n) & 1;
+  return PCLB_OK;
 }
 
 pclb_status pclb_moments(pclb_ctx* ctx, void* rho, void* u_r, void* u_theta, void* T) {
@@ -864,6 +918,7 @@ pclb_status pclb_set_scheme(pclb_ctx* ctx, int32_t scheme, int32_t relaxation) {
     return fail(ctx, PCLB_EINVAL, "relaxation = %d is unknown", relaxation);
   if (relaxation == PCLB_RELAX_EULER && ctx->dt > 2.0 * ctx->tau)
     return fail(ctx, PCLB_ECFL, "forward-Euler relaxation is unstable for dt / tau = %g > 2", ctx->dt / ctx->tau);
+  drop_graphs(ctx);
   ctx->scheme = scheme;
   ctx->relaxation = relaxation;
   ctx->sp.scheme = scheme;

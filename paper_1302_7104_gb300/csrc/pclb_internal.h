@@ -144,6 +144,12 @@ struct pclb_ctx {
   int32_t relaxation = 0;   // pclb_relaxation
   cudaStream_t stream;
   cudaStream_t side = nullptr;        // high-priority stream for the adjoint's wall work
+  cudaStream_t capture = nullptr;     // private stream for capturing step graphs
+  struct StepGraph {
+    int32_t n, cur;                   // steps and starting buffer of the captured sequence
+    cudaGraphExec_t exec;
+  } graphs[4] = {};
+  int32_t n_graphs = 0;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   unsigned char* ws;
   pclb::Layout lay;

@@ -67,6 +67,7 @@ _SIGS = {
     "pclb_set_f": (ctypes.c_int, [_vp, _vp]),
     "pclb_get_f": (ctypes.c_int, [_vp, _vp]),
     "pclb_step": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "pclb_step_graph": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "pclb_moments": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "pclb_noneq": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
     "pclb_set_scheme": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
@@ -237,6 +238,12 @@ class PCLB:
 
     def step(self, n: int = 1):
         _check(lib().pclb_step(self.ctx, int(n)), self.ctx)
+        return self
+
+    def step_graph(self, n: int = 1):
+        """The same n steps as ``step``, launched as one CUDA graph (captured on
+        first use for this n and state buffer, replayed afterwards)."""
+        _check(lib().pclb_step_graph(self.ctx, int(n)), self.ctx)
         return self
 
     def moments(self, out: Optional[Sequence] = None):
