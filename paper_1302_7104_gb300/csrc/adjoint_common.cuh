@@ -42,6 +42,25 @@ __device__ __forceinline__ void mwb_partials(T a, T K, T D, T Dp, T& MD, T& MDp)
   MD = fma(K, fma(br, fma(-s, br, ar), ar), a);   // a + K (ar + br (ar - s br))
   MDp = -(T(1) + s) * (Ka * ar);
 }
+// FP64: the same, with the zero tests and the sign of D Dp taken on the bit
+// patterns by integer instructions (GB300 runs FP64 arithmetic at 1/64 of the
+// FP32 rate; integer compares keep it free for the products).
+template <>
+__device__ __forceinline__ void mwb_partials<double>(double a, double K, double D, double Dp, double& MD,
+                                                     double& MDp) {
+  const long long bD = __double_as_longlong(D), bP = __double_as_longlong(Dp);
+  const double aD = fabs(D), aP = fabs(Dp), n = aD + aP;
+  // n >= 2^-1022 (n is non-negative: its high word orders like the value)
+  const double rn = __double2hiint(n) >= 0x00100000 ? recip_fast(n) : 0.0;
+  const double ar = aD * rn, br = aP * rn;
+  // |D| > 0 and |Dp| > 0: a nonzero magnitude (sign bit cleared); the sign of
+  // D Dp from the sign bits
+  const bool nz = ((bD & 0x7fffffffffffffffll) != 0) && ((bP & 0x7fffffffffffffffll) != 0);
+  const double s = nz ? ((bD ^ bP) < 0 ? -1.0 : 1.0) : 0.0;
+  const double Ka = K * ar;
+  MD = fma(K, fma(br, fma(-s, br, ar), ar), a);   // a + K (ar + br (ar - s br))
+  MDp = -(1.0 + s) * (Ka * ar);
+}
 
 // The terms of one pair of opposite velocities (v, -v) of a shell in the sums
 // of eq_cotangent below, added to Ak, Bxk, Byk, Ck, Dk; lp, lm: the
