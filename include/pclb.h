@@ -232,6 +232,15 @@ pclb_status pclb_set_scheme(pclb_ctx* ctx, int32_t scheme, int32_t relaxation);
 #define PCLB_NEQ_DSTAR 8  /* Delta*_m = M*_m(f - f^eq) */
 pclb_status pclb_noneq(pclb_ctx* ctx, int32_t groups, void* out);
 
+/* Arithmetic throughput of the current GPU, measured (no paper counterpart:
+ * the reference for the rooflines of the ALU-bound kernels).  out: host,
+ * 2 doubles: [0] packed FP32x2 fused multiply-add rate, [1] FP64 fused
+ * multiply-add rate, both in TFLOP/s (2 flops per multiply-add), from
+ * independent multiply-add chains on every SM.  Runs on `stream` (a
+ * cudaStream_t; NULL for the default stream) and synchronizes it; allocates
+ * nothing.  PCLB_ECUDA on a CUDA error. */
+pclb_status pclb_alu_peaks(void* stream, double* out);
+
 /* Global integrals of the current state with the area element r dr dtheta,
  * summed in double: out[0] mass, out[1] x-momentum, out[2] y-momentum,
  * out[3] total energy (rho (E + u^2/2)), out[4] min rho, out[5] min T,

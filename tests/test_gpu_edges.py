@@ -113,3 +113,12 @@ def test_forward_and_adjoint_interleave_on_the_stream():
     a_f, a_l = run(False)
     b_f, b_l = run(True)
     assert torch.equal(a_f, b_f) and torch.equal(a_l, b_l)
+
+
+def test_alu_peaks_are_plausible():
+    """pclb_alu_peaks: packed FP32 and FP64 multiply-add rates within a factor
+    of a few of GB300's nominal rates (152 SMs at up to 2.07 GHz: 80 and
+    1.26 TFLOP/s)."""
+    pk = P.alu_peaks()
+    assert 20.0 < pk["ffma2_tflops"] < 120.0
+    assert 0.3 < pk["dfma_tflops"] < 3.0
