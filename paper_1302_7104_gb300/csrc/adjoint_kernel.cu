@@ -637,13 +637,11 @@ template <class T>
 cudaError_t launch_adjoint(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, const T* f, const T* lam_in,
                            T* lam_out, const AdjScratch& ws, const StepParams& p, const DvmConst<T>& d,
                            cudaStream_t stream, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
-  static bool configured = false;
+  static std::atomic<unsigned long long> configured{0};
   constexpr int smem = AdjSize<T>::smem;
-  if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(adjoint_pair_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  {
+    const cudaError_t e = set_smem_once(adjoint_pair_kernel<T>, smem, configured);
     if (e != cudaSuccess) return e;
-    configured = true;
   }
   EqParams<T>* ghost = reinterpret_cast<EqParams<T>*>(ws.ghost);
   T* gwall = reinterpret_cast<T*>(ws.gwall);

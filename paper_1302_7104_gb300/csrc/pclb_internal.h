@@ -2,6 +2,7 @@
 // Not part of the public interface (include/pclb.h).
 #pragma once
 
+#include <atomic>
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -117,6 +118,21 @@ struct AdjScratch {
   unsigned char* ghost;       // [side][layer][n_theta] EqParams of the radial ghost layers
   unsigned char* gwall;       // [side][node][n_theta][4] cotangent the ghosts return
 };
+// Raises kernel fn's dynamic shared-memory limit to `bytes` once per device
+// (the attribute belongs to each device's context); `done` holds one bit per
+// device ordinal.
+template <class F>
+inline cudaError_t set_smem_once(F* fn, int bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
+
 size_t adjoint_scratch_bytes(int n_theta, int elem);
 AdjScratch adjoint_scratch(unsigned char* base, int n_theta, int elem);
 

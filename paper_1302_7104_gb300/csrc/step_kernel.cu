@@ -225,12 +225,11 @@ __global__ void __launch_bounds__(kThreads64, 1)
 template <class T, int SCH>
 static cudaError_t launch_scheme(const CUtensorMap* tmap_in, T* f_out, const StepParams& p, const DvmConst<T>& d,
                                  cudaStream_t stream) {
-  static bool configured = false;   // one-time attribute set per instantiation
+  static std::atomic<unsigned long long> configured{0};   // per instantiation and device
   const int smem = step_smem_bytes<T>();
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<T, SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  {
+    const cudaError_t e = set_smem_once(step_kernel<T, SCH>, smem, configured);
     if (e != cudaSuccess) return e;
-    configured = true;
   }
   dim3 grid((p.n_r + kTileR - 1) / kTileR, (p.n_theta + kTileT - 1) / kTileT);
   step_kernel<T, SCH><<<grid, kThreads64, smem, stream>>>(*tmap_in, f_out, p, d);

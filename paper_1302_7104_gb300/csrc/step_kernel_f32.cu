@@ -435,12 +435,10 @@ __global__ void __launch_bounds__(kStepThreads32, kCtasPerSm32)
 template <int SCH>
 static cudaError_t launch_scheme_f32(const CUtensorMap* tmap_in, float* f_out, const StepParams& p,
                                      const DvmConst<float>& d, cudaStream_t stream) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(step_kernel_f32<SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemF32);
+  static std::atomic<unsigned long long> configured{0};   // per instantiation and device
+  {
+    const cudaError_t e = set_smem_once(step_kernel_f32<SCH>, kSmemF32, configured);
     if (e != cudaSuccess) return e;
-    configured = true;
   }
   dim3 grid((p.n_r + kTileR - 1) / kTileR, (p.n_theta + kTileT32 - 1) / kTileT32);
   step_kernel_f32<SCH><<<grid, kStepThreads32, kSmemF32, stream>>>(*tmap_in, f_out, p, d);
