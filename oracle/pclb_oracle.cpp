@@ -28,7 +28,7 @@
 //     plain definition: forward-mode derivatives column by column, each
 //     dotted with the cotangent.
 //
-// Readings where the paper is silent (each is also listed in the design notes):
+// Readings where the paper is silent:
 //   * velocity labels are fixed in Cartesian space: v_r = v.e_r(theta),
 //     v_theta = v.e_theta(theta) at the node being updated;
 //   * delta == 0 in Eq. (28): eta is undefined, the bracket times delta is
