@@ -71,7 +71,7 @@ typedef enum {
   PCLB_ETIMEOUT = 5,     /* a bounded wait for the stream (or a device-side wait) ran out */
   PCLB_ECFL = 6,         /* max over velocities and nodes of |C_r| + |C_theta| exceeds 1 */
   PCLB_ESTATE = 7,       /* call out of order, e.g. pclb_step before any state was set */
-  PCLB_EUNSUPPORTED = 8  /* configuration this build does not implement (e.g. n_dirs not 8, 16, 24) */
+  PCLB_EUNSUPPORTED = 8  /* configuration the library does not implement (e.g. n_dirs not 8, 16, 24) */
 } pclb_status;
 
 typedef enum { PCLB_FP32 = 0, PCLB_FP64 = 1 } pclb_precision;

@@ -102,7 +102,7 @@ pclb_status validate_problem(const pclb_grid* g, const pclb_dvm* d, pclb_precisi
   if (!(g->r_in > 0.0) || !(g->r_out > g->r_in) || !std::isfinite(g->r_out))
     return fail(nullptr, PCLB_EINVAL, "need 0 < r_in < r_out (got %g, %g)", g->r_in, g->r_out);
   if (d->n_dirs != kNDirs && d->n_dirs != 16 && d->n_dirs != 24)
-    return fail(nullptr, PCLB_EUNSUPPORTED, "n_dirs = %d; this build implements 8, 16 and 24 directions", d->n_dirs);
+    return fail(nullptr, PCLB_EUNSUPPORTED, "n_dirs = %d; the library implements 8, 16 and 24 directions", d->n_dirs);
   if (g->n_f < 1 || g->n_f > d->n_dirs)
     return fail(nullptr, PCLB_EINVAL, "n_f = %d must be in [1, n_dirs]", g->n_f);
   if (d->speeds[0] != 0.0) return fail(nullptr, PCLB_EINVAL, "speeds[0] must be 0 (rest velocity)");
@@ -281,7 +281,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
 // with a box of kWinR columns by box_rows rows and one label.
 pclb_status encode_map(pclb_ctx* ctx, const void* base, int box_rows, CUtensorMap* out) {
   auto enc = get_encode_fn();
-  if (!enc) return fail(ctx, PCLB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (!enc) return fail(ctx, PCLB_ECUDA, "cuTensorMapEncodeTiled is not available from the CUDA driver");
   if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return fail(ctx, PCLB_EINVAL, "state buffer not 16-byte aligned");
   const size_t es = elem_size(ctx->prec);
   cuuint64_t dims[3] = {(cuuint64_t)ctx->grid.n_r, (cuuint64_t)ctx->sp.rows, (cuuint64_t)kQ};

@@ -3,7 +3,7 @@ annulus, N_r x N_theta = 4096 x 4096, 33 velocities, through the same C ABI
 call and launch configuration the benchmark times (one fused step launch over
 the whole grid).
 
-The oracle cannot step 16.8 M nodes in a test's time budget as a whole-grid
+The oracle cannot step 16.8 M nodes within a test's running time as a whole-grid
 reference in FP64 per case, so the comparison is on sampled outputs, each of
 which the oracle computes by itself: every node next to a wall, every node of
 the azimuthal seam rows, nodes on tile edges and random interior nodes
