@@ -291,6 +291,14 @@ pclb_status pclb_state_bytes(pclb_ctx* ctx, size_t* bytes);
 pclb_status pclb_save_state(pclb_ctx* ctx, void* state);
 pclb_status pclb_load_state(pclb_ctx* ctx, const void* state);
 
+/* One step of Eq. (38) from the state in f_from to f_to, both buffers of
+ * pclb_state_bytes bytes in the layout pclb_save_state writes (device,
+ * 16-byte aligned, distinct); the context's own state is left alone.  Lets a
+ * backward pass recompute a segment's states straight into the buffers the
+ * adjoint steps read.  Asynchronous, one kernel launch (two for n_dirs 16,
+ * 24). */
+pclb_status pclb_step_states(pclb_ctx* ctx, const void* f_from, void* f_to);
+
 /* Set / read the adjoint variable: device, [Q][n_theta][n_r], context
  * precision. */
 pclb_status pclb_lambda_set(pclb_ctx* ctx, const void* lam);

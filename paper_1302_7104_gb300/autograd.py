@@ -6,7 +6,8 @@ fields (Eq. 10), advances ``n_steps`` steps of Eq. (38) and returns the fields
 with respect to the initial fields: the backward pass runs the library's
 adjoint step (pclb_adjoint_state) in reverse with sqrt(N) checkpointing --
 checkpoints every ``segment`` steps on the forward pass, each segment's states
-recomputed on the backward pass -- and ends with the adjoint of the
+recomputed on the backward pass straight into the buffers the adjoint steps
+read (pclb_step_states) -- and ends with the adjoint of the
 equilibrium initialisation (pclb_set_state_vjp).  Checkpoints can live in
 device memory or in page-locked host memory (``offload="host"``), which lets
 the 2.2 GB states of a 4096 x 4096 run use the host's memory.
@@ -71,15 +72,15 @@ class _Rollout(torch.autograd.Function):
         starts = list(range(0, ctx.n, ctx.seg))
         for si in reversed(range(len(starts))):
             k = min(ctx.seg, ctx.n - starts[si])
-            sim.load_state(_restore(ctx.ckpts[si], sim.device))
-            while len(pool) < k:
+            first = _restore(ctx.ckpts[si], sim.device)  # f at the segment start
+            while len(pool) < k - 1:
                 pool.append(sim.new_state())
-            sim.save_state(pool[0])                      # f at the segment start
-            for j in range(1, k):
-                sim.step(1)
-                sim.save_state(pool[j])
+            states = [first] + pool[:k - 1]
+            for j in range(1, k):                        # recompute the segment in place
+                sim.step_states(states[j - 1], states[j])
             for j in reversed(range(k)):
-                sim.adjoint_state(pool[j])               # lam <- J(f_j)^T lam
+                sim.adjoint_state(states[j])             # lam <- J(f_j)^T lam
+            sim.sync()                                   # the segment's buffers are reused next
         grads = sim.set_state_vjp(rho.detach(), u_r.detach(), u_t.detach(), T.detach())
         ctx.ckpts = None
         return (*grads, None, None, None, None)

@@ -666,6 +666,31 @@ pclb_status pclb_step(pclb_ctx* ctx, int32_t n) {
   return ctx->prec == PCLB_FP32 ? do_step<float>(ctx, n) : do_step<double>(ctx, n);
 }
 
+pclb_status pclb_step_states(pclb_ctx* ctx, const void* f_from, void* f_to) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (!f_from || !f_to) return fail(ctx, PCLB_EINVAL, "f_from and f_to must not be NULL");
+  if (f_from == f_to) return fail(ctx, PCLB_EINVAL, "f_from and f_to must be different buffers");
+  if ((reinterpret_cast<uintptr_t>(f_from) | reinterpret_cast<uintptr_t>(f_to)) % 16 != 0)
+    return fail(ctx, PCLB_EINVAL, "state buffers must be 16-byte aligned");
+  cudaError_t e;
+  if (generic(ctx)) {
+    e = ctx->prec == PCLB_FP32
+            ? gen_launch_step<float>((const float*)f_from, (float*)f_to,
+                                     reinterpret_cast<float*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg,
+                                     ctx->stream)
+            : gen_launch_step<double>((const double*)f_from, (double*)f_to,
+                                      reinterpret_cast<double*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg,
+                                      ctx->stream);
+  } else {
+    CUtensorMap map;
+    pclb_status st = encode_map(ctx, f_from, ctx->prec == PCLB_FP32 ? kTileT32 + 4 : kWinT, &map);
+    if (st != PCLB_OK) return st;
+    e = ctx->prec == PCLB_FP32 ? launch_step_f32(&map, (float*)f_to, ctx->sp, ctx->dvm32, ctx->stream)
+                               : launch_step<double>(&map, (double*)f_to, ctx->sp, ctx->dvm64, ctx->stream);
+  }
+  return e == cudaSuccess ? PCLB_OK : cuda_fail(ctx, e, "step kernel launch");
+}
+
 pclb_status pclb_step_graph(pclb_ctx* ctx, int32_t n) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
   if (n < 0) return fail(ctx, PCLB_EINVAL, "n = %d must be >= 0", n);

@@ -68,6 +68,7 @@ _SIGS = {
     "pclb_get_f": (ctypes.c_int, [_vp, _vp]),
     "pclb_step": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "pclb_step_graph": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "pclb_step_states": (ctypes.c_int, [_vp, _vp, _vp]),
     "pclb_alu_peaks": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "pclb_moments": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "pclb_noneq": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
@@ -239,6 +240,14 @@ class PCLB:
 
     def step(self, n: int = 1):
         _check(lib().pclb_step(self.ctx, int(n)), self.ctx)
+        return self
+
+    def step_states(self, f_from, f_to):
+        """One step from the saved state ``f_from`` into the buffer ``f_to``
+        (both from ``new_state``/``save_state``); the context's state is left
+        alone."""
+        _check(lib().pclb_step_states(self.ctx, _vp(f_from.data_ptr()), _vp(f_to.data_ptr())), self.ctx)
+        self._hold = (f_from, f_to)
         return self
 
     def step_graph(self, n: int = 1):

@@ -122,3 +122,20 @@ def test_alu_peaks_are_plausible():
     pk = P.alu_peaks()
     assert 20.0 < pk["ffma2_tflops"] < 120.0
     assert 0.3 < pk["dfma_tflops"] < 3.0
+
+
+@pytest.mark.parametrize("prec,n_dirs", [("fp32", 8), ("fp64", 8), ("fp64", 16)])
+def test_step_states_equals_step(prec, n_dirs):
+    """pclb_step_states: one step between saved-state buffers equals pclb_step
+    bit for bit and leaves the context's own state alone."""
+    w = I.random_smooth(45, 21, seed=36, n_dirs=n_dirs, n_f=n_dirs, bc_kind=(I.BC_WALL, I.BC_EXTRAP))
+    dtype = torch.float32 if prec == "fp32" else torch.float64
+    with P.PCLB(w, precision=prec) as g:
+        g.set_f(torch.as_tensor(_noisy(w), dtype=dtype, device="cuda"))
+        s0 = g.save_state()
+        s1, s2 = g.new_state(), g.new_state()
+        g.step_states(s0, s1).step_states(s1, s2)
+        assert torch.equal(g.save_state(), s0)          # the context's state is untouched
+        want = g.step(2).get_f()
+        got = g.load_state(s2).get_f()                  # the nodes (buffer padding is not state)
+        assert torch.equal(got, want)
