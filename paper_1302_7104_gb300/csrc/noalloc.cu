@@ -177,6 +177,10 @@ extern "C" pclb_status pclb_diagnostics_noalloc(const pclb_grid* grid, const pcl
     set_thread_error("f and out must not be NULL");
     return PCLB_EINVAL;
   }
+  if (reinterpret_cast<uintptr_t>(f) % (prec == PCLB_FP32 ? 4 : 8) != 0) {
+    set_thread_error("f must be aligned to the element size");
+    return PCLB_EINVAL;
+  }
   if (grid->n_theta > kNoAllocMaxRows) {
     std::snprintf(err, sizeof(err),
                   "n_theta = %d exceeds the %d azimuthal rows the static scratch of "

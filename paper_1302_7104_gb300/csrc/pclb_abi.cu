@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/pclb.h: argument validation,
 // workspace layout, host-computed tables, TMA descriptors, launches, bounded
 // waits and error reporting.
+#include <initializer_list>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -347,6 +348,19 @@ pclb_status check_launch(pclb_ctx* ctx, cudaError_t e, const char* what) {
   return e == cudaSuccess ? PCLB_OK : cuda_fail(ctx, e, what);
 }
 
+// Caller pointers that kernels dereference element by element must be aligned
+// to the element size (a misaligned one would fault on the device): refused
+// here with PCLB_EINVAL.
+bool misaligned(const pclb_ctx* c, std::initializer_list<const void*> ptrs) {
+  const uintptr_t a = c->prec == PCLB_FP32 ? 4 : 8;
+  for (const void* p : ptrs)
+    if (p && reinterpret_cast<uintptr_t>(p) % a != 0) return true;
+  return false;
+}
+pclb_status misaligned_fail(pclb_ctx* c) {
+  return fail(c, PCLB_EINVAL, "pointers must be aligned to the element size (%d bytes)", c->prec == PCLB_FP32 ? 4 : 8);
+}
+
 // N_i = 16 or 24: the generic kernels
 bool generic(const pclb_ctx* c) { return c->dvm.n_dirs != kNDirs; }
 
@@ -607,6 +621,7 @@ pclb_status pclb_set_stream(pclb_ctx* ctx, void* stream) {
 pclb_status pclb_set_state(pclb_ctx* ctx, const void* rho, const void* u_r, const void* u_theta,
                            const void* T) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (misaligned(ctx, {rho, u_r, u_theta, T})) return misaligned_fail(ctx);
   if (!rho || !u_r || !u_theta || !T) return fail(ctx, PCLB_EINVAL, "field pointers must not be NULL");
   cudaError_t e;
   if (generic(ctx) && ctx->prec == PCLB_FP32)
@@ -628,6 +643,7 @@ pclb_status pclb_set_state(pclb_ctx* ctx, const void* rho, const void* u_r, cons
 
 pclb_status pclb_set_f(pclb_ctx* ctx, const void* f) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (misaligned(ctx, {f})) return misaligned_fail(ctx);
   if (!f) return fail(ctx, PCLB_EINVAL, "f must not be NULL");
   cudaError_t e;
   if (generic(ctx))
@@ -645,6 +661,7 @@ pclb_status pclb_set_f(pclb_ctx* ctx, const void* f) {
 
 pclb_status pclb_get_f(pclb_ctx* ctx, void* f) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (misaligned(ctx, {f})) return misaligned_fail(ctx);
   if (!f) return fail(ctx, PCLB_EINVAL, "f must not be NULL");
   if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
   cudaError_t e;
@@ -738,6 +755,7 @@ pclb_status pclb_step_graph(pclb_ctx* ctx, int32_t n) {
 
 pclb_status pclb_moments(pclb_ctx* ctx, void* rho, void* u_r, void* u_theta, void* T) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (misaligned(ctx, {rho, u_r, u_theta, T})) return misaligned_fail(ctx);
   if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
   if (!rho && !u_r && !u_theta && !T) return PCLB_OK;
   cudaError_t e;
@@ -758,6 +776,7 @@ pclb_status pclb_moments(pclb_ctx* ctx, void* rho, void* u_r, void* u_theta, voi
 
 pclb_status pclb_noneq(pclb_ctx* ctx, int32_t groups, void* out) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (misaligned(ctx, {out})) return misaligned_fail(ctx);
   if (generic(ctx)) return fail(ctx, PCLB_EUNSUPPORTED, "pclb_noneq implements n_dirs = 8 only");
   if (groups < 1 || groups > 15) return fail(ctx, PCLB_EINVAL, "groups = %d must be in 1..15", (int)groups);
   if (!out) return fail(ctx, PCLB_EINVAL, "out must not be NULL");
@@ -839,7 +858,7 @@ pclb_status pclb_run_host(pclb_ctx* ctx, const void* rho, const void* u_r, const
       if (cudaPointerGetAttributes(&a, ptrs[i]) != cudaSuccess) {
         cudaGetLastError();
         direct = false;
-      } else if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) {
+      } else if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr || misaligned(ctx, {a.devicePointer})) {
         direct = false;
       } else {
         mapped[i] = a.devicePointer;
@@ -902,6 +921,7 @@ pclb_status pclb_load_state(pclb_ctx* ctx, const void* state) {
 
 pclb_status pclb_lambda_set(pclb_ctx* ctx, const void* lam) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (misaligned(ctx, {lam})) return misaligned_fail(ctx);
   if (generic(ctx)) return fail(ctx, PCLB_EUNSUPPORTED, "reverse mode implements n_dirs = 8 only");
   if (!lam) return fail(ctx, PCLB_EINVAL, "lam must not be NULL");
   void* dst = ctx->ws + ctx->lay.lam[ctx->cur_lam];
@@ -915,6 +935,7 @@ pclb_status pclb_lambda_set(pclb_ctx* ctx, const void* lam) {
 
 pclb_status pclb_lambda_get(pclb_ctx* ctx, void* lam) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (misaligned(ctx, {lam})) return misaligned_fail(ctx);
   if (generic(ctx)) return fail(ctx, PCLB_EUNSUPPORTED, "reverse mode implements n_dirs = 8 only");
   if (!lam) return fail(ctx, PCLB_EINVAL, "lam must not be NULL");
   if (!ctx->has_lam) return fail(ctx, PCLB_ESTATE, "no adjoint variable: call pclb_lambda_set or pclb_moments_vjp");
@@ -953,6 +974,8 @@ pclb_status pclb_set_scheme(pclb_ctx* ctx, int32_t scheme, int32_t relaxation) {
 
 pclb_status pclb_adjoint_state(pclb_ctx* ctx, const void* f_state) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (f_state && reinterpret_cast<uintptr_t>(f_state) % 16 != 0)
+    return fail(ctx, PCLB_EINVAL, "f_state must be 16-byte aligned");
   if (adjoint_supported(ctx) != PCLB_OK) return PCLB_EUNSUPPORTED;
   if (!ctx->has_lam) return fail(ctx, PCLB_ESTATE, "no adjoint variable: call pclb_lambda_set or pclb_moments_vjp");
   const CUtensorMap* map;
@@ -972,6 +995,7 @@ pclb_status pclb_adjoint_state(pclb_ctx* ctx, const void* f_state) {
 
 pclb_status pclb_adjoint_step(pclb_ctx* ctx, const void* f_n, const void* lam_np1, void* lam_n) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (misaligned(ctx, {f_n, lam_np1, lam_n})) return misaligned_fail(ctx);
   if (adjoint_supported(ctx) != PCLB_OK) return PCLB_EUNSUPPORTED;
   if (!f_n || !lam_np1 || !lam_n) return fail(ctx, PCLB_EINVAL, "f_n, lam_np1 and lam_n must not be NULL");
   void* adj = ctx->ws + ctx->lay.adj_f;
@@ -989,6 +1013,7 @@ pclb_status pclb_adjoint_step(pclb_ctx* ctx, const void* f_n, const void* lam_np
 
 pclb_status pclb_moments_vjp(pclb_ctx* ctx, const void* g_rho, const void* g_ur, const void* g_ut, const void* g_T) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (misaligned(ctx, {g_rho, g_ur, g_ut, g_T})) return misaligned_fail(ctx);
   if (generic(ctx)) return fail(ctx, PCLB_EUNSUPPORTED, "reverse mode implements n_dirs = 8 only");
   if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
   void* lam = ctx->ws + ctx->lay.lam[ctx->cur_lam];
@@ -1009,6 +1034,7 @@ pclb_status pclb_moments_vjp(pclb_ctx* ctx, const void* g_rho, const void* g_ur,
 pclb_status pclb_set_state_vjp(pclb_ctx* ctx, const void* rho, const void* u_r, const void* u_theta, const void* T,
                                void* g_rho, void* g_ur, void* g_ut, void* g_T) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (misaligned(ctx, {rho, u_r, u_theta, T, g_rho, g_ur, g_ut, g_T})) return misaligned_fail(ctx);
   if (generic(ctx)) return fail(ctx, PCLB_EUNSUPPORTED, "reverse mode implements n_dirs = 8 only");
   if (!rho || !u_r || !u_theta || !T) return fail(ctx, PCLB_EINVAL, "field pointers must not be NULL");
   if (!ctx->has_lam) return fail(ctx, PCLB_ESTATE, "no adjoint variable: call pclb_lambda_set first");

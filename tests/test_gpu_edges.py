@@ -139,3 +139,23 @@ def test_step_states_equals_step(prec, n_dirs):
         want = g.step(2).get_f()
         got = g.load_state(s2).get_f()                  # the nodes (buffer padding is not state)
         assert torch.equal(got, want)
+
+
+def test_misaligned_pointers_are_refused_before_any_launch():
+    """Pointers the kernels would read or write element by element must be
+    aligned to the element size: a misaligned one is refused on the host
+    (PCLB_EINVAL) and nothing is launched."""
+    import ctypes
+    w = I.random_smooth(20, 12, seed=37)
+    with P.PCLB(w, precision="fp32") as g:
+        g.set_state()
+        buf = torch.zeros(4 * w.n_theta * w.n_r + 4, dtype=torch.float32, device="cuda")
+        bad = ctypes.c_void_p(buf.data_ptr() + 2)
+        ok = ctypes.c_void_p(buf.data_ptr())
+        assert P.lib().pclb_set_state(g.ctx, bad, ok, ok, ok) == 1
+        assert P.lib().pclb_moments(g.ctx, bad, None, None, None) == 1
+        f = torch.zeros(w.q * w.n_theta * w.n_r + 4, dtype=torch.float32, device="cuda")
+        assert P.lib().pclb_get_f(g.ctx, ctypes.c_void_p(f.data_ptr() + 2)) == 1
+        st = g.new_state()
+        assert P.lib().pclb_adjoint_state(g.ctx, ctypes.c_void_p(st.data_ptr() + 8)) in (1, 8)
+        assert g.status_flags() == 0
