@@ -261,12 +261,18 @@ pclb_status pclb_sync(pclb_ctx* ctx, int32_t timeout_ms);
 /* End-to-end call with host buffers: bring rho, u_r, u_theta, T (host,
  * [n_theta][n_r], context precision) to the device, set f = f^eq, advance n
  * steps, compute the moments and bring them back to the host arrays
- * out_rho .. out_T (any may be NULL).  When every buffer is page-locked
- * (cudaHostAlloc / cudaHostRegister, e.g. torch's pin_memory) the set-state
- * and moment kernels read and write them through their device mapping, so the
- * transfers overlap the kernels; otherwise the fields are staged through the
- * workspace tail (pclb_workspace_size reserves it) with stream-ordered copies.
- * The call returns after the results are on the host (bounded wait). */
+ * out_rho .. out_T (any may be NULL).  The fields pass through the workspace
+ * tail (pclb_workspace_size reserves it).  When every buffer is page-locked
+ * (cudaHostAlloc / cudaHostRegister, e.g. torch's pin_memory) and n_dirs = 8,
+ * the grid is processed in azimuthal slabs of whole tile rows: each slab's
+ * copies run on the copy engines (streams of the context's own) while the
+ * set-state, step and moment kernels of other slabs run, the first and the
+ * last step slab by slab and the steps in between on the whole grid; the
+ * results are bit for bit those of the plain sequence.  Otherwise the copies
+ * and kernels run one after another on the context's stream.  Either way an
+ * output array may be an input array (input rows are read before the same
+ * output rows are written).  The call returns after the results are on the
+ * host (bounded wait). */
 pclb_status pclb_run_host(pclb_ctx* ctx, const void* rho, const void* u_r, const void* u_theta,
                           const void* T, int32_t n, void* out_rho, void* out_u_r,
                           void* out_u_theta, void* out_T);

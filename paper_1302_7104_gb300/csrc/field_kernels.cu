@@ -26,9 +26,10 @@ __device__ __forceinline__ void store_with_ghosts(T* f, const StepParams& p, con
 template <class T>
 __global__ void set_state_kernel(T* __restrict__ f, const T* __restrict__ rho, const T* __restrict__ u_r,
                                  const T* __restrict__ u_t, const T* __restrict__ temp,
-                                 const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
+                                 const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d,
+                                 int t_begin) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  const int t = blockIdx.y;
+  const int t = blockIdx.y + t_begin;
   if (r >= p.n_r || t >= p.n_theta) return;
   const size_t n = (size_t)t * p.n_r + r;
   const T c = (T)p.cos_t[t], s = (T)p.sin_t[t];
@@ -50,18 +51,21 @@ __global__ void set_state_kernel(T* __restrict__ f, const T* __restrict__ rho, c
 __global__ void set_state_f32_kernel(float* __restrict__ f, const float* __restrict__ rho,
                                      const float* __restrict__ u_r, const float* __restrict__ u_t,
                                      const float* __restrict__ temp, const __grid_constant__ StepParams p,
-                                     const __grid_constant__ DvmConst<float> d) {
+                                     const __grid_constant__ DvmConst<float> d, int t_begin) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  const int t = blockIdx.y;
+  const int t = blockIdx.y + t_begin;
   if (r >= p.n_r || t >= p.n_theta) return;
   const size_t n = (size_t)t * p.n_r + r;
-  const double c = p.cos_t[t], s = p.sin_t[t];
-  const double ur = u_r[n], ut = u_t[n];
+  // the rotation to Cartesian components in float-float (GB300 runs FP64 at
+  // 1/64 of the FP32 rate, and double arithmetic here would bound the kernel)
+  const float4 cs = p.cs_ff[t];
+  const ff c{cs.x, cs.y}, s{cs.z, cs.w};
+  const ff ur = ff_of(u_r[n]), ut = ff_of(u_t[n]);
   State32 st;
   st.rho = ff_of(rho[n]);
   st.E = ff_of(temp[n]);                      // E = T for gamma = 2
-  st.ux = ff_from(ur * c - ut * s);
-  st.uy = ff_from(ur * s + ut * c);
+  st.ux = ff_add(ff_mul(ur, c), ff_neg(ff_mul(ut, s)));
+  st.uy = ff_add(ff_mul(ur, s), ff_mul(ut, c));
   if (!(rho[n] > 0.f && temp[n] > 0.f)) atomicOr(p.status, PCLB_FLAG_NONPHYS);
   const Eq32 e = eq32(st, d);
   store_with_ghosts<float>(f, p, d, 0, t, r, feq32(e, d, 0, 0, 1.f));
@@ -76,26 +80,29 @@ __global__ void set_state_f32_kernel(float* __restrict__ f, const float* __restr
 }
 
 __global__ void moments_f32_kernel(const float* __restrict__ f, float* rho, float* u_r, float* u_t,
-                                   float* temp, const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<float> d) {
+                                   float* temp, const __grid_constant__ StepParams p,
+                                   const __grid_constant__ DvmConst<float> d, int t_begin) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  const int t = blockIdx.y;
+  const int t = blockIdx.y + t_begin;
   if (r >= p.n_r || t >= p.n_theta) return;
   const size_t plane = (size_t)p.rows * p.pitch;
   const State32 m = state32(f + (size_t)(t + kGhostRows) * p.pitch + r, plane, d);
   const size_t n = (size_t)t * p.n_r + r;
-  const double c = p.cos_t[t], s = p.sin_t[t];
-  const double ux = (double)m.ux.hi + (double)m.ux.lo, uy = (double)m.uy.hi + (double)m.uy.lo;
+  // polar components in float-float, rounded once (no FP64 arithmetic)
+  const float4 cs = p.cs_ff[t];
+  const ff c{cs.x, cs.y}, s{cs.z, cs.w};
   if (rho) rho[n] = m.rho.hi + m.rho.lo;
-  if (u_r) u_r[n] = (float)(ux * c + uy * s);
-  if (u_t) u_t[n] = (float)(uy * c - ux * s);
+  if (u_r) u_r[n] = ff_add(ff_mul(m.ux, c), ff_mul(m.uy, s)).hi;
+  if (u_t) u_t[n] = ff_add(ff_mul(m.uy, c), ff_neg(ff_mul(m.ux, s))).hi;
   if (temp) temp[n] = m.E.hi + m.E.lo;
 }
 
 template <class T>
 __global__ void moments_kernel(const T* __restrict__ f, T* rho, T* u_r, T* u_t, T* temp,
-                               const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
+                               const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d,
+                               int t_begin) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  const int t = blockIdx.y;
+  const int t = blockIdx.y + t_begin;
   if (r >= p.n_r || t >= p.n_theta) return;
   const size_t plane = (size_t)p.rows * p.pitch;
   const NodeState<T> m = node_moments(f + (size_t)(t + kGhostRows) * p.pitch + r, plane, d);
@@ -185,25 +192,31 @@ __global__ void diag_final_kernel(const double* partials, int n_blocks, double* 
 // ---------------------------------------------------------------------------
 constexpr int kRowThreads = 128;
 
+// Rows [t_begin, t_end) of the grid (t_end < 0: to the last row); the field
+// arrays are always indexed with the full [n_theta][n_r] layout.
 template <class T>
 cudaError_t launch_set_state(T* f, const T* rho, const T* ur, const T* ut, const T* temp,
-                             const StepParams& p, const DvmConst<T>& d, cudaStream_t s) {
-  dim3 grid((p.n_r + kRowThreads - 1) / kRowThreads, p.n_theta);
+                             const StepParams& p, const DvmConst<T>& d, cudaStream_t s, int t_begin, int t_end) {
+  if (t_end < 0) t_end = p.n_theta;
+  if (t_begin < 0 || t_end <= t_begin) return cudaSuccess;
+  dim3 grid((p.n_r + kRowThreads - 1) / kRowThreads, t_end - t_begin);
   if constexpr (sizeof(T) == 4)
-    set_state_f32_kernel<<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d);
+    set_state_f32_kernel<<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d, t_begin);
   else
-    set_state_kernel<T><<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d);
+    set_state_kernel<T><<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d, t_begin);
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t launch_moments(const T* f, T* rho, T* ur, T* ut, T* temp, const StepParams& p,
-                           const DvmConst<T>& d, cudaStream_t s) {
-  dim3 grid((p.n_r + kRowThreads - 1) / kRowThreads, p.n_theta);
+                           const DvmConst<T>& d, cudaStream_t s, int t_begin, int t_end) {
+  if (t_end < 0) t_end = p.n_theta;
+  if (t_begin < 0 || t_end <= t_begin) return cudaSuccess;
+  dim3 grid((p.n_r + kRowThreads - 1) / kRowThreads, t_end - t_begin);
   if constexpr (sizeof(T) == 4)
-    moments_f32_kernel<<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d);
+    moments_f32_kernel<<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d, t_begin);
   else
-    moments_kernel<T><<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d);
+    moments_kernel<T><<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d, t_begin);
   return cudaGetLastError();
 }
 
@@ -234,9 +247,10 @@ cudaError_t launch_diagnostics(const T* f, double* partials, double* out, const 
 
 #define PCLB_INSTANTIATE(T)                                                                         \
   template cudaError_t launch_set_state<T>(T*, const T*, const T*, const T*, const T*,             \
-                                           const StepParams&, const DvmConst<T>&, cudaStream_t);   \
+                                           const StepParams&, const DvmConst<T>&, cudaStream_t,    \
+                                           int, int);                                              \
   template cudaError_t launch_moments<T>(const T*, T*, T*, T*, T*, const StepParams&,              \
-                                         const DvmConst<T>&, cudaStream_t);                        \
+                                         const DvmConst<T>&, cudaStream_t, int, int);              \
   template cudaError_t launch_pack<T>(const T*, T*, const StepParams&, cudaStream_t);              \
   template cudaError_t launch_unpack<T>(const T*, T*, const StepParams&, const DvmConst<T>&,       \
                                         cudaStream_t);                                             \

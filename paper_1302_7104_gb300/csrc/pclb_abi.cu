@@ -6,6 +6,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -18,15 +19,19 @@
 #include "pclb_internal.h"
 
 namespace pclb {
+// Step launchers take a range of tile rows, the field kernels a range of
+// grid rows (the whole grid by default).
 cudaError_t launch_step_f32(const CUtensorMap*, float*, const StepParams&, const DvmConst<float>&,
-                            cudaStream_t);
+                            cudaStream_t, int ty_begin = 0, int ty_end = -1);
 template <class T>
-cudaError_t launch_step(const CUtensorMap*, T*, const StepParams&, const DvmConst<T>&, cudaStream_t);
+cudaError_t launch_step(const CUtensorMap*, T*, const StepParams&, const DvmConst<T>&, cudaStream_t,
+                        int ty_begin = 0, int ty_end = -1);
 template <class T>
 cudaError_t launch_set_state(T*, const T*, const T*, const T*, const T*, const StepParams&,
-                             const DvmConst<T>&, cudaStream_t);
+                             const DvmConst<T>&, cudaStream_t, int t_begin = 0, int t_end = -1);
 template <class T>
-cudaError_t launch_moments(const T*, T*, T*, T*, T*, const StepParams&, const DvmConst<T>&, cudaStream_t);
+cudaError_t launch_moments(const T*, T*, T*, T*, T*, const StepParams&, const DvmConst<T>&, cudaStream_t,
+                           int t_begin = 0, int t_end = -1);
 template <class T>
 cudaError_t launch_pack(const T*, T*, const StepParams&, cudaStream_t);
 template <class T>
@@ -71,7 +76,7 @@ constexpr int kDefaultTimeoutMs = 120000;
 
 struct HostCtx : pclb_ctx {
   std::vector<double> cos_t, sin_t, inv_r, bc_vals;
-  std::vector<float> courant, inv_r_f;
+  std::vector<float> courant, inv_r_f, cs_ff;
   std::vector<double> courant64;
 };
 
@@ -145,6 +150,7 @@ Layout make_layout(const pclb_grid* g, const pclb_dvm* d, pclb_precision prec) {
   L.courant = off; off = align_up(off + (size_t)(g->n_theta + 2 * kGhostRows) * npairs * 16, 256);
   L.courant64 = off; off = align_up(off + (size_t)(g->n_theta + 2 * kGhostRows) * npairs * 32, 256);
   L.inv_r_f = off; off = align_up(off + (size_t)g->n_r * 4, 256);
+  L.cs_ff = off; off = align_up(off + (size_t)g->n_theta * 16, 256);
   L.status = off; off = align_up(off + 256, 256);
   L.partials = off; off = align_up(off + (size_t)kDiagBlocks * 8 * 8, 256);
   L.diag_out = off; off = align_up(off + 8 * 8, 256);
@@ -413,6 +419,214 @@ pclb_status do_adjoint(pclb_ctx* ctx, const CUtensorMap* tmap_f, const void* f) 
   return PCLB_OK;
 }
 
+// ---- pclb_run_host with page-locked host buffers --------------------------
+// The grid is cut into S azimuthal slabs of whole tile rows, and five streams
+// form a pipeline over them:
+//   io_in   copies the input fields of each slab into the staging area, the
+//           last slab first (its rows n_theta - 2, n_theta - 1 feed the
+//           azimuthal ghost rows that the first slab's step reads);
+//   io_set  sets the state of each slab once its fields have landed;
+//   stream  (the caller's) and io_alt, alternating by slab: step each slab
+//           once its rows and the two rows on either side are set, and
+//           compute its moments into the staging area (two streams, so that
+//           one slab's step starts while the previous one drains);
+//   io_out  copies each slab's moments to the host.
+// The transfers run on the copy engines and the set-state kernels beside the
+// steps, instead of one after another.  A set-state kernel writes only its
+// own slab's rows (and the ghost rows they feed), which no step running at
+// the same time reads; the steps of two slabs read set rows and write
+// disjoint rows; a moment kernel reads only rows its own step wrote.
+
+void destroy_io(pclb_ctx* ctx) {
+  for (cudaStream_t* st : {&ctx->io_in, &ctx->io_set, &ctx->io_out, &ctx->io_alt}) {
+    if (*st) cudaStreamDestroy(*st);
+    *st = nullptr;
+  }
+  for (cudaEvent_t* ev : {&ctx->io_start, &ctx->io_done}) {
+    if (*ev) cudaEventDestroy(*ev);
+    *ev = nullptr;
+  }
+  for (int s = 0; s < pclb_ctx::kIoSlabs; ++s)
+    for (cudaEvent_t* ev : {&ctx->io_loaded[s], &ctx->io_isset[s], &ctx->io_ready[s]}) {
+      if (*ev) cudaEventDestroy(*ev);
+      *ev = nullptr;
+    }
+}
+
+pclb_status io_streams(pclb_ctx* ctx) {   // created on first use
+  if (ctx->io_in) return PCLB_OK;
+  int lo = 0, hi = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->io_in, cudaStreamNonBlocking);
+  // the set-state kernels unblock later steps: scheduled first
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->io_set, cudaStreamNonBlocking, hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->io_out, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->io_alt, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->io_start, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->io_done, cudaEventDisableTiming);
+  for (int s = 0; s < pclb_ctx::kIoSlabs && e == cudaSuccess; ++s)
+    for (cudaEvent_t* ev : {&ctx->io_loaded[s], &ctx->io_isset[s], &ctx->io_ready[s]})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    destroy_io(ctx);
+    return cuda_fail(ctx, e, "host-transfer streams");
+  }
+  return PCLB_OK;
+}
+
+// Number of slabs: about one per 2^17 nodes, at least 2, at most kIoSlabs and
+// the number of tile rows.
+int io_slab_count(const pclb_ctx* ctx) {
+  static_assert(kTileT == kTileT32, "slabs are whole tile rows of either step kernel");
+  const long long tiles = (ctx->grid.n_theta + kTileT - 1) / kTileT;
+  const long long nodes = (long long)ctx->grid.n_r * ctx->grid.n_theta;
+  return (int)std::min(std::min((long long)pclb_ctx::kIoSlabs, tiles), std::max(2ll, nodes >> 17));
+}
+
+// First tile rows of the S slabs (bounds[S] = tiles).  With enough tile rows
+// the slabs at both ends are smaller (weights 1, 2, 4, ..., 4, 2, 1): the
+// first step waits for the first, second and last slab's input, and the call
+// ends with the last slabs' moments and copies out.  Every slab has at least
+// one tile row.
+void io_slab_bounds(int tiles, int S, int* bounds) {
+  if (S < 5 || tiles < 4 * S) {
+    for (int s = 0; s <= S; ++s) bounds[s] = (int)((long long)s * tiles / S);
+    return;
+  }
+  auto weight = [&](int s) { return (s == 0 || s == S - 1) ? 1 : (s == 1 || s == S - 2) ? 2 : 4; };
+  long long total = 0;
+  for (int s = 0; s < S; ++s) total += weight(s);
+  long long acc = 0;
+  for (int s = 0; s < S; ++s) {
+    bounds[s] = (int)(acc * tiles / total);
+    acc += weight(s);
+  }
+  bounds[S] = tiles;
+}
+
+template <class T>
+pclb_status run_host_slabs(pclb_ctx* ctx, const void* const in[4], int n, void* const out[4]) {
+  pclb_status st = io_streams(ctx);
+  if (st != PCLB_OK) return st;
+  const int nt = ctx->grid.n_theta, S = io_slab_count(ctx);
+  const int tiles = (nt + kTileT - 1) / kTileT;
+  const size_t row_bytes = (size_t)ctx->grid.n_r * sizeof(T), field_bytes = row_bytes * nt;
+  unsigned char* stage = ctx->ws + ctx->lay.stage;
+  const T* fin[4];
+  T* fout[4];
+  for (int i = 0; i < 4; ++i) {
+    fin[i] = reinterpret_cast<const T*>(stage + i * field_bytes);
+    fout[i] = out[i] ? reinterpret_cast<T*>(stage + (4 + i) * field_bytes) : nullptr;
+  }
+  const bool any_out = out[0] || out[1] || out[2] || out[3];
+  cudaStream_t ms = ctx->stream;
+  int bounds[pclb_ctx::kIoSlabs + 1];
+  io_slab_bounds(tiles, S, bounds);
+  auto tile0 = [&](int s) { return bounds[s]; };                         // first tile row of slab s
+  auto row0 = [&](int s) { return std::min(tile0(s) * kTileT, nt); };    // first grid row of slab s
+  auto slab_of = [&](int t) {                                             // slab of row t (periodic)
+    t = ((t % nt) + nt) % nt;
+    int s = 0;
+    while (t >= row0(s + 1)) ++s;
+    return s;
+  };
+  auto order = [&](int j) { return j == 0 ? S - 1 : j - 1; };   // slabs in the order they are brought in
+  auto position = [&](int s) { return s == S - 1 ? 0 : s + 1; };   // inverse of order
+  auto cs = [&](int s) { return (s & 1) ? ctx->io_alt : ms; };   // compute stream of slab s
+  // the caller's stream waits for everything queued so far on `o`
+  auto join = [&](cudaStream_t o) {
+    cudaError_t e = cudaEventRecord(ctx->io_done, o);
+    return e == cudaSuccess ? cudaStreamWaitEvent(ms, ctx->io_done, 0) : e;
+  };
+  // on an error: the caller's stream waits for the other four before the
+  // error is returned (no copy or kernel of the call outlives it)
+  auto bail = [&](pclb_status err) {
+    for (cudaStream_t o : {ctx->io_in, ctx->io_set, ctx->io_alt, ctx->io_out}) join(o);
+    bounded_sync(ctx, kDefaultTimeoutMs);
+    return err;
+  };
+  auto step = [&](int src, int s) -> cudaError_t {
+    if constexpr (sizeof(T) == 4)
+      return launch_step_f32(&ctx->tmap[src], fbuf<float>(ctx, 1 - src), ctx->sp, ctx->dvm32, cs(s), tile0(s),
+                             tile0(s + 1));
+    else
+      return launch_step<T>(&ctx->tmap[src], fbuf<T>(ctx, 1 - src), ctx->sp, dvm_of<T>(ctx), cs(s), tile0(s),
+                            tile0(s + 1));
+  };
+  // moments of slab s of buffer b into the staging area (on the slab's
+  // compute stream), then their copies to the host on io_out
+  auto emit = [&](int b, int s) -> cudaError_t {
+    cudaError_t e = launch_moments<T>(fbuf<T>(ctx, b), fout[0], fout[1], fout[2], fout[3], ctx->sp, dvm_of<T>(ctx),
+                                      cs(s), row0(s), row0(s + 1));
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->io_ready[s], cs(s));
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->io_out, ctx->io_ready[s], 0);
+    const size_t off = (size_t)row0(s) * row_bytes, len = (size_t)(row0(s + 1) - row0(s)) * row_bytes;
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+      if (out[i])
+        e = cudaMemcpyAsync(static_cast<unsigned char*>(out[i]) + off, stage + (4 + i) * field_bytes + off, len,
+                            cudaMemcpyDeviceToHost, ctx->io_out);
+    return e;
+  };
+
+  const int src = ctx->cur;
+  cudaError_t e = cudaEventRecord(ctx->io_start, ms);   // everything follows earlier work on the stream
+  for (cudaStream_t o : {ctx->io_in, ctx->io_set, ctx->io_out, ctx->io_alt})
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(o, ctx->io_start, 0);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "host-transfer ordering");
+  for (int j = 0; j < S; ++j) {
+    const int s = order(j);
+    const size_t off = (size_t)row0(s) * row_bytes, len = (size_t)(row0(s + 1) - row0(s)) * row_bytes;
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(stage + i * field_bytes + off, static_cast<const unsigned char*>(in[i]) + off, len,
+                          cudaMemcpyHostToDevice, ctx->io_in);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->io_loaded[s], ctx->io_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->io_set, ctx->io_loaded[s], 0);
+    if (e == cudaSuccess)
+      e = launch_set_state<T>(fbuf<T>(ctx, src), fin[0], fin[1], fin[2], fin[3], ctx->sp, dvm_of<T>(ctx),
+                              ctx->io_set, row0(s), row0(s + 1));
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->io_isset[s], ctx->io_set);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "input copy or set_state launch"));
+  }
+
+  // the first step slab by slab, each after the set-state kernels of the
+  // slabs its stencil reaches (the latest of them in io_set's order); when it
+  // is also the last step (or n = 0), each slab's moments follow at once
+  for (int c = 0; c < S; ++c) {
+    int last = position(c);
+    if (n >= 1) {
+      const int a = row0(c), b = row0(c + 1);
+      for (int t : {a - 2, a - 1, b, b + 1}) last = std::max(last, position(slab_of(t)));
+    }
+    e = cudaStreamWaitEvent(cs(c), ctx->io_isset[order(last)], 0);
+    if (e == cudaSuccess && n >= 1) e = step(src, c);
+    if (e == cudaSuccess && n <= 1 && any_out) e = emit(n == 0 ? src : 1 - src, c);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "step, moments or output copy"));
+  }
+  ctx->has_state = true;
+  if (n >= 1) ctx->cur = 1 - src;
+  if (n >= 2) {
+    // the steps in between on the whole grid (after every slab's first
+    // step), the last one slab by slab again
+    if ((e = join(ctx->io_set)) != cudaSuccess || (e = join(ctx->io_alt)) != cudaSuccess)
+      return bail(cuda_fail(ctx, e, "host-transfer ordering"));
+    if ((st = do_step<T>(ctx, n - 2)) != PCLB_OK) return bail(st);
+    e = cudaEventRecord(ctx->io_start, ms);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->io_alt, ctx->io_start, 0);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "host-transfer ordering"));
+    const int s2 = ctx->cur;
+    for (int c = 0; c < S; ++c) {
+      if ((e = step(s2, c)) != cudaSuccess) return bail(cuda_fail(ctx, e, "step kernel launch"));
+      if (any_out && (e = emit(1 - s2, c)) != cudaSuccess) return bail(cuda_fail(ctx, e, "moments or output copy"));
+    }
+    ctx->cur = 1 - s2;
+  }
+  // the caller's stream takes up everything: later calls see the new state
+  for (cudaStream_t o : {ctx->io_set, ctx->io_alt, ctx->io_out})
+    if (e == cudaSuccess) e = join(o);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "host-transfer ordering"));
+  return bounded_sync(ctx, kDefaultTimeoutMs);
+}
+
 }  // namespace
 
 extern "C" {
@@ -533,6 +747,16 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
       }
   ctx->inv_r_f.resize(NR);
   for (int r = 0; r < NR; ++r) ctx->inv_r_f[r] = (float)ctx->inv_r[r];
+  // cos and sin as float-float pairs for the FP32 field kernels' rotations
+  ctx->cs_ff.resize((size_t)NT * 4);
+  for (int t = 0; t < NT; ++t) {
+    const double cs[2] = {ctx->cos_t[t], ctx->sin_t[t]};
+    for (int j = 0; j < 2; ++j) {
+      const float hi = (float)cs[j];
+      ctx->cs_ff[(size_t)t * 4 + 2 * j] = hi;
+      ctx->cs_ff[(size_t)t * 4 + 2 * j + 1] = (float)(cs[j] - (double)hi);
+    }
+  }
   ctx->bc_vals.assign((size_t)2 * 2 * 4 * NT, 0.0);
   for (int s = 0; s < 2; ++s)
     if ((bc->kind[s] & ~PCLB_BC_NEQ) != PCLB_BC_EXTRAP)
@@ -556,6 +780,7 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
   sp.courant = reinterpret_cast<const float4*>(ctx->ws + lay.courant);
   sp.courant64 = reinterpret_cast<const double*>(ctx->ws + lay.courant64);
   sp.inv_r_f = reinterpret_cast<const float*>(ctx->ws + lay.inv_r_f);
+  sp.cs_ff = reinterpret_cast<const float4*>(ctx->ws + lay.cs_ff);
   sp.status = reinterpret_cast<uint32_t*>(ctx->ws + lay.status);
   if (dvm->n_dirs == kNDirs) {
     fill_dvm(ctx->dvm32, *dvm, *grid);
@@ -568,7 +793,8 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
       {lay.cos_t, ctx->cos_t.data(), NT * 8ul}, {lay.sin_t, ctx->sin_t.data(), NT * 8ul},
       {lay.inv_r, ctx->inv_r.data(), NR * 8ul}, {lay.bc_vals, ctx->bc_vals.data(), ctx->bc_vals.size() * 8},
       {lay.courant, ctx->courant.data(), ctx->courant.size() * 4},
-      {lay.courant64, ctx->courant64.data(), ctx->courant64.size() * 8}, {lay.inv_r_f, ctx->inv_r_f.data(), NR * 4ul}};
+      {lay.courant64, ctx->courant64.data(), ctx->courant64.size() * 8}, {lay.inv_r_f, ctx->inv_r_f.data(), NR * 4ul},
+      {lay.cs_ff, ctx->cs_ff.data(), NT * 16ul}};
   for (const Up& u : ups) {
     cudaError_t e = cudaMemcpyAsync(ctx->ws + u.off, u.src, u.n, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) {
@@ -608,6 +834,7 @@ pclb_status pclb_destroy(pclb_ctx* ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->side) cudaStreamDestroy(ctx->side);
+  destroy_io(ctx);
   delete static_cast<HostCtx*>(ctx);
   return st;
 }
@@ -845,31 +1072,26 @@ pclb_status pclb_run_host(pclb_ctx* ctx, const void* rho, const void* u_r, const
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
   if (!rho || !u_r || !u_theta || !T) return fail(ctx, PCLB_EINVAL, "input pointers must not be NULL");
   if (n < 0) return fail(ctx, PCLB_EINVAL, "n = %d must be >= 0", n);
-  // Page-locked host buffers are read and written by the kernels themselves
-  // through their device mapping (the transfers overlap the set-state and
-  // moment kernels); other host memory goes through staging copies.
-  {
+  // Page-locked host buffers (the tuned kernels): transfers slab by slab on
+  // copy streams, overlapped with the kernels; other host memory goes
+  // through staging copies in stream order.
+  if (!generic(ctx)) {
     const void* ptrs[8] = {rho, u_r, u_theta, T, out_rho, out_u_r, out_u_theta, out_T};
-    void* mapped[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    bool direct = true;
-    for (int i = 0; i < 8 && direct; ++i) {
+    bool pinned = true;
+    for (int i = 0; i < 8 && pinned; ++i) {
       if (!ptrs[i]) continue;
       cudaPointerAttributes a;
       if (cudaPointerGetAttributes(&a, ptrs[i]) != cudaSuccess) {
         cudaGetLastError();
-        direct = false;
-      } else if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr || misaligned(ctx, {a.devicePointer})) {
-        direct = false;
+        pinned = false;
       } else {
-        mapped[i] = a.devicePointer;
+        pinned = a.type == cudaMemoryTypeHost;
       }
     }
-    if (direct) {
-      pclb_status st = pclb_set_state(ctx, mapped[0], mapped[1], mapped[2], mapped[3]);
-      if (st != PCLB_OK) return st;
-      if ((st = pclb_step(ctx, n)) != PCLB_OK) return st;
-      if ((st = pclb_moments(ctx, mapped[4], mapped[5], mapped[6], mapped[7])) != PCLB_OK) return st;
-      return bounded_sync(ctx, kDefaultTimeoutMs);
+    if (pinned) {
+      const void* in[4] = {rho, u_r, u_theta, T};
+      void* out[4] = {out_rho, out_u_r, out_u_theta, out_T};
+      return ctx->prec == PCLB_FP32 ? run_host_slabs<float>(ctx, in, n, out) : run_host_slabs<double>(ctx, in, n, out);
     }
   }
   const size_t bytes = (size_t)ctx->grid.n_r * ctx->grid.n_theta * elem_size(ctx->prec);

@@ -94,6 +94,7 @@ struct StepParams {
                               // flags (bit 0: v_r < 0, bit 1: v_theta < 0) as int bits
   const double* courant64;    // the same table in double: [n_theta + 4][pairs][4] (flags as value)
   const float* inv_r_f;       // [n_r] 1 / r_i in float
+  const float4* cs_ff;        // [n_theta] cos theta_i, sin theta_i as float-float pairs (hi, lo, hi, lo)
   uint32_t* status;           // device status word (PCLB_FLAG_*)
 };
 
@@ -103,7 +104,7 @@ struct Layout {
   size_t adj_f;               // a state copy for pclb_adjoint_step
   size_t lam[2];              // ping-pong adjoint variables, same layout as f
   size_t f_bytes;
-  size_t cos_t, sin_t, inv_r, bc_vals, courant, courant64, inv_r_f;
+  size_t cos_t, sin_t, inv_r, bc_vals, courant, courant64, inv_r_f, cs_ff;
   size_t status;              // uint32 status word (+ padding)
   size_t partials;            // double [kDiagBlocks][8] reduction partials
   size_t diag_out;            // double [8]
@@ -167,6 +168,14 @@ struct pclb_ctx {
   } graphs[4] = {};
   int32_t n_graphs = 0;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // pclb_run_host with page-locked buffers: the host transfers of each
+  // azimuthal slab run on two copy streams and its set-state kernel on a
+  // third stream while the steps of other slabs run on `stream` and io_alt
+  // (created on first use)
+  static constexpr int kIoSlabs = 16;
+  cudaStream_t io_in = nullptr, io_set = nullptr, io_out = nullptr, io_alt = nullptr;
+  cudaEvent_t io_start = nullptr, io_done = nullptr;
+  cudaEvent_t io_loaded[kIoSlabs] = {}, io_isset[kIoSlabs] = {}, io_ready[kIoSlabs] = {};
   unsigned char* ws;
   pclb::Layout lay;
   int cur;                    // which of the two f buffers holds the state

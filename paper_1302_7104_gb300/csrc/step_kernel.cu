@@ -69,14 +69,14 @@ __device__ __forceinline__ double convect_aK(double a, double K, double f0, doub
 template <class T, int SCH>
 __global__ void __launch_bounds__(kThreads64, 1)
     step_kernel(const __grid_constant__ CUtensorMap tmap_in, T* __restrict__ f_out,
-                const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
+                const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d, int ty0) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   T* tab = sm + kQ * kPlane;                           // [pair][row][a_r, k_r, a_w, flags]
   uint64_t* bar = reinterpret_cast<uint64_t*>(tab + kPairs64 * kTileT * 4);
 
   const int r0 = blockIdx.x * kTileR;
-  const int t0 = blockIdx.y * kTileT;
+  const int t0 = (blockIdx.y + ty0) * kTileT;   // ty0: first tile row of the launch
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
 
@@ -224,30 +224,35 @@ __global__ void __launch_bounds__(kThreads64, 1)
 
 template <class T, int SCH>
 static cudaError_t launch_scheme(const CUtensorMap* tmap_in, T* f_out, const StepParams& p, const DvmConst<T>& d,
-                                 cudaStream_t stream) {
+                                 cudaStream_t stream, int ty_begin, int ty_end) {
   static std::atomic<unsigned long long> configured{0};   // per instantiation and device
   const int smem = step_smem_bytes<T>();
   {
     const cudaError_t e = set_smem_once(step_kernel<T, SCH>, smem, configured);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid((p.n_r + kTileR - 1) / kTileR, (p.n_theta + kTileT - 1) / kTileT);
-  step_kernel<T, SCH><<<grid, kThreads64, smem, stream>>>(*tmap_in, f_out, p, d);
+  dim3 grid((p.n_r + kTileR - 1) / kTileR, ty_end - ty_begin);
+  step_kernel<T, SCH><<<grid, kThreads64, smem, stream>>>(*tmap_in, f_out, p, d, ty_begin);
   return cudaGetLastError();
 }
 
+// Tile rows [ty_begin, ty_end) of the grid (ty_end < 0: to the last tile row);
+// an empty range launches nothing.
 template <class T>
 cudaError_t launch_step(const CUtensorMap* tmap_in, T* f_out, const StepParams& p,
-                        const DvmConst<T>& d, cudaStream_t stream) {
+                        const DvmConst<T>& d, cudaStream_t stream, int ty_begin, int ty_end) {
+  if (ty_end < 0) ty_end = (p.n_theta + kTileT - 1) / kTileT;
+  if (ty_begin < 0 || ty_end <= ty_begin) return cudaSuccess;
   switch (p.scheme) {
-    case PCLB_SCHEME_WB: return launch_scheme<T, PCLB_SCHEME_WB>(tmap_in, f_out, p, d, stream);
-    case PCLB_SCHEME_LW: return launch_scheme<T, PCLB_SCHEME_LW>(tmap_in, f_out, p, d, stream);
-    case PCLB_SCHEME_UPWIND2: return launch_scheme<T, PCLB_SCHEME_UPWIND2>(tmap_in, f_out, p, d, stream);
-    default: return launch_scheme<T, PCLB_SCHEME_MWB>(tmap_in, f_out, p, d, stream);
+    case PCLB_SCHEME_WB: return launch_scheme<T, PCLB_SCHEME_WB>(tmap_in, f_out, p, d, stream, ty_begin, ty_end);
+    case PCLB_SCHEME_LW: return launch_scheme<T, PCLB_SCHEME_LW>(tmap_in, f_out, p, d, stream, ty_begin, ty_end);
+    case PCLB_SCHEME_UPWIND2:
+      return launch_scheme<T, PCLB_SCHEME_UPWIND2>(tmap_in, f_out, p, d, stream, ty_begin, ty_end);
+    default: return launch_scheme<T, PCLB_SCHEME_MWB>(tmap_in, f_out, p, d, stream, ty_begin, ty_end);
   }
 }
 
 template cudaError_t launch_step<double>(const CUtensorMap*, double*, const StepParams&,
-                                         const DvmConst<double>&, cudaStream_t);
+                                         const DvmConst<double>&, cudaStream_t, int, int);
 
 }  // namespace pclb

@@ -250,14 +250,14 @@ __device__ __forceinline__ f2 limiter2(f2 D, f2 Dp) {
 template <int SCH>
 __global__ void __launch_bounds__(kStepThreads32, kCtasPerSm32)
     step_kernel_f32(const __grid_constant__ CUtensorMap tmap_in, float* __restrict__ f_out,
-                    const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<float> d) {
+                    const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<float> d, int ty0) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
   float4* tab = reinterpret_cast<float4*>(smem_raw + kPlanesBytes);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + kPlanesBytes + kTabBytes);
 
   const int r0 = blockIdx.x * kTileR;
-  const int t0 = blockIdx.y * kTileT32;
+  const int t0 = (blockIdx.y + ty0) * kTileT32;   // ty0: first tile row of the launch
   const int tid = threadIdx.x;
 
   // Thread 0 initialises the barriers and issues the copies at once; the
@@ -434,24 +434,29 @@ __global__ void __launch_bounds__(kStepThreads32, kCtasPerSm32)
 
 template <int SCH>
 static cudaError_t launch_scheme_f32(const CUtensorMap* tmap_in, float* f_out, const StepParams& p,
-                                     const DvmConst<float>& d, cudaStream_t stream) {
+                                     const DvmConst<float>& d, cudaStream_t stream, int ty_begin, int ty_end) {
   static std::atomic<unsigned long long> configured{0};   // per instantiation and device
   {
     const cudaError_t e = set_smem_once(step_kernel_f32<SCH>, kSmemF32, configured);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid((p.n_r + kTileR - 1) / kTileR, (p.n_theta + kTileT32 - 1) / kTileT32);
-  step_kernel_f32<SCH><<<grid, kStepThreads32, kSmemF32, stream>>>(*tmap_in, f_out, p, d);
+  dim3 grid((p.n_r + kTileR - 1) / kTileR, ty_end - ty_begin);
+  step_kernel_f32<SCH><<<grid, kStepThreads32, kSmemF32, stream>>>(*tmap_in, f_out, p, d, ty_begin);
   return cudaGetLastError();
 }
 
+// Tile rows [ty_begin, ty_end) of the grid (ty_end < 0: to the last tile row);
+// an empty range launches nothing.
 cudaError_t launch_step_f32(const CUtensorMap* tmap_in, float* f_out, const StepParams& p,
-                            const DvmConst<float>& d, cudaStream_t stream) {
+                            const DvmConst<float>& d, cudaStream_t stream, int ty_begin, int ty_end) {
+  if (ty_end < 0) ty_end = (p.n_theta + kTileT32 - 1) / kTileT32;
+  if (ty_begin < 0 || ty_end <= ty_begin) return cudaSuccess;
   switch (p.scheme) {
-    case PCLB_SCHEME_WB: return launch_scheme_f32<PCLB_SCHEME_WB>(tmap_in, f_out, p, d, stream);
-    case PCLB_SCHEME_LW: return launch_scheme_f32<PCLB_SCHEME_LW>(tmap_in, f_out, p, d, stream);
-    case PCLB_SCHEME_UPWIND2: return launch_scheme_f32<PCLB_SCHEME_UPWIND2>(tmap_in, f_out, p, d, stream);
-    default: return launch_scheme_f32<PCLB_SCHEME_MWB>(tmap_in, f_out, p, d, stream);
+    case PCLB_SCHEME_WB: return launch_scheme_f32<PCLB_SCHEME_WB>(tmap_in, f_out, p, d, stream, ty_begin, ty_end);
+    case PCLB_SCHEME_LW: return launch_scheme_f32<PCLB_SCHEME_LW>(tmap_in, f_out, p, d, stream, ty_begin, ty_end);
+    case PCLB_SCHEME_UPWIND2:
+      return launch_scheme_f32<PCLB_SCHEME_UPWIND2>(tmap_in, f_out, p, d, stream, ty_begin, ty_end);
+    default: return launch_scheme_f32<PCLB_SCHEME_MWB>(tmap_in, f_out, p, d, stream, ty_begin, ty_end);
   }
 }
 
