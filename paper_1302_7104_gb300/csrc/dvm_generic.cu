@@ -4,8 +4,11 @@
 // node, stencil values read from global memory (L1/L2).  Moments, temperature
 // recovery and the equilibrium factors are formed in double; the per-velocity
 // work (equilibrium polynomial, relaxation, convection) runs in the storage
-// type.  These sets serve the paper's velocity-set
-// comparison; the tuned TMA kernels cover N_i = 8.
+// type.  For FP32 storage the step forms the moments without FP64
+// arithmetic in the per-velocity sums (float shell sums with float-float unit
+// vectors, shell totals combined in double; GB300 runs FP64 at 1/64 of the
+// FP32 rate).  These sets serve the paper's velocity-set comparison; the
+// tuned TMA kernels cover N_i = 8.
 //
 // Radial ghost nodes (Sec. II C 1) are formed once per wall row by
 // gen_ghost_kernel into a small buffer [side][layer][n_theta][Q] (f = f^eq of
@@ -14,9 +17,11 @@
 // are stored rows, written by the producer of the seam rows with the label
 // rotation, as in the rest of the library.
 #include <cfloat>
+#include <cmath>
 #include <cstddef>
 #include <cuda_runtime.h>
 
+#include "dvm_generic.h"
 #include "pclb_internal.h"
 
 namespace pclb {
@@ -36,6 +41,54 @@ struct GenState {
   bool ok;
 };
 
+// Velocity and temperature from the sums rho, rho u, rho (E + u^2/2).
+__device__ __forceinline__ GenState gen_state_of(double s0, double sx, double sy, double se) {
+  GenState m;
+  m.rho = s0;
+  m.ux = sx / s0;
+  m.uy = sy / s0;
+  m.E = (se - 0.5 * (sx * m.ux + sy * m.uy)) / s0;
+  m.ok = s0 > 0.0 && m.E > 0.0 && isfinite(m.E) && isfinite(m.ux) && isfinite(m.uy);
+  return m;
+}
+
+// FP32 storage: the same moments with the per-velocity sums in float.  Per
+// shell, float sums over opposite-direction pairs (f_a + f_b, and f_a - f_b
+// times the float-float unit vector); shells 2 and 3 (nearly equal speeds,
+// equilibrium weights of opposite sign) are added direction by direction
+// first so that their large contributions cancel before rounding, and shell
+// 3 enters once more with the speed differences; the shell totals are
+// combined in double.
+__device__ GenState gen_moments_f32(const float* f, size_t plane, const DvmG& d, const DvmG32& c) {
+  const int nd = d.n_dirs, h = nd / 2;
+  double s0 = (double)f[0], sx = 0.0, sy = 0.0, se = 0.0;
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const int k = g == 0 ? 1 : (g == 1 ? 2 : (g == 2 ? 3 : 4));   // g = 1: shells 2 + 3; g = 2: shell 3
+    float S = 0.f, X = 0.f, Xl = 0.f, Y = 0.f, Yl = 0.f;
+    for (int i = 0; i < h; ++i) {
+      const int q = 1 + (k - 1) * nd + i;
+      float fa = f[(size_t)q * plane], fb = f[(size_t)(q + h) * plane];
+      if (g == 1) {
+        fa += f[(size_t)(q + nd) * plane];
+        fb += f[(size_t)(q + nd + h) * plane];
+      }
+      S += fa + fb;
+      const float dd = fa - fb;   // the pair has opposite unit vectors
+      X = fmaf(c.cxh[i], dd, X);
+      Xl = fmaf(c.cxl[i], dd, Xl);
+      Y = fmaf(c.cyh[i], dd, Y);
+      Yl = fmaf(c.cyl[i], dd, Yl);
+    }
+    const double sp = g == 2 ? c.dv23 : c.speed[k], hv = g == 2 ? c.dh23 : c.half_v2[k];
+    if (g != 2) s0 += (double)S;
+    sx = fma(sp, (double)X + (double)Xl, sx);
+    sy = fma(sp, (double)Y + (double)Yl, sy);
+    se = fma(hv, (double)S, se);
+  }
+  return gen_state_of(s0, sx, sy, se);
+}
+
 // Moments (Eqs. 3-5): rho = sum f, rho u = sum f v, rho (E + u^2/2) = sum f v^2/2.
 template <class T>
 __device__ GenState gen_moments_node(const T* f, size_t plane, const DvmG& d) {
@@ -47,13 +100,7 @@ __device__ GenState gen_moments_node(const T* f, size_t plane, const DvmG& d) {
     sy = fma(d.vy[q], v, sy);
     se = fma(d.half_v2[d.shell[q]], v, se);
   }
-  GenState m;
-  m.rho = s0;
-  m.ux = sx / s0;
-  m.uy = sy / s0;
-  m.E = (se - 0.5 * (sx * m.ux + sy * m.uy)) / s0;
-  m.ok = s0 > 0.0 && m.E > 0.0 && isfinite(m.E) && isfinite(m.ux) && isfinite(m.uy);
-  return m;
+  return gen_state_of(s0, sx, sy, se);
 }
 
 __device__ GenEq gen_eq(double rho, double ux, double uy, double E, const DvmG& d) {
@@ -130,12 +177,12 @@ __device__ __forceinline__ C gen_convect(C a, C K, C f0, C u1, C u2, C d1) {
 // Store of label q at interior node (t, r), and of the azimuthal ghost rows
 // of the receiving labels when t is a seam row (Eq. 40).
 template <class T>
-__device__ __forceinline__ void gen_store(T* f, const StepParams& p, const DvmG& d, int q, int t, int r, double v) {
+__device__ __forceinline__ void gen_store(T* f, const StepParams& p, const DvmG& d, int q, int t, int r, T v) {
   const size_t plane = (size_t)p.rows * p.pitch;
-  f[(size_t)q * plane + (size_t)(t + kGhostRows) * p.pitch + r] = (T)v;
+  f[(size_t)q * plane + (size_t)(t + kGhostRows) * p.pitch + r] = v;
   if (t >= p.n_theta - 2)
-    f[(size_t)d.recv_lo[q] * plane + (size_t)(t - (p.n_theta - 2)) * p.pitch + r] = (T)v;
-  if (t < 2) f[(size_t)d.recv_hi[q] * plane + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r] = (T)v;
+    f[(size_t)d.recv_lo[q] * plane + (size_t)(t - (p.n_theta - 2)) * p.pitch + r] = v;
+  if (t < 2) f[(size_t)d.recv_hi[q] * plane + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -152,7 +199,7 @@ __global__ void __launch_bounds__(kGenThreads)
   const double R = (double)rho[n], ur = (double)u_r[n], ut = (double)u_t[n], E = (double)temp[n];  // E = T
   if (!(R > 0.0 && E > 0.0)) atomicOr(p.status, PCLB_FLAG_NONPHYS);
   const GenEq e = gen_eq(R, ur * c - ut * s, ur * s + ut * c, E, d);
-  for (int q = 0; q < d.q; ++q) gen_store<T>(f, p, d, q, t, r, gen_feq(e, d, q));
+  for (int q = 0; q < d.q; ++q) gen_store<T>(f, p, d, q, t, r, (T)gen_feq(e, d, q));
 }
 
 template <class T>
@@ -188,7 +235,7 @@ __global__ void __launch_bounds__(kGenThreads)
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y, q = blockIdx.z;
   if (r >= p.n_r) return;
-  gen_store<T>(f, p, d, q, t, r, (double)in[((size_t)q * p.n_theta + t) * p.n_r + r]);
+  gen_store<T>(f, p, d, q, t, r, in[((size_t)q * p.n_theta + t) * p.n_r + r]);
 }
 
 // Radial ghost layers of wall `side` at row t: layer l sits at r = -1 - l
@@ -242,22 +289,29 @@ __global__ void __launch_bounds__(kGenThreads)
   if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
 }
 
-// One step (Eq. 38) at node (t, r): moments and equilibrium factors in
-// double, then per pair of opposite velocities (sharing the Courant entry and
-// the even and odd parts of the equilibrium polynomial) the relaxation (decay
-// d = exp(-dt/tau) or 1 - dt/tau) minus the convection increments in r and
-// theta, in the storage type T.
+// One step (Eq. 38) at node (t, r): moments (in double, or for FP32 storage
+// from float shell sums) and equilibrium factors in double, then per pair of
+// opposite velocities (sharing the Courant entry and the even and odd parts
+// of the equilibrium polynomial) the relaxation (decay d = exp(-dt/tau) or
+// 1 - dt/tau) minus the convection increments in r and theta, in the storage
+// type T (for FP32 with the float Courant table and velocities).
 template <class T, int SCH>
 __global__ void __launch_bounds__(kGenThreads)
     gen_step_kernel(const T* __restrict__ f, T* __restrict__ f_out, const T* __restrict__ ghost,
-                    const __grid_constant__ StepParams p, const __grid_constant__ DvmG d) {
+                    const __grid_constant__ StepParams p, const __grid_constant__ DvmG d,
+                    const __grid_constant__ DvmG32 d32) {
+  constexpr bool kF32 = sizeof(T) == 4;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
   if (r >= p.n_r) return;
   const size_t plane = (size_t)p.rows * p.pitch;
   const int srow = t + kGhostRows;
   const T* fn = f + (size_t)srow * p.pitch + r;
-  const GenState m = gen_moments_node(fn, plane, d);
+  GenState m;
+  if constexpr (kF32)
+    m = gen_moments_f32(fn, plane, d, d32);
+  else
+    m = gen_moments_node(fn, plane, d);
   if (!m.ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
   const GenEq ed = gen_eq(m.rho, m.ux, m.uy, m.E, d);
   const GenEqC<T> e = gen_eq_c<T>(ed);
@@ -281,19 +335,35 @@ __global__ void __launch_bounds__(kGenThreads)
   for (int k = 1; k <= 4; ++k)
     for (int i = 0; i < half; ++i) {
       const int q1 = 1 + (k - 1) * d.n_dirs + i, q2 = q1 + half;
-      const double* ce = p.courant64 + ((size_t)srow * npairs + (k - 1) * half + i) * 4;
-      const T ar = (T)ce[0], kr = (T)ce[1], at = (T)ce[2] * inv_r, kt = at - at * at;
-      const int fl = (int)ce[3];
+      T ar, kr, at;
+      int fl;
+      if constexpr (kF32) {
+        const float4 ce = p.courant[(size_t)srow * npairs + (k - 1) * half + i];
+        ar = ce.x;
+        kr = ce.y;
+        at = ce.z * inv_r;
+        fl = __float_as_int(ce.w);
+      } else {
+        const double* ce = p.courant64 + ((size_t)srow * npairs + (k - 1) * half + i) * 4;
+        ar = ce[0];
+        kr = ce[1];
+        at = ce[2] * inv_r;
+        fl = (int)ce[3];
+      }
+      const T kt = at - at * at;
       const int sr = (fl & 1) ? 1 : -1;   // v_r < 0 for q1: upwind at larger r
       const int st = (fl & 2) ? 1 : -1;   // v_theta < 0 for q1: upwind at larger theta
       T fe[2];
-      gen_feq_pair<T>(e, (T)d.vx[q1], (T)d.vy[q1], k, fe[0], fe[1]);
+      if constexpr (kF32)
+        gen_feq_pair<T>(e, d32.vx[q1], d32.vy[q1], k, fe[0], fe[1]);
+      else
+        gen_feq_pair<T>(e, d.vx[q1], d.vy[q1], k, fe[0], fe[1]);
       for (int L = 0; L < 2; ++L) {
         const int q = L ? q2 : q1, s_r = L ? -sr : sr, s_t = L ? -st : st;
         const T a = fn[(size_t)q * plane];
         const T cr = gen_convect<SCH, T>(ar, kr, a, fr(q, r + s_r), fr(q, r + 2 * s_r), lw ? fr(q, r - s_r) : T(0));
         const T ct = gen_convect<SCH, T>(at, kt, a, ft(q, s_t), ft(q, 2 * s_t), lw ? ft(q, -s_t) : T(0));
-        gen_store<T>(f_out, p, d, q, t, r, (double)(fe[L] + (a - fe[L]) * decay - cr - ct));
+        gen_store<T>(f_out, p, d, q, t, r, fe[L] + (a - fe[L]) * decay - cr - ct);
       }
     }
 }
@@ -348,10 +418,11 @@ __global__ void gen_diag_final_kernel(const double* partials, int n_blocks, doub
 }
 
 template <class T, int SCH>
-cudaError_t gen_step_scheme(const T* f, T* f_out, T* ghost, const StepParams& p, const DvmG& d, cudaStream_t s) {
+cudaError_t gen_step_scheme(const T* f, T* f_out, T* ghost, const StepParams& p, const DvmG& d, const DvmG32& d32,
+                            cudaStream_t s) {
   gen_ghost_kernel<T><<<dim3((p.n_theta + kGenThreads - 1) / kGenThreads, 2), kGenThreads, 0, s>>>(f, ghost, p, d);
   gen_step_kernel<T, SCH><<<dim3((p.n_r + kGenThreads - 1) / kGenThreads, p.n_theta), kGenThreads, 0, s>>>(
-      f, f_out, ghost, p, d);
+      f, f_out, ghost, p, d, d32);
   return cudaGetLastError();
 }
 
@@ -387,13 +458,44 @@ cudaError_t gen_launch_unpack(const T* in, T* f, const StepParams& p, const DvmG
 }
 
 template <class T>
-cudaError_t gen_launch_step(const T* f, T* f_out, T* ghost, const StepParams& p, const DvmG& d, cudaStream_t s) {
+cudaError_t gen_launch_step(const T* f, T* f_out, T* ghost, const StepParams& p, const DvmG& d, const DvmG32& d32,
+                            cudaStream_t s) {
   switch (p.scheme) {
-    case PCLB_SCHEME_WB: return gen_step_scheme<T, PCLB_SCHEME_WB>(f, f_out, ghost, p, d, s);
-    case PCLB_SCHEME_LW: return gen_step_scheme<T, PCLB_SCHEME_LW>(f, f_out, ghost, p, d, s);
-    case PCLB_SCHEME_UPWIND2: return gen_step_scheme<T, PCLB_SCHEME_UPWIND2>(f, f_out, ghost, p, d, s);
-    default: return gen_step_scheme<T, PCLB_SCHEME_MWB>(f, f_out, ghost, p, d, s);
+    case PCLB_SCHEME_WB: return gen_step_scheme<T, PCLB_SCHEME_WB>(f, f_out, ghost, p, d, d32, s);
+    case PCLB_SCHEME_LW: return gen_step_scheme<T, PCLB_SCHEME_LW>(f, f_out, ghost, p, d, d32, s);
+    case PCLB_SCHEME_UPWIND2: return gen_step_scheme<T, PCLB_SCHEME_UPWIND2>(f, f_out, ghost, p, d, d32, s);
+    default: return gen_step_scheme<T, PCLB_SCHEME_MWB>(f, f_out, ghost, p, d, d32, s);
   }
+}
+
+void fill_dvm_generic32(DvmG32& c, const pclb_dvm& d) {
+  const int nd = d.n_dirs;
+  c = DvmG32{};
+  for (int k = 0; k < 5; ++k) {
+    c.speed[k] = d.speeds[k];
+    c.half_v2[k] = 0.5 * d.speeds[k] * d.speeds[k];
+  }
+  c.dv23 = d.speeds[3] - d.speeds[2];
+  c.dh23 = c.half_v2[3] - c.half_v2[2];
+  for (int i = 0; i < nd / 2; ++i) {
+    const double phi = 2.0 * M_PI * i / nd;
+    const double u[2] = {std::cos(phi), std::sin(phi)};
+    float* hi[2] = {c.cxh, c.cyh};
+    float* lo[2] = {c.cxl, c.cyl};
+    for (int j = 0; j < 2; ++j) {
+      hi[j][i] = (float)u[j];
+      lo[j][i] = (float)(u[j] - (double)hi[j][i]);
+    }
+  }
+  // the same velocities as DvmG (opposite directions exactly antisymmetric)
+  for (int k = 1; k <= 4; ++k)
+    for (int i = 0; i < nd; ++i) {
+      const int q = 1 + (k - 1) * nd + i;
+      const int ib = i % (nd / 2);
+      const double phi = 2.0 * M_PI * ib / nd, sgn = i < nd / 2 ? 1.0 : -1.0;
+      c.vx[q] = (float)(d.speeds[k] * sgn * std::cos(phi));
+      c.vy[q] = (float)(d.speeds[k] * sgn * std::sin(phi));
+    }
 }
 
 template <class T>
@@ -411,7 +513,8 @@ cudaError_t gen_launch_diagnostics(const T* f, double* partials, double* out, co
                                              cudaStream_t);                                                   \
   template cudaError_t gen_launch_pack<T>(const T*, T*, const StepParams&, const DvmG&, cudaStream_t);        \
   template cudaError_t gen_launch_unpack<T>(const T*, T*, const StepParams&, const DvmG&, cudaStream_t);      \
-  template cudaError_t gen_launch_step<T>(const T*, T*, T*, const StepParams&, const DvmG&, cudaStream_t);    \
+  template cudaError_t gen_launch_step<T>(const T*, T*, T*, const StepParams&, const DvmG&, const DvmG32&,    \
+                                          cudaStream_t);                                                      \
   template cudaError_t gen_launch_diagnostics<T>(const T*, double*, double*, const StepParams&, const DvmG&,  \
                                                  double, double, double, cudaStream_t);
 PCLB_GEN_INSTANTIATE(float)

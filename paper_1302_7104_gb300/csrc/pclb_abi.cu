@@ -16,6 +16,7 @@
 #include <thread>
 #include <vector>
 
+#include "dvm_generic.h"
 #include "pclb_internal.h"
 
 namespace pclb {
@@ -55,7 +56,7 @@ cudaError_t gen_launch_pack(const T*, T*, const StepParams&, const DvmG&, cudaSt
 template <class T>
 cudaError_t gen_launch_unpack(const T*, T*, const StepParams&, const DvmG&, cudaStream_t);
 template <class T>
-cudaError_t gen_launch_step(const T*, T*, T*, const StepParams&, const DvmG&, cudaStream_t);
+cudaError_t gen_launch_step(const T*, T*, T*, const StepParams&, const DvmG&, const DvmG32&, cudaStream_t);
 template <class T>
 cudaError_t gen_launch_diagnostics(const T*, double*, double*, const StepParams&, const DvmG&, double, double,
                                    double, cudaStream_t);
@@ -78,7 +79,10 @@ struct HostCtx : pclb_ctx {
   std::vector<double> cos_t, sin_t, inv_r, bc_vals;
   std::vector<float> courant, inv_r_f, cs_ff;
   std::vector<double> courant64;
+  DvmG32 dvmg32;   // N_i = 16, 24: float tables of the FP32 generic step
 };
+
+const DvmG32& dvmg32(const pclb_ctx* c) { return static_cast<const HostCtx*>(c)->dvmg32; }
 
 pclb_status fail(pclb_ctx* ctx, pclb_status st, const char* fmt, ...) {
   char* buf = ctx ? ctx->err : g_err;
@@ -384,7 +388,7 @@ pclb_status do_step(pclb_ctx* ctx, int n) {
     cudaError_t e;
     if (generic(ctx))
       e = gen_launch_step<T>(fbuf<T>(ctx, src), fbuf<T>(ctx, dst), reinterpret_cast<T*>(ctx->ws + ctx->lay.gen_ghost),
-                             ctx->sp, ctx->dvmg, ctx->stream);
+                             ctx->sp, ctx->dvmg, dvmg32(ctx), ctx->stream);
     else if constexpr (sizeof(T) == 4)
       e = launch_step_f32(&ctx->tmap[src], fbuf<float>(ctx, dst), ctx->sp, ctx->dvm32, ctx->stream);
     else
@@ -787,6 +791,7 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
     fill_dvm(ctx->dvm64, *dvm, *grid);
   } else {
     fill_dvm_generic(ctx->dvmg, *dvm, *grid);
+    fill_dvm_generic32(ctx->dvmg32, *dvm);
   }
 
   struct Up { size_t off; const void* src; size_t n; } ups[] = {
@@ -921,10 +926,10 @@ pclb_status pclb_step_states(pclb_ctx* ctx, const void* f_from, void* f_to) {
     e = ctx->prec == PCLB_FP32
             ? gen_launch_step<float>((const float*)f_from, (float*)f_to,
                                      reinterpret_cast<float*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg,
-                                     ctx->stream)
+                                     dvmg32(ctx), ctx->stream)
             : gen_launch_step<double>((const double*)f_from, (double*)f_to,
                                       reinterpret_cast<double*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg,
-                                      ctx->stream);
+                                      dvmg32(ctx), ctx->stream);
   } else {
     CUtensorMap map;
     pclb_status st = encode_map(ctx, f_from, ctx->prec == PCLB_FP32 ? kTileT32 + 4 : kWinT, &map);
