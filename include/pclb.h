@@ -46,8 +46,10 @@
  * are accumulated across shells with two-sum / two-product corrections, the
  * temperature recovery T = (e - |j|^2 / (2 rho)) / rho and the weights F_k(T)
  * of Eq. (11) are evaluated in float-float, and so is x = v.u / T with
- * float-float velocity constants.  The adjoint step (PCLB_FP32) recovers the
- * moments in double.  PCLB_FP64 computes everything in double.
+ * float-float velocity constants.  The adjoint step (PCLB_FP32) takes each
+ * node's state from the same float-float moments, rounded to float, and
+ * evaluates the cotangents in float (the ghost states at the walls in
+ * double).  PCLB_FP64 computes everything in double.
  */
 #ifndef PCLB_H
 #define PCLB_H
