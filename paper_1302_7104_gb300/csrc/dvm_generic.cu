@@ -4,11 +4,12 @@
 // node, stencil values read from global memory (L1/L2).  Moments, temperature
 // recovery and the equilibrium factors are formed in double; the per-velocity
 // work (equilibrium polynomial, relaxation, convection) runs in the storage
-// type.  For FP32 storage the step forms the moments without FP64
-// arithmetic in the per-velocity sums (float shell sums with float-float unit
-// vectors, shell totals combined in double; GB300 runs FP64 at 1/64 of the
-// FP32 rate).  These sets serve the paper's velocity-set comparison; the
-// tuned TMA kernels cover N_i = 8.
+// type.  For FP32 storage the step forms the node state and the equilibrium
+// factors without FP64 arithmetic (GB300 runs FP64 at 1/64 of the FP32 rate):
+// float shell sums with float-float unit vectors, combined, and the
+// temperature and weights evaluated, in float-float, as the tuned FP32 kernel
+// does.  These sets serve the paper's velocity-set comparison; the tuned TMA
+// kernels cover N_i = 8.
 //
 // Radial ghost nodes (Sec. II C 1) are formed once per wall row by
 // gen_ghost_kernel into a small buffer [side][layer][n_theta][Q] (f = f^eq of
@@ -22,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include "dvm_generic.h"
+#include "f32_state.cuh"
 #include "pclb_internal.h"
 
 namespace pclb {
@@ -50,43 +52,6 @@ __device__ __forceinline__ GenState gen_state_of(double s0, double sx, double sy
   m.E = (se - 0.5 * (sx * m.ux + sy * m.uy)) / s0;
   m.ok = s0 > 0.0 && m.E > 0.0 && isfinite(m.E) && isfinite(m.ux) && isfinite(m.uy);
   return m;
-}
-
-// FP32 storage: the same moments with the per-velocity sums in float.  Per
-// shell, float sums over opposite-direction pairs (f_a + f_b, and f_a - f_b
-// times the float-float unit vector); shells 2 and 3 (nearly equal speeds,
-// equilibrium weights of opposite sign) are added direction by direction
-// first so that their large contributions cancel before rounding, and shell
-// 3 enters once more with the speed differences; the shell totals are
-// combined in double.
-__device__ GenState gen_moments_f32(const float* f, size_t plane, const DvmG& d, const DvmG32& c) {
-  const int nd = d.n_dirs, h = nd / 2;
-  double s0 = (double)f[0], sx = 0.0, sy = 0.0, se = 0.0;
-#pragma unroll
-  for (int g = 0; g < 4; ++g) {
-    const int k = g == 0 ? 1 : (g == 1 ? 2 : (g == 2 ? 3 : 4));   // g = 1: shells 2 + 3; g = 2: shell 3
-    float S = 0.f, X = 0.f, Xl = 0.f, Y = 0.f, Yl = 0.f;
-    for (int i = 0; i < h; ++i) {
-      const int q = 1 + (k - 1) * nd + i;
-      float fa = f[(size_t)q * plane], fb = f[(size_t)(q + h) * plane];
-      if (g == 1) {
-        fa += f[(size_t)(q + nd) * plane];
-        fb += f[(size_t)(q + nd + h) * plane];
-      }
-      S += fa + fb;
-      const float dd = fa - fb;   // the pair has opposite unit vectors
-      X = fmaf(c.cxh[i], dd, X);
-      Xl = fmaf(c.cxl[i], dd, Xl);
-      Y = fmaf(c.cyh[i], dd, Y);
-      Yl = fmaf(c.cyl[i], dd, Yl);
-    }
-    const double sp = g == 2 ? c.dv23 : c.speed[k], hv = g == 2 ? c.dh23 : c.half_v2[k];
-    if (g != 2) s0 += (double)S;
-    sx = fma(sp, (double)X + (double)Xl, sx);
-    sy = fma(sp, (double)Y + (double)Yl, sy);
-    se = fma(hv, (double)S, se);
-  }
-  return gen_state_of(s0, sx, sy, se);
 }
 
 // Moments (Eqs. 3-5): rho = sum f, rho u = sum f v, rho (E + u^2/2) = sum f v^2/2.
@@ -139,6 +104,73 @@ __device__ __forceinline__ GenEqC<C> gen_eq_c(const GenEq& e) {
   for (int k = 0; k < 5; ++k) c.w[k] = (C)e.w[k];
   c.a0 = (C)e.a0; c.a1 = (C)e.a1; c.a1h = (C)e.a1h; c.uxE = (C)e.uxE; c.uyE = (C)e.uyE;
   return c;
+}
+
+// FP32 storage: the node's moments (Eqs. 3-5), temperature and equilibrium
+// factors (Eqs. 10-11) in float-float, rounded to float once.  Per shell,
+// float sums over opposite-direction pairs (f_a + f_b, and f_a - f_b times the
+// float-float unit vector); shells 2 and 3 (nearly equal speeds, equilibrium
+// weights of opposite sign) are added direction by direction first so that
+// their large contributions cancel before rounding, and shell 3 enters once
+// more with the speed differences; the shell totals are combined with
+// error-free transformations.  Returns whether the state is physical.
+__device__ bool gen_node_f32(const float* f, size_t plane, const DvmG& d, const DvmG32& c, GenEqC<float>& out) {
+  const int nd = d.n_dirs, h = nd / 2;
+  ff rho = ff_of(f[0]), jx = ff_of(0.f), jy = ff_of(0.f), e = ff_of(0.f);
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const int k = g == 0 ? 1 : (g == 1 ? 2 : (g == 2 ? 3 : 4));   // g = 1: shells 2 + 3; g = 2: shell 3
+    float S = 0.f, X = 0.f, Xl = 0.f, Y = 0.f, Yl = 0.f;
+    for (int i = 0; i < h; ++i) {
+      const int q = 1 + (k - 1) * nd + i;
+      float fa = f[(size_t)q * plane], fb = f[(size_t)(q + h) * plane];
+      if (g == 1) {
+        fa += f[(size_t)(q + nd) * plane];
+        fb += f[(size_t)(q + nd + h) * plane];
+      }
+      S += fa + fb;
+      const float dd = fa - fb;   // the pair has opposite unit vectors
+      X = fmaf(c.cxh[i], dd, X);
+      Xl = fmaf(c.cxl[i], dd, Xl);
+      Y = fmaf(c.cyh[i], dd, Y);
+      Yl = fmaf(c.cyl[i], dd, Yl);
+    }
+    const ff sp = g == 2 ? ff{c.dv23h, c.dv23l} : ff{c.sph[k], c.spl[k]};
+    const ff hv = g == 2 ? ff{c.dh23h, c.dh23l} : ff{c.hvh[k], c.hvl[k]};
+    if (g != 2) rho = ff_add(rho, ff_of(S));
+    jx = ff_add(jx, ff_mul(sp, ff{X, Xl}));
+    jy = ff_add(jy, ff_mul(sp, ff{Y, Yl}));
+    e = ff_add(e, ff_mul(hv, ff_of(S)));
+  }
+  const ff inv = ff_recip(rho);
+  const ff ux = ff_mul(jx, inv), uy = ff_mul(jy, inv);
+  const ff ke = ff_add(ff_mul(jx, ux), ff_mul(jy, uy));   // |j|^2 / rho
+  const ff E = ff_mul(ff_add(e, ff_scale(ke, -0.5f)), inv);
+  const bool ok = rho.hi > 0.f && E.hi > 0.f && isfinite(e.hi) && isfinite(jx.hi) && isfinite(jy.hi);
+  ff sum = ff_of(0.f);
+#pragma unroll
+  for (int k = 1; k <= 4; ++k) {
+    ff a{c.Fch[k][3], c.Fcl[k][3]};
+#pragma unroll
+    for (int n = 2; n >= 0; --n) a = ff_mul_add(a, E, ff{c.Fch[k][n], c.Fcl[k][n]});
+    a = ff_mul(a, E);   // F_k(E)
+    sum = ff_add(sum, a);
+    const ff w = ff_mul(rho, a);
+    out.w[k] = w.hi + w.lo;
+  }
+  const ff w0 = ff_mul(rho, ff_add(ff_of(1.f), ff_mul(ff{-c.B0h, -c.B0l}, sum)));
+  out.w[0] = w0.hi + w0.lo;
+  const ff invE = ff_recip(E);
+  const ff uxE = ff_mul(ux, invE), uyE = ff_mul(uy, invE);
+  const ff u2E = ff_add(ff_mul(ux, uxE), ff_mul(uy, uyE));   // u^2 / E
+  const ff a1 = ff_add(ff_of(1.f), ff_scale(u2E, -0.5f));
+  const ff a0 = ff_add(a1, ff_scale(ff_mul(u2E, u2E), 0.125f));
+  out.a1 = a1.hi + a1.lo;
+  out.a0 = a0.hi + a0.lo;
+  out.a1h = 0.5f * out.a1;
+  out.uxE = uxE.hi + uxE.lo;
+  out.uyE = uyE.hi + uyE.lo;
+  return ok;
 }
 
 // f^eq of velocity (vx, vy) of shell k, Eq. (10), as even and odd parts in x
@@ -289,8 +321,8 @@ __global__ void __launch_bounds__(kGenThreads)
   if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
 }
 
-// One step (Eq. 38) at node (t, r): moments (in double, or for FP32 storage
-// from float shell sums) and equilibrium factors in double, then per pair of
+// One step (Eq. 38) at node (t, r): moments and equilibrium factors (in
+// double for FP64 storage, in float-float for FP32), then per pair of
 // opposite velocities (sharing the Courant entry and the even and odd parts
 // of the equilibrium polynomial) the relaxation (decay d = exp(-dt/tau) or
 // 1 - dt/tau) minus the convection increments in r and theta, in the storage
@@ -307,14 +339,16 @@ __global__ void __launch_bounds__(kGenThreads)
   const size_t plane = (size_t)p.rows * p.pitch;
   const int srow = t + kGhostRows;
   const T* fn = f + (size_t)srow * p.pitch + r;
-  GenState m;
-  if constexpr (kF32)
-    m = gen_moments_f32(fn, plane, d, d32);
-  else
-    m = gen_moments_node(fn, plane, d);
-  if (!m.ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
-  const GenEq ed = gen_eq(m.rho, m.ux, m.uy, m.E, d);
-  const GenEqC<T> e = gen_eq_c<T>(ed);
+  GenEqC<T> e;
+  bool ok;
+  if constexpr (kF32) {
+    ok = gen_node_f32(fn, plane, d, d32, e);
+  } else {
+    const GenState m = gen_moments_node(fn, plane, d);
+    ok = m.ok;
+    e = gen_eq_c<T>(gen_eq(m.rho, m.ux, m.uy, m.E, d));
+  }
+  if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
   const T decay = (T)p.decay;
   // value of label q at radial index rr of row t (a ghost layer outside the grid)
   auto fr = [&](int q, int rr) -> T {
@@ -468,15 +502,21 @@ cudaError_t gen_launch_step(const T* f, T* f_out, T* ghost, const StepParams& p,
   }
 }
 
-void fill_dvm_generic32(DvmG32& c, const pclb_dvm& d) {
+void fill_dvm_generic32(DvmG32& c, const pclb_dvm& d, const DvmG& g) {
   const int nd = d.n_dirs;
   c = DvmG32{};
+  auto split = [](double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+  };
   for (int k = 0; k < 5; ++k) {
-    c.speed[k] = d.speeds[k];
-    c.half_v2[k] = 0.5 * d.speeds[k] * d.speeds[k];
+    split(d.speeds[k], c.sph[k], c.spl[k]);
+    split(g.half_v2[k], c.hvh[k], c.hvl[k]);
+    for (int n = 0; n < 4; ++n) split(g.Fc[k][n], c.Fch[k][n], c.Fcl[k][n]);
   }
-  c.dv23 = d.speeds[3] - d.speeds[2];
-  c.dh23 = c.half_v2[3] - c.half_v2[2];
+  split(d.speeds[3] - d.speeds[2], c.dv23h, c.dv23l);
+  split(g.half_v2[3] - g.half_v2[2], c.dh23h, c.dh23l);
+  split(g.B0, c.B0h, c.B0l);
   for (int i = 0; i < nd / 2; ++i) {
     const double phi = 2.0 * M_PI * i / nd;
     const double u[2] = {std::cos(phi), std::sin(phi)};

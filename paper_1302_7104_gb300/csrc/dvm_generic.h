@@ -9,14 +9,17 @@ namespace pclb {
 
 constexpr int kMaxPairsG = kMaxQ / 8;   // N_i / 2 <= 12 opposite-direction pairs per shell
 
+// Float-float constants are pairs (h, l) with h + l the double value.
 struct DvmG32 {
   float vx[kMaxQ], vy[kMaxQ];                  // v_q rounded to float
-  float cxh[kMaxPairsG], cxl[kMaxPairsG];      // unit vector of direction i < N_i / 2 (Eq. 2) as
-  float cyh[kMaxPairsG], cyl[kMaxPairsG];      //   float-float pairs (hi, lo)
-  double speed[5], half_v2[5];                 // v_k and v_k^2 / 2
-  double dv23, dh23;                           // v_3 - v_2 and (v_3^2 - v_2^2) / 2
+  float cxh[kMaxPairsG], cxl[kMaxPairsG];      // unit vector of direction i < N_i / 2 (Eq. 2)
+  float cyh[kMaxPairsG], cyl[kMaxPairsG];
+  float sph[5], spl[5], hvh[5], hvl[5];        // v_k and v_k^2 / 2
+  float dv23h, dv23l, dh23h, dh23l;            // v_3 - v_2 and (v_3^2 - v_2^2) / 2
+  float Fch[5][4], Fcl[5][4];                  // F_k(E) = sum_n Fc[k][n-1] E^n (Eq. 11a)
+  float B0h, B0l;                              // F_0 = 1 - B0 sum_k F_k (Eq. 11b)
 };
 
-void fill_dvm_generic32(DvmG32& c, const pclb_dvm& d);
+void fill_dvm_generic32(DvmG32& c, const pclb_dvm& d, const DvmG& g);
 
 }  // namespace pclb

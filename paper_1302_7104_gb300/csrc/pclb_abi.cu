@@ -791,7 +791,7 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
     fill_dvm(ctx->dvm64, *dvm, *grid);
   } else {
     fill_dvm_generic(ctx->dvmg, *dvm, *grid);
-    fill_dvm_generic32(ctx->dvmg32, *dvm);
+    fill_dvm_generic32(ctx->dvmg32, *dvm, ctx->dvmg);
   }
 
   struct Up { size_t off; const void* src; size_t n; } ups[] = {

@@ -78,3 +78,31 @@ def test_sector_grid_and_scheme():
         got = g.run_host(*ins, 2, [torch.empty_like(x).pin_memory() for x in ins])
         for a, b in zip(got, want):
             assert torch.equal(a, b)
+
+
+def test_nonphysical_input_is_flagged():
+    """A row with rho <= 0 inside a middle slab: the pipelined call completes
+    and the status word reports the non-physical state."""
+    n_r, n_theta = CASES[0]
+    w = I.random_smooth(n_r, n_theta, seed=54)
+    ins = _pinned(w, torch.float32)
+    ins[0][20, 100:110] = -1.0          # row 20 lies in the second of the four slabs
+    outs = [torch.empty_like(x).pin_memory() for x in ins]
+    with P.PCLB(w, precision="fp32") as g:
+        g.run_host(*ins, 1, outs)
+        assert g.status_flags() & P.FLAG_NONPHYS
+
+
+def test_on_the_legacy_default_stream():
+    """A context on the legacy default stream (handle 0): the copy streams
+    are ordered against it by events only, and the results still equal the
+    device path."""
+    n_r, n_theta = CASES[0]
+    w = I.random_smooth(n_r, n_theta, seed=55)
+    ins = _pinned(w, torch.float32)
+    with P.PCLB(w, precision="fp32", stream=torch.cuda.default_stream()) as g:
+        assert g.stream.cuda_stream == 0
+        want = _device_path(g, ins, 1)
+        got = g.run_host(*ins, 1, [torch.empty_like(x).pin_memory() for x in ins])
+        for a, b in zip(got, want):
+            assert torch.equal(a, b)
