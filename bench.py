@@ -72,9 +72,9 @@ def _peaks():
 
 
 _KERNEL_SOURCES = {
-    "fp32": ("paper_1302_7104_gb300/csrc/step_kernel_f32.cu", "paper_1302_7104_gb300/csrc/f32_state.cuh",
-             "paper_1302_7104_gb300/csrc/f32x2.cuh", "paper_1302_7104_gb300/csrc/device_common.cuh",
-             "paper_1302_7104_gb300/csrc/pclb_internal.h"),
+    "fp32": ("paper_1302_7104_gb300/csrc/step_kernel_f32.cu", "paper_1302_7104_gb300/csrc/f32_eq2.cuh",
+             "paper_1302_7104_gb300/csrc/f32_state.cuh", "paper_1302_7104_gb300/csrc/f32x2.cuh",
+             "paper_1302_7104_gb300/csrc/device_common.cuh", "paper_1302_7104_gb300/csrc/pclb_internal.h"),
     "fp64": ("paper_1302_7104_gb300/csrc/step_kernel.cu", "paper_1302_7104_gb300/csrc/ghost_cols.cuh",
              "paper_1302_7104_gb300/csrc/device_common.cuh", "paper_1302_7104_gb300/csrc/pclb_internal.h"),
 }

@@ -6,6 +6,7 @@
 #include <float.h>
 
 #include "device_common.cuh"
+#include "f32_eq2.cuh"
 #include "f32_state.cuh"
 #include "pclb_internal.h"
 
@@ -47,36 +48,65 @@ __global__ void set_state_kernel(T* __restrict__ f, const T* __restrict__ rho, c
 }
 
 
-// FP32 path: the same float-float node state and equilibrium as the step.
-__global__ void set_state_f32_kernel(float* __restrict__ f, const float* __restrict__ rho,
-                                     const float* __restrict__ u_r, const float* __restrict__ u_t,
-                                     const float* __restrict__ temp, const __grid_constant__ StepParams p,
-                                     const __grid_constant__ DvmConst<float> d, int t_begin) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+// FP32 path: two radially adjacent nodes per thread in packed FP32x2
+// arithmetic, with the step's float-float equilibrium (eq2, feq_pair2) of the
+// given fields; the velocity is rotated to Cartesian components in
+// float-float (no FP64 arithmetic), values are stored in pairs.
+constexpr int kSetThreads32 = 128;   // 256 nodes of a row per block
+
+__global__ void __launch_bounds__(kSetThreads32)
+    set_state_f32_kernel(float* __restrict__ f, const float* __restrict__ rho, const float* __restrict__ u_r,
+                         const float* __restrict__ u_t, const float* __restrict__ temp,
+                         const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<float> d,
+                         int t_begin) {
+  const int r = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int t = blockIdx.y + t_begin;
   if (r >= p.n_r || t >= p.n_theta) return;
+  const bool v1 = r + 1 < p.n_r;             // the second node exists
   const size_t n = (size_t)t * p.n_r + r;
-  // the rotation to Cartesian components in float-float (GB300 runs FP64 at
-  // 1/64 of the FP32 rate, and double arithmetic here would bound the kernel)
+  auto field = [&](const float* a) { return mk2(a[n], v1 ? a[n + 1] : a[n]); };
+  const f2 R = field(rho), E = field(temp);   // E = T for gamma = 2
+  if (!(R.x > 0.f && E.x > 0.f && R.y > 0.f && E.y > 0.f)) atomicOr(p.status, PCLB_FLAG_NONPHYS);
   const float4 cs = p.cs_ff[t];
-  const ff c{cs.x, cs.y}, s{cs.z, cs.w};
-  const ff ur = ff_of(u_r[n]), ut = ff_of(u_t[n]);
-  State32 st;
-  st.rho = ff_of(rho[n]);
-  st.E = ff_of(temp[n]);                      // E = T for gamma = 2
-  st.ux = ff_add(ff_mul(ur, c), ff_neg(ff_mul(ut, s)));
-  st.uy = ff_add(ff_mul(ur, s), ff_mul(ut, c));
-  if (!(rho[n] > 0.f && temp[n] > 0.f)) atomicOr(p.status, PCLB_FLAG_NONPHYS);
-  const Eq32 e = eq32(st, d);
-  store_with_ghosts<float>(f, p, d, 0, t, r, feq32(e, d, 0, 0, 1.f));
+  const ff2 c = ffc(cs.x, cs.y), s = ffc(cs.z, cs.w);
+  const ff2 ur = ff2_of(field(u_r)), ut = ff2_of(field(u_t));
+  State2 st;
+  st.rho = ff2_of(R);
+  st.E = ff2_of(E);
+  const ff2 uts = ff2_mul(ut, s);
+  st.ux = ff2_add(ff2_mul(ur, c), ff2{neg2(uts.hi), neg2(uts.lo)});
+  st.uy = ff2_add(ff2_mul(ur, s), ff2_mul(ut, c));
+  const Eq2 eq = eq2(st, d);
+
+  const size_t plane = (size_t)p.rows * p.pitch;
+  float* row = f + (size_t)(t + kGhostRows) * p.pitch + r;
+  float* lo = t >= p.n_theta - 2 ? f + (size_t)(t - (p.n_theta - 2)) * p.pitch + r : nullptr;
+  float* hi = t < 2 ? f + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r : nullptr;
+  // label q at this row, and at the azimuthal ghost rows it feeds (Eq. 40)
+  auto put = [&](int q, f2 v) {
+    auto one = [&](float* base) {
+      if (v1)
+        *reinterpret_cast<float2*>(base) = v;   // r even, pitch even: 8-byte aligned
+      else
+        base[0] = v.x;
+    };
+    one(row + (size_t)q * plane);
+    if (lo) one(lo + (size_t)d.recv_lo[q] * plane);
+    if (hi) one(hi + (size_t)d.recv_hi[q] * plane);
+  };
+  put(0, mul2(eq.w[0], eq.a0));
 #pragma unroll
-  for (int k = 1; k <= 4; ++k)
+  for (int k = 1; k <= 4; ++k) {
+    const f2 sh = bc2(d.speed[k]), sl = bc2(d.speed_lo[k]);
 #pragma unroll
     for (int i = 0; i < kHalf; ++i) {
       const int q = 1 + (k - 1) * kNDirs + i;
-      store_with_ghosts<float>(f, p, d, q, t, r, feq32(e, d, k, i, 1.f));
-      store_with_ghosts<float>(f, p, d, q + kHalf, t, r, feq32(e, d, k, i, -1.f));
+      f2 fp, fm;
+      feq_pair2(eq, sh, sl, i, eq.w[k], fp, fm);
+      put(q, fp);
+      put(q + kHalf, fm);
     }
+  }
 }
 
 __global__ void moments_f32_kernel(const float* __restrict__ f, float* rho, float* u_r, float* u_t,
@@ -199,11 +229,13 @@ cudaError_t launch_set_state(T* f, const T* rho, const T* ur, const T* ut, const
                              const StepParams& p, const DvmConst<T>& d, cudaStream_t s, int t_begin, int t_end) {
   if (t_end < 0) t_end = p.n_theta;
   if (t_begin < 0 || t_end <= t_begin) return cudaSuccess;
-  dim3 grid((p.n_r + kRowThreads - 1) / kRowThreads, t_end - t_begin);
-  if constexpr (sizeof(T) == 4)
-    set_state_f32_kernel<<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d, t_begin);
-  else
+  if constexpr (sizeof(T) == 4) {
+    const dim3 grid((p.n_r + 2 * kSetThreads32 - 1) / (2 * kSetThreads32), t_end - t_begin);
+    set_state_f32_kernel<<<grid, kSetThreads32, 0, s>>>(f, rho, ur, ut, temp, p, d, t_begin);
+  } else {
+    const dim3 grid((p.n_r + kRowThreads - 1) / kRowThreads, t_end - t_begin);
     set_state_kernel<T><<<grid, kRowThreads, 0, s>>>(f, rho, ur, ut, temp, p, d, t_begin);
+  }
   return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
+#include "f32_eq2.cuh"
 #include "f32_state.cuh"
 #include "f32x2.cuh"
 #include "pclb_internal.h"
@@ -42,11 +43,6 @@ constexpr int kGroups = 4;
 __device__ __forceinline__ int group_first(int g) { return g == 0 ? 0 : 1 + g * kNDirs; }
 __device__ __forceinline__ int group_planes(int g) { return g == 0 ? 1 + kNDirs : kNDirs; }
 constexpr uint64_t kWaitNs = 2000000000ull;
-
-// Unit vectors of the first direction of each opposite pair, i = 0..3 of the
-// octagon (Eq. 2), as float-float pairs: (1,0), (s,s), (0,1), (-s,s), s = 1/sqrt 2.
-constexpr float kS = 0.7071067690849304f;
-constexpr float kSl = 1.2101617152815436e-08f;
 
 __device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
@@ -80,12 +76,6 @@ __device__ __forceinline__ void shell_sums2(const float* f, f2& S, f2& X, f2& Xl
     }
   }
 }
-
-struct State2 {
-  ff2 rho, ux, uy, E;
-};
-
-__device__ __forceinline__ ff2 ffc(float hi, float lo) { return ff2{bc2(hi), bc2(lo)}; }
 
 // Moments (Eqs. 3-5) and temperature recovery of the two nodes.  ready(g)
 // is called before plane group g (the rest plane and shell 1, then shells 2,
@@ -130,44 +120,6 @@ __device__ __forceinline__ State2 state2(const float* f, const DvmConst<float>& 
   const ff2 ke = ff2_add(ff2_mul(jx, s.ux), ff2_mul(jy, s.uy));    // |j|^2 / rho
   s.E = ff2_mul(ff2_add(e, ff2_scale(ke, -0.5f)), inv);
   return s;
-}
-
-struct Eq2 {
-  f2 w[5];                  // rho F_k(E)
-  f2 a0, a1, a1h;           // Eq. (10) polynomial coefficients
-  f2 yh[kHalf], yl[kHalf];  // c_i . u / E, float-float
-};
-
-__device__ __forceinline__ Eq2 eq2(const State2& s, const DvmConst<float>& d) {
-  Eq2 q;
-  ff2 sum = ff2_of(bc2(0.f));
-#pragma unroll
-  for (int k = 1; k <= 4; ++k) {
-    ff2 a = ffc(d.Fc[k][3], d.Fc_lo[k][3]);
-#pragma unroll
-    for (int n = 2; n >= 0; --n) a = ff2_mul_add(a, s.E, ffc(d.Fc[k][n], d.Fc_lo[k][n]));
-    a = ff2_mul(a, s.E);                               // F_k(E)
-    sum = ff2_add(sum, a);
-    q.w[k] = ff2_round(ff2_mul(s.rho, a));
-  }
-  const ff2 f0 = ff2_add(ff2_of(bc2(1.f)), ff2_mul(ff2_of(bc2(-d.B0)), sum));   // F_0
-  q.w[0] = ff2_round(ff2_mul(s.rho, f0));
-  const ff2 invE = ff2_recip(s.E);
-  const ff2 uxE = ff2_mul(s.ux, invE), uyE = ff2_mul(s.uy, invE);
-  const ff2 u2E = ff2_add(ff2_mul(s.ux, uxE), ff2_mul(s.uy, uyE));   // u^2 / E
-  const ff2 a1 = ff2_add(ff2_of(bc2(1.f)), ff2_scale(u2E, -0.5f));
-  const ff2 a0 = ff2_add(a1, ff2_scale(ff2_mul(u2E, u2E), 0.125f));
-  q.a1 = ff2_round(a1);
-  q.a0 = ff2_round(a0);
-  q.a1h = mul2(bc2(0.5f), q.a1);
-  const ff2 sq = ffc(kS, kSl);
-  const ff2 y1 = ff2_mul(sq, ff2_add(uxE, uyE));
-  const ff2 y3 = ff2_mul(sq, ff2_add(uyE, ff2{neg2(uxE.hi), neg2(uxE.lo)}));
-  q.yh[0] = uxE.hi; q.yl[0] = uxE.lo;
-  q.yh[1] = y1.hi;  q.yl[1] = y1.lo;
-  q.yh[2] = uyE.hi; q.yl[2] = uyE.lo;
-  q.yh[3] = y3.hi;  q.yl[3] = y3.lo;
-  return q;
 }
 
 // Ghost columns of one wall for tile row `row` (window row index), Sec. II C 1.
@@ -421,13 +373,10 @@ __global__ void __launch_bounds__(kStepThreads32, kCtasPerSm32)
       const f2 nar = bc2(-tb.x), nkr = bc2(-tb.y);
       const f2 nat = mul2(bc2(-tb.z), invr);
       const f2 nkt = fma2(nat, nat, nat);            // -(a - a^2) with a = -nat
-      // equilibrium of the pair: P(+x) = ev + od, P(-x) = ev - od
-      const f2 x = fma2(sh, eq.yh[i], fma2(sh, eq.yl[i], mul2(sl, eq.yh[i])));
-      const f2 x2 = mul2(x, x);
-      const f2 ev = fma2(x2, fma2(x2, bc2(1.0f / 24.0f), eq.a1h), eq.a0);
-      const f2 od = mul2(x, fma2(x2, bc2(1.0f / 6.0f), eq.a1));
-      update(q, sr, st, nar, nkr, nat, nkt, mul2(wk, add2(ev, od)));
-      update(q + kHalf, -sr, -st, nar, nkr, nat, nkt, mul2(wk, sub2(ev, od)));
+      f2 fp, fm;   // equilibrium of the pair
+      feq_pair2(eq, sh, sl, i, wk, fp, fm);
+      update(q, sr, st, nar, nkr, nat, nkt, fp);
+      update(q + kHalf, -sr, -st, nar, nkr, nat, nkt, fm);
     }
   }
 }
