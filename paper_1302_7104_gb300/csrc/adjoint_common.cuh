@@ -17,6 +17,14 @@ __device__ __forceinline__ float recip_fast(float x) {
 }
 __device__ __forceinline__ double recip_fast(double x) { return recip_newton(x); }
 
+// 1/x for the cotangent factors: FP32 by the hardware approximation and one
+// Newton-Raphson step r + r (1 - x r); FP64 the correctly rounded quotient.
+__device__ __forceinline__ float recip1(float x) {
+  const float r = recip_fast(x);
+  return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+__device__ __forceinline__ double recip1(double x) { return 1.0 / x; }
+
 template <class T>
 __device__ __forceinline__ T smallest_normal();
 template <>
@@ -106,7 +114,7 @@ __device__ __forceinline__ void eq_cotangent(T rho, T ux, T uy, T E, const DvmCo
   }
   F[0] = T(1) - d.B0 * Fs;
   Fd[0] = -d.B0 * Fds;
-  const T invE = T(1) / E;
+  const T invE = recip1(E);
   const T s = (ux * ux + uy * uy) * invE;
   const T a1 = T(1) - T(0.5) * s;
   const T a0 = a1 + T(0.125) * s * s;
@@ -140,7 +148,7 @@ __device__ __forceinline__ void eq_cotangent(T rho, T ux, T uy, T E, const DvmCo
 // Cotangent in (rho, u, E) -> cotangent in m = (rho, j_x, j_y, e).
 template <class T>
 __device__ __forceinline__ void to_moment_cotangent(T rho, T ux, T uy, T E, const T G[4], T g[4]) {
-  const T inv = T(1) / rho;
+  const T inv = recip1(rho);
   g[0] = G[0] - (ux * G[1] + uy * G[2]) * inv + (T(0.5) * (ux * ux + uy * uy) - E) * G[3] * inv;
   g[1] = (G[1] - ux * G[3]) * inv;
   g[2] = (G[2] - uy * G[3]) * inv;

@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(128)
       const T* cf = d.Fc[k];
       const T F = E * (cf[0] + E * (cf[1] + E * (cf[2] + E * cf[3])));
       const T Fd = cf[0] + E * (T(2) * cf[1] + E * (T(3) * cf[2] + E * T(4) * cf[3]));
-      const T invE = T(1) / E;
+      const T invE = recip1(E);
       const T s = (ux * ux + uy * uy) * invE;
       const T a1 = T(1) - T(0.5) * s;
       const T a0 = a1 + T(0.125) * s * s;
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(128)
   for (int l = 0; l < 2; ++l) {
     // G of eq_cotangent at the ghost state (the rest velocity returns nothing)
     const T rho = (T)grho[l], E = (T)gE[l], ux = gux[l], uy = guy[l];
-    const T invE = T(1) / E;
+    const T invE = recip1(E);
     const T s = (ux * ux + uy * uy) * invE;
     Gl[l][0] = c[l][0];
     Gl[l][1] = rho * (c[l][1] + T(2) * ux * c[l][3]) * invE;
