@@ -106,3 +106,21 @@ def test_on_the_legacy_default_stream():
         got = g.run_host(*ins, 1, [torch.empty_like(x).pin_memory() for x in ins])
         for a, b in zip(got, want):
             assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("n_r,n_theta,n_dirs", [(3, 2, 8), (37, 17, 8), (40, 24, 16)])
+def test_small_grids_and_the_generic_set(prec, n_r, n_theta, n_dirs):
+    """One slab whose stencil rows wrap around the seam (3 x 2), a last slab of
+    one row (37 x 17: two slabs), and N_i = 16 (page-locked buffers, which
+    take the sequential path for the generic kernels): 0 to 2 steps."""
+    w = I.random_smooth(n_r, n_theta, seed=56, n_dirs=n_dirs, n_f=n_dirs)
+    dtype = _dtype(prec)
+    ins = _pinned(w, dtype)
+    with P.PCLB(w, precision=prec) as g:
+        for n in (0, 1, 2):
+            want = _device_path(g, ins, n)
+            got = g.run_host(*ins, n, [torch.empty_like(x).pin_memory() for x in ins])
+            for a, b in zip(got, want):
+                assert torch.equal(a, b), n
+        assert g.status_flags() == 0
