@@ -1,15 +1,14 @@
 // The step and its field kernels for the larger velocity sets of Table I,
 // N_i = 16 and 24 directions per shell (Q = 65, 97): the same model (Eqs. 2-5,
 // 10-11, 19 or 18, 28 or the other convection schemes, 38-40), one thread per
-// node, stencil values read from global memory (L1/L2).  Moments, temperature
-// recovery and the equilibrium factors are formed in double; the per-velocity
-// work (equilibrium polynomial, relaxation, convection) runs in the storage
-// type.  For FP32 storage the step forms the node state and the equilibrium
-// factors without FP64 arithmetic (GB300 runs FP64 at 1/64 of the FP32 rate):
-// float shell sums with float-float unit vectors, combined, and the
-// temperature and weights evaluated, in float-float, as the tuned FP32 kernel
-// does.  These sets serve the paper's velocity-set comparison; the tuned TMA
-// kernels cover N_i = 8.
+// node, stencil values read from global memory (L1/L2).  The field kernels and
+// the FP64 step form the moments, the temperature and the equilibrium factors
+// in double.  The FP32 step does no FP64 arithmetic (GB300 runs it at 1/64 of
+// the FP32 rate): float shell sums with float-float unit vectors, combined,
+// and the temperature and weights evaluated, in float-float, as the tuned FP32
+// kernel does.  The per-velocity work (equilibrium polynomial, relaxation,
+// convection) runs in the storage type.  These sets serve the paper's
+// velocity-set comparison; the tuned TMA kernels cover N_i = 8.
 //
 // Radial ghost nodes (Sec. II C 1) are formed once per wall row by
 // gen_ghost_kernel into a small buffer [side][layer][n_theta][Q] (f = f^eq of
