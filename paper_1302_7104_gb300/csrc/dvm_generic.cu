@@ -192,12 +192,23 @@ __device__ __forceinline__ double smallest_normal_c<double>() { return DBL_MIN; 
 
 // Convection increment in upwind form from a = |C|, K = a (1 - a), the node
 // value f0, its upwind neighbours u1, u2 and (Lax-Wendroff) the downwind one d1.
+// The limiter ratio |D| / (|D| + |Dp|) takes the hardware reciprocal in FP32
+// (as the tuned kernel does) and the correctly rounded quotient in FP64.
 template <int SCH, class C>
 __device__ __forceinline__ C gen_convect(C a, C K, C f0, C u1, C u2, C d1) {
   const C D = f0 - u1, Dp = u1 - u2;
   if (SCH == PCLB_SCHEME_MWB) {
     const C den = fabs(D) + fabs(Dp);
-    const C h = den >= smallest_normal_c<C>() ? fabs(D) * (D - Dp) / den : C(0);
+    C h = C(0);
+    if (den >= smallest_normal_c<C>()) {
+      if constexpr (sizeof(C) == 4) {
+        float rden;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rden) : "f"(den));
+        h = fabsf(D) * rden * (D - Dp);
+      } else {
+        h = fabs(D) * (D - Dp) / den;
+      }
+    }
     return a * D + K * h;
   }
   if (SCH == PCLB_SCHEME_WB) return a * D + C(0.5) * K * (D - Dp);
@@ -349,18 +360,29 @@ __global__ void __launch_bounds__(kGenThreads)
   }
   if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
   const T decay = (T)p.decay;
-  // value of label q at radial index rr of row t (a ghost layer outside the grid)
-  auto fr = [&](int q, int rr) -> T {
+  // value of label q (plane fq) at radial index rr of row t (a ghost layer
+  // outside the grid)
+  auto fr = [&](const T* fq, int q, int rr) -> T {
     if (rr < 0) return ghost[((size_t)(0 * 2 + (-1 - rr)) * p.n_theta + t) * d.q + q];
     if (rr >= p.n_r) return ghost[((size_t)(1 * 2 + (rr - p.n_r)) * p.n_theta + t) * d.q + q];
-    return fn[(size_t)q * plane + (rr - r)];
+    return fq[rr - r];
   };
-  // value of label q at stored row srow + dt_rows of column r
-  auto ft = [&](int q, int dt_rows) -> T { return fn[(size_t)q * plane + (ptrdiff_t)dt_rows * p.pitch]; };
+  // value of plane fq at stored row srow + dt_rows of column r
+  const ptrdiff_t pitch = p.pitch;
+  auto ft = [&](const T* fq, int dt_rows) -> T { return fq[dt_rows * pitch]; };
+  // label q at this node and at the azimuthal ghost rows it feeds (Eq. 40)
+  T* out_row = f_out + (size_t)srow * p.pitch + r;
+  T* out_lo = t >= p.n_theta - 2 ? f_out + (size_t)(t - (p.n_theta - 2)) * p.pitch + r : nullptr;
+  T* out_hi = t < 2 ? f_out + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r : nullptr;
+  auto put = [&](int q, T v) {
+    out_row[(size_t)q * plane] = v;
+    if (out_lo) out_lo[(size_t)d.recv_lo[q] * plane] = v;
+    if (out_hi) out_hi[(size_t)d.recv_hi[q] * plane] = v;
+  };
   {
     const T f0 = fn[0];
     const T fe = e.w[0] * e.a0;
-    gen_store<T>(f_out, p, d, 0, t, r, fe + (f0 - fe) * decay);
+    put(0, fe + (f0 - fe) * decay);
   }
   const int half = d.n_dirs / 2, npairs = 2 * d.n_dirs;
   const T inv_r = (T)p.inv_r[r];
@@ -393,10 +415,12 @@ __global__ void __launch_bounds__(kGenThreads)
         gen_feq_pair<T>(e, d.vx[q1], d.vy[q1], k, fe[0], fe[1]);
       for (int L = 0; L < 2; ++L) {
         const int q = L ? q2 : q1, s_r = L ? -sr : sr, s_t = L ? -st : st;
-        const T a = fn[(size_t)q * plane];
-        const T cr = gen_convect<SCH, T>(ar, kr, a, fr(q, r + s_r), fr(q, r + 2 * s_r), lw ? fr(q, r - s_r) : T(0));
-        const T ct = gen_convect<SCH, T>(at, kt, a, ft(q, s_t), ft(q, 2 * s_t), lw ? ft(q, -s_t) : T(0));
-        gen_store<T>(f_out, p, d, q, t, r, fe[L] + (a - fe[L]) * decay - cr - ct);
+        const T* fq = fn + (size_t)q * plane;
+        const T a = fq[0];
+        const T cr = gen_convect<SCH, T>(ar, kr, a, fr(fq, q, r + s_r), fr(fq, q, r + 2 * s_r),
+                                         lw ? fr(fq, q, r - s_r) : T(0));
+        const T ct = gen_convect<SCH, T>(at, kt, a, ft(fq, s_t), ft(fq, 2 * s_t), lw ? ft(fq, -s_t) : T(0));
+        put(q, fe[L] + (a - fe[L]) * decay - cr - ct);
       }
     }
 }
