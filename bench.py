@@ -50,14 +50,21 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # ---------------------------------------------------------------------------
 # helpers
 # ---------------------------------------------------------------------------
-def _workload(name: str):
+def _workload(name: str, size: str = ""):
+    """The named workload; ``size`` = "N_rxN_theta" replaces its grid (the
+    same fields sampled on another grid, e.g. for a profile that must stay
+    small)."""
     from paper_1302_7104_gb300 import inputs as I
+    kw = {}
+    if size:
+        n_r, n_t = (int(x) for x in size.lower().split("x"))
+        kw = {"n_r": n_r, "n_theta": n_t}
     return {
-        "kh": lambda: I.kh(),
-        "rm": lambda: I.rm(),
-        "rm_adj": lambda: I.rm_adj(),
-        "shock": lambda: I.shock(),
-        "rot": lambda: I.rot(),
+        "kh": lambda: I.kh(**kw),
+        "rm": lambda: I.rm(**kw),
+        "rm_adj": lambda: I.rm_adj(**kw),
+        "shock": lambda: I.shock(**kw),
+        "rot": lambda: I.rot(**kw),
     }[name]()
 
 
@@ -108,6 +115,22 @@ def _profiled_traffic(kernel_tag: str, cells: int):
     if key not in rec:
         return None
     return float(rec[key]) * cells
+
+
+def _alu_peaks(stream) -> dict:
+    """Measured packed FP32x2 and FP64 multiply-add rates of this GPU in
+    TFLOP/s, from the benchmark's own helper library (libpclb_bench.so, built
+    beside the product library; not part of its C ABI)."""
+    import ctypes
+    from paper_1302_7104_gb300 import build as B
+    L = ctypes.CDLL(B.BENCH_LIB)
+    L.bench_alu_peaks.restype = ctypes.c_int
+    L.bench_alu_peaks.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    out = (ctypes.c_double * 2)()
+    rc = L.bench_alu_peaks(ctypes.c_void_p(stream.cuda_stream), out)
+    if rc != 0:
+        raise RuntimeError(f"bench_alu_peaks failed ({rc})")
+    return {"ffma2_tflops": out[0], "dfma_tflops": out[1]}
 
 
 class ClockSampler:
@@ -261,7 +284,7 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = _workload(args.workload)
+    w = _workload(args.workload, args.size)
     cells = w.n_r * w.n_theta
     updates = cells * Q
     hbm, peak_src = _peaks()
@@ -376,7 +399,7 @@ def run_ours(args):
         tflops = updates * FP64_FLOPS_PER_UPDATE / t64 / 1e12
         # the FP64 multiply-add rate measured on this GPU, as context for the derived peak
         try:
-            measured = P.alu_peaks(torch.cuda.current_stream(local))
+            measured = _alu_peaks(torch.cuda.current_stream(local))
         except Exception:   # context only; the derived peak stands
             measured = None
         fp64 = {"value": updates * k64 / s64, "unit": UNIT, "steps": k64, "ms_per_step": t64 * 1e3,
@@ -462,6 +485,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="kh", choices=["kh", "rm", "rm_adj", "shock", "rot"])
+    ap.add_argument("--size", default="", help="N_rxN_theta: the workload's fields on another grid")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")

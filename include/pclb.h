@@ -216,6 +216,18 @@ pclb_status pclb_moments(pclb_ctx* ctx, void* rho, void* u_r, void* u_theta, voi
  * both relaxations are supported. */
 pclb_status pclb_set_scheme(pclb_ctx* ctx, int32_t scheme, int32_t relaxation);
 
+/* How long a step kernel (pclb_step, pclb_step_graph, pclb_step_states,
+ * pclb_run_host) waits for the TMA copies of its own stencil window before
+ * it gives the tile up and sets PCLB_FLAG_TIMEOUT; the default is
+ * 2000000000 ns (2 s), the maximum 60 s.  A tile given up stores nothing;
+ * its copies still get the default limit to land before its block exits, so
+ * the context stays usable, but the state after such a step is undefined
+ * (reload it) and pclb_status_flags returns PCLB_ETIMEOUT.  A limit of 0
+ * gives every tile up without waiting, which exercises that path.  No paper
+ * counterpart: an execution detail.  Drops cached step graphs.  Errors:
+ * PCLB_EINVAL (limit above the maximum). */
+pclb_status pclb_set_wait_limit(pclb_ctx* ctx, uint64_t limit_ns);
+
 /* Non-equilibrium manifestations of the current state (Sec. IV).  At every
  * node, with c = v (plain) or c = v - u (central, u the node's velocity) in
  * polar components at the node, and w = f (moments) or w = f - f^eq
@@ -233,15 +245,6 @@ pclb_status pclb_set_scheme(pclb_ctx* ctx, int32_t scheme, int32_t relaxation);
 #define PCLB_NEQ_MSTAR 4  /* M*_m(f), central */
 #define PCLB_NEQ_DSTAR 8  /* Delta*_m = M*_m(f - f^eq) */
 pclb_status pclb_noneq(pclb_ctx* ctx, int32_t groups, void* out);
-
-/* Arithmetic throughput of the current GPU, measured (no paper counterpart:
- * the reference for the rooflines of the ALU-bound kernels).  out: host,
- * 2 doubles: [0] packed FP32x2 fused multiply-add rate, [1] FP64 fused
- * multiply-add rate, both in TFLOP/s (2 flops per multiply-add), from
- * independent multiply-add chains on every SM.  Runs on `stream` (a
- * cudaStream_t; NULL for the default stream) and synchronizes it; allocates
- * nothing.  PCLB_ECUDA on a CUDA error. */
-pclb_status pclb_alu_peaks(void* stream, double* out);
 
 /* Global integrals of the current state with the area element r dr dtheta,
  * summed in double: out[0] mass, out[1] x-momentum, out[2] y-momentum,
@@ -337,27 +340,32 @@ pclb_status pclb_set_state_vjp(pclb_ctx* ctx, const void* rho, const void* u_r, 
 /* Global integrals of a distribution, as pclb_diagnostics computes them, but
  * without a context and without allocating any device memory.  The paper has
  * no counterpart: this entry point exists for callers that cannot call
- * cudaMalloc -- code running inside a stream capture or inside an allocator's
- * own callbacks, plug-ins that own no memory pool, hosts that have handed all
- * device memory to another framework.  They pass only the input and the
- * output; the reduction's scratch is a fixed file-scope device array.
+ * cudaMalloc -- code running inside an allocator's own callbacks (which
+ * would re-enter the allocator), plug-ins that own no memory pool, hosts that
+ * have handed all device memory to another framework.  They pass only the
+ * input and the output; the reduction's scratch is a fixed file-scope device
+ * array.
  *
  * grid, dvm, prec: as for pclb_create (host, read during the call).
  * f: device, [Q][n_theta][n_r] in prec's element type, not modified.
  * out: host, 8 doubles laid out as in pclb_diagnostics.
  * stream: cudaStream_t the kernels are queued on; the call waits for it
  * (bounded wait, PCLB_ETIMEOUT) before copying the 8 results to out.
+ * On a stream that is being captured it returns PCLB_EUNSUPPORTED and
+ * queues nothing.
  *
  * Limit: n_theta <= 16384 (one 8-double partial per azimuthal row); larger
  * grids are rejected with PCLB_EINVAL and a message.  The scratch array,
  * (16384 + 1) x 8 doubles = 1 MiB, is held by every device that loads the
  * library until the process exits.  The first call on a device looks up the
- * array's device address with that device current; make that first call
- * before any stream capture.  Every call overwrites every slot it reads, so
- * nothing needs clearing, and the array keeps the last call's contents.  All
- * calls share the one array: calls that overlap on the GPU (other streams,
- * other host threads) race on it and must be serialized by the caller.
- * Allocates nothing: no cudaMalloc, cudaFree or allocating library routine. */
+ * array's device address with that device current.  Every call overwrites
+ * every slot it reads, so nothing needs clearing, and the array keeps the
+ * last call's contents.  All calls share the one array: calls that overlap
+ * on the GPU (other streams, other host threads) race on it and must be
+ * serialized by the caller.  After PCLB_ETIMEOUT the call's kernels may
+ * still be queued and will write the array later: synchronize the stream
+ * before the next call.  Allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine. */
 pclb_status pclb_diagnostics_noalloc(const pclb_grid* grid, const pclb_dvm* dvm, pclb_precision prec,
                                      const void* f, double* out, void* stream);
 

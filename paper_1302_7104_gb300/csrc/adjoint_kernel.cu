@@ -90,7 +90,6 @@ struct AdjSize {
 
 namespace {
 
-constexpr uint64_t kAdjWaitNs = 2000000000ull;
 
 template <class T>
 struct Cour {
@@ -508,7 +507,7 @@ __global__ void __launch_bounds__(AdjSize<T>::threads, AdjTile<T>::min_blocks)
     const int s = pair % S;
     const T* st = ring + s * 4 * PLANE;
     T* pb = prod + (pair & 1) * 2 * PROD;                // this pair's products: [label][...]
-    if (ok) ok = mbar_wait_bounded(&bar[s], (uint32_t)((pair / S) & 1), kAdjWaitNs);
+    if (ok) ok = mbar_wait_bounded(&bar[s], (uint32_t)((pair / S) & 1), kDefaultWaitNs);
     if (wall_tile) {
       // radial ghost columns of this pair's f planes (f = f^eq of the ghost states)
       if (fills && ok) {
@@ -625,7 +624,7 @@ __global__ void __launch_bounds__(AdjSize<T>::threads, AdjTile<T>::min_blocks)
     const int issued = brk + S < NP ? brk + S : NP;
     for (int s = 0; s < S && s < issued; ++s) {
       const int last = s + ((issued - 1 - s) / S) * S;
-      mbar_wait_bounded(&bar[s], (uint32_t)((last / S) & 1), kAdjWaitNs);
+      mbar_wait_bounded(&bar[s], (uint32_t)((last / S) & 1), kDefaultWaitNs);
     }
   }
 }

@@ -1,12 +1,14 @@
-// Arithmetic throughput of this GPU, for the rooflines of the ALU-bound
-// kernels: packed FP32x2 fused multiply-adds (FFMA2, the step's arithmetic)
-// and FP64 fused multiply-adds, each thread running eight independent chains
-// so that the pipes stay full.  The results are written into a file-scope
-// device array (no allocation); the call synchronizes its stream.
+// Measurement helper of the benchmark, not part of the library's C ABI:
+// arithmetic throughput of this GPU, for the rooflines of the ALU-bound
+// kernels -- packed FP32x2 fused multiply-adds (FFMA2, the FP32 step's
+// arithmetic) and FP64 fused multiply-adds, each thread running eight
+// independent chains so that the pipes stay full.  Built into its own
+// library (libpclb_bench.so), loaded only by the benchmark and its test.
+// Returns 0 on success, 1 for a NULL output, 3 on a CUDA error; the call
+// synchronizes its stream and allocates nothing.
 #include <cuda_runtime.h>
 
 #include "f32x2.cuh"
-#include "pclb_internal.h"
 
 namespace {
 
@@ -47,23 +49,23 @@ __global__ void __launch_bounds__(kThreads) dfma_chains(double seed) {
 
 }  // namespace
 
-extern "C" pclb_status pclb_alu_peaks(void* stream, double* out) {
-  if (!out) return PCLB_EINVAL;
+extern "C" int bench_alu_peaks(void* stream, double* out) {
+  if (!out) return 1;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int dev = 0, n_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return PCLB_ECUDA;
+    return 3;
   cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess) return PCLB_ECUDA;
+  if (cudaEventCreate(&e0) != cudaSuccess) return 3;
   if (cudaEventCreate(&e1) != cudaSuccess) {
     cudaEventDestroy(e0);
-    return PCLB_ECUDA;
+    return 3;
   }
   const int blocks = 8 * n_sm;   // 8 CTAs of 256 threads per SM
   const double threads = (double)blocks * kThreads;
-  pclb_status st = PCLB_OK;
-  for (int k = 0; k < 2 && st == PCLB_OK; ++k) {
+  int st = 0;
+  for (int k = 0; k < 2 && st == 0; ++k) {
     float best = 1e30f;
     for (int rep = 0; rep < 4; ++rep) {   // the first launch warms up
       cudaEventRecord(e0, s);
@@ -73,7 +75,7 @@ extern "C" pclb_status pclb_alu_peaks(void* stream, double* out) {
         dfma_chains<<<blocks, kThreads, 0, s>>>(1.0 + rep);
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
-        st = PCLB_ECUDA;
+        st = 3;
         break;
       }
       float ms = 0.f;

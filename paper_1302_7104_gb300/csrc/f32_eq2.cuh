@@ -60,14 +60,16 @@ __device__ __forceinline__ Eq2 eq2(const State2& s, const DvmConst<float>& d) {
 
 // Equilibrium (Eq. 10) of direction i of a shell (speed sh + sl, weight wk =
 // rho F_k) and of its opposite direction: with x = v.u/E, P(+x) = ev + od and
-// P(-x) = ev - od share the even and odd parts of the polynomial.
+// P(-x) = ev - od share the even and odd parts of the polynomial; the pair
+// is formed as w ev +- w od with fused multiply-adds.
 __device__ __forceinline__ void feq_pair2(const Eq2& eq, f2 sh, f2 sl, int i, f2 wk, f2& fp, f2& fm) {
   const f2 x = fma2(sh, eq.yh[i], fma2(sh, eq.yl[i], mul2(sl, eq.yh[i])));
   const f2 x2 = mul2(x, x);
   const f2 ev = fma2(x2, fma2(x2, bc2(1.0f / 24.0f), eq.a1h), eq.a0);
   const f2 od = mul2(x, fma2(x2, bc2(1.0f / 6.0f), eq.a1));
-  fp = mul2(wk, add2(ev, od));
-  fm = mul2(wk, sub2(ev, od));
+  const f2 wev = mul2(wk, ev);                     // w (ev +- od) with one rounding after w ev
+  fp = fma2(wk, od, wev);
+  fm = fma2(neg2(wk), od, wev);
 }
 
 }  // namespace pclb

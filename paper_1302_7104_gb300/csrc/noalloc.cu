@@ -1,13 +1,15 @@
 // pclb_diagnostics_noalloc: the global integrals of a distribution computed
 // without allocating any device memory.
 //
-// Some callers cannot call cudaMalloc at all: code that runs inside a stream
-// capture, a custom allocator's own callbacks, a driver plug-in that owns no
-// memory pool, or a host that has handed every byte of the GPU to another
-// framework.  They still hold the distribution in device memory and want its
-// mass, momentum and energy.  This variant of the diagnostics reduction keeps
-// its per-row partial sums in a fixed, file-scope device array instead of a
-// workspace, so the call needs nothing but its input, its output and a stream.
+// Some callers cannot call cudaMalloc at all: a custom allocator's own
+// callbacks (which would re-enter the allocator), a driver or framework
+// plug-in that owns no memory pool, or a host that has handed every byte of
+// the GPU to another framework.  They still hold the distribution in device
+// memory and want its mass, momentum and energy.  This variant of the
+// diagnostics reduction keeps its per-row partial sums in a fixed, file-scope
+// device array instead of a workspace, so the call needs nothing but its
+// input, its output and a stream.  It waits for its stream and copies the
+// result to the host, and refuses a stream that is being captured.
 #include <cuda_runtime.h>
 #include <float.h>
 
@@ -189,12 +191,28 @@ extern "C" pclb_status pclb_diagnostics_noalloc(const pclb_grid* grid, const pcl
     set_thread_error(err);
     return PCLB_EINVAL;
   }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  {
+    // the call waits for the stream and copies to the host: a stream that
+    // is being captured is refused before anything is queued
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce != cudaSuccess) {
+      std::snprintf(err, sizeof(err), "cudaStreamIsCapturing: %s", cudaGetErrorString(ce));
+      set_thread_error(err);
+      return PCLB_ECUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) {
+      set_thread_error("pclb_diagnostics_noalloc waits for its stream and copies to the host; "
+                       "it cannot run on a stream that is being captured");
+      return PCLB_EUNSUPPORTED;
+    }
+  }
   double* scratch = nullptr;
   if ((st = scratch_for_current_device(&scratch, err, sizeof(err))) != PCLB_OK) {
     set_thread_error(err);
     return st;
   }
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = prec == PCLB_FP32 ? launch_rows<float>(f, scratch, *grid, *dvm, s)
                                     : launch_rows<double>(f, scratch, *grid, *dvm, s);
   if (e != cudaSuccess) {

@@ -775,6 +775,7 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
   sp.dt_dth = dt / dth;
   sp.decay = std::exp(-dt / tau);
   sp.scheme = PCLB_SCHEME_MWB;
+  sp.wait_ns = kDefaultWaitNs;
   sp.bc_kind[0] = bc->kind[0];
   sp.bc_kind[1] = bc->kind[1];
   sp.cos_t = reinterpret_cast<const double*>(ctx->ws + lay.cos_t);
@@ -1196,6 +1197,14 @@ pclb_status pclb_set_scheme(pclb_ctx* ctx, int32_t scheme, int32_t relaxation) {
   ctx->relaxation = relaxation;
   ctx->sp.scheme = scheme;
   ctx->sp.decay = relaxation == PCLB_RELAX_EULER ? 1.0 - ctx->dt / ctx->tau : std::exp(-ctx->dt / ctx->tau);
+  return PCLB_OK;
+}
+
+pclb_status pclb_set_wait_limit(pclb_ctx* ctx, uint64_t limit_ns) {
+  if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
+  if (limit_ns > kMaxWaitNs) return fail(ctx, PCLB_EINVAL, "limit_ns must be at most %llu", (unsigned long long)kMaxWaitNs);
+  drop_graphs(ctx);   // captured launches hold the old parameters
+  ctx->sp.wait_ns = limit_ns;
   return PCLB_OK;
 }
 

@@ -37,6 +37,13 @@ constexpr int kGhostRows = 2;       // azimuthal ghost rows stored on each side
 // Tile rows of the adjoint kernel (its window holds f and lam for all labels).
 constexpr int kAdjRows32 = 8;
 constexpr int kAdjRows64 = 8;
+// Time a kernel waits for the TMA copies of its own window (mbarrier phase)
+// before it reports PCLB_FLAG_TIMEOUT and gives the tile up; the copies of a
+// tile given up get the default limit again to land before the CTA exits.
+// The step kernels take their first wait's limit from StepParams::wait_ns
+// (pclb_set_wait_limit); every other wait uses the default.
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;   // 2 s
+constexpr uint64_t kMaxWaitNs = 60000000000ull;      // 60 s
 
 // Per-velocity constants, in the arithmetic type T of the kernel, plus the
 // double-precision ones the moment / temperature recovery uses.
@@ -96,6 +103,7 @@ struct StepParams {
   const float* inv_r_f;       // [n_r] 1 / r_i in float
   const float4* cs_ff;        // [n_theta] cos theta_i, sin theta_i as float-float pairs (hi, lo, hi, lo)
   uint32_t* status;           // device status word (PCLB_FLAG_*)
+  uint64_t wait_ns;           // a step's wait for its own window copies before it gives the tile up
 };
 
 // Workspace layout (byte offsets from the caller's base pointer).

@@ -28,7 +28,6 @@
 namespace pclb {
 
 constexpr int kPlane = kWinR * kWinT;   // elements per velocity plane in shared memory
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
 constexpr int kPairs64 = 4 * kNDirs / 2;   // pairs of opposite velocities
 constexpr int kThreads64 = 512;            // 16 warps: one node per thread
@@ -100,10 +99,14 @@ __global__ void __launch_bounds__(kThreads64, 1)
 #pragma unroll
     for (int j = 0; j < 4; ++j) tab[(pair * kTileT + rl) * 4 + j] = (T)e[j];
   }
-  if (!mbar_wait_bounded(bar, 0, kWaitLimitNs)) {
-    if (threadIdx.x == 0) atomicOr(p.status, PCLB_FLAG_TIMEOUT);
-    // give the copies one more bounded chance to land before the CTA exits
-    mbar_wait_bounded(bar, 0, kWaitLimitNs);
+  // The whole block gives the tile up if any thread's wait ran out (a block
+  // barrier follows below, so the decision must be uniform); thread 0 then
+  // gives the copies one more bounded chance to land before the block exits.
+  if (__syncthreads_or(p.wait_ns == 0 || !mbar_wait_bounded(bar, 0, p.wait_ns))) {   // 0: give up at once
+    if (threadIdx.x == 0) {
+      atomicOr(p.status, PCLB_FLAG_TIMEOUT);
+      mbar_wait_bounded(bar, 0, kDefaultWaitNs);
+    }
     return;
   }
 

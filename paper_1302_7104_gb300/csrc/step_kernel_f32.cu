@@ -17,7 +17,11 @@
 //     float-float constants, the even and odd parts of the equilibrium
 //     polynomial (Eq. 10) shared by q and q'; then per velocity the relaxation
 //     (Eq. 19) minus the MWB increments (Eq. 28) in r and theta, stored with
-//     8-byte stores, plus the azimuthal ghost rows of the seam (Eq. 40).
+//     8-byte streaming stores, plus the azimuthal ghost rows of the seam
+//     (Eq. 40).  The convection increments -M_r - M_theta are summed first
+//     and added once to the relaxed value, so that they cost one rounding at
+//     the magnitude of f instead of four (this halves the FP32 path's drift
+//     from the FP64 one over long runs).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -42,7 +46,6 @@ static_assert((kPlaneF * 4) % 128 == 0 && kPlanesBytes % 16 == 0, "TMA destinati
 constexpr int kGroups = 4;
 __device__ __forceinline__ int group_first(int g) { return g == 0 ? 0 : 1 + g * kNDirs; }
 __device__ __forceinline__ int group_planes(int g) { return g == 0 ? 1 + kNDirs : kNDirs; }
-constexpr uint64_t kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
@@ -191,10 +194,10 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // Limiter part of the MWB increment of both nodes, |D| (D - Dp) / (|D| + |Dp|)
 // (0 when D = Dp = 0), Eq. (28) in upwind form.
 __device__ __forceinline__ f2 limiter2(f2 D, f2 Dp) {
-  const float den0 = fmaxf(fabsf(D.x) + fabsf(Dp.x), 1e-30f);
-  const float den1 = fmaxf(fabsf(D.y) + fabsf(Dp.y), 1e-30f);
-  const f2 t = mk2(fabsf(D.x) * rcp_approx(den0), fabsf(D.y) * rcp_approx(den1));
-  return mul2(t, sub2(D, Dp));
+  const f2 aD = abs2(D);
+  const f2 den = add2(aD, abs2(Dp));
+  const f2 rr = mk2(rcp_approx(fmaxf(den.x, 1e-30f)), rcp_approx(fmaxf(den.y, 1e-30f)));
+  return mul2(mul2(aD, rr), sub2(D, Dp));
 }
 
 }  // namespace
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(kStepThreads32, kCtasPerSm32)
   Eq2 eq;
   {
     auto ready = [&](int g) {
-      if (ok) ok = mbar_wait_bounded(&bar[g], 0, kWaitNs);
+      if (ok) ok = p.wait_ns != 0 && mbar_wait_bounded(&bar[g], 0, p.wait_ns);   // 0: give up at once
     };
     State2 s = state2(win, d, ready);
     const bool ok0 = s.rho.hi.x > 0.f && s.E.hi.x > 0.f && isfinite(s.E.hi.x) && isfinite(s.ux.hi.x) &&
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(kStepThreads32, kCtasPerSm32)
     if (__syncthreads_or(!ok)) {   // ghost columns visible; a copy that timed out stops the tile
       if (tid == 0) {
         atomicOr(p.status, PCLB_FLAG_TIMEOUT);
-        for (int g = 0; g < kGroups; ++g) mbar_wait_bounded(&bar[g], 0, kWaitNs);
+        for (int g = 0; g < kGroups; ++g) mbar_wait_bounded(&bar[g], 0, kDefaultWaitNs);
       }
       return;
     }
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(kStepThreads32, kCtasPerSm32)
     // a copy did not land in time: report it, give the copies a bounded time
     // to finish, and leave (no barrier follows in this tile)
     atomicOr(p.status, PCLB_FLAG_TIMEOUT);
-    for (int g = 0; g < kGroups; ++g) mbar_wait_bounded(&bar[g], 0, kWaitNs);
+    for (int g = 0; g < kGroups; ++g) mbar_wait_bounded(&bar[g], 0, kDefaultWaitNs);
     return;
   }
 
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(kStepThreads32, kCtasPerSm32)
   const bool plain_tile = r0 + kTileR <= p.n_r && t0 >= 2 && t0 + kTileT32 <= p.n_theta - 2;
   auto store = [&](int q, f2 o) {
     if (plain_tile) {
-      *reinterpret_cast<float2*>(out_row + (size_t)q * plane_out) = o;
+      __stcs(reinterpret_cast<float2*>(out_row + (size_t)q * plane_out), o);   // not read again before the next step
     } else if (v1) {
       *reinterpret_cast<float2*>(out_row + (size_t)q * plane_out) = o;
       if (lo_ghost) *reinterpret_cast<float2*>(out_lo + (size_t)d.recv_lo[q] * plane_out) = o;
@@ -334,26 +337,27 @@ __global__ void __launch_bounds__(kStepThreads32, kCtasPerSm32)
     const f2 T2 = ld2(w + 2 * st * kWinR);
     const f2 u1 = sr < 0 ? mk2(S.y, C.x) : mk2(C.y, S.x);   // first upwind neighbours
     const f2 Dr = sub2(C, u1), Dt = sub2(C, T1);
-    f2 o = fma2(sub2(C, fe), decay, fe);
-    o = fma2(nar, Dr, o);
-    o = fma2(nat, Dt, o);
+    // the convection increments summed first (small), then added once to
+    // the relaxed value (one rounding at the magnitude of f for them)
+    f2 dc = mul2(nar, Dr);
+    dc = fma2(nat, Dt, dc);
     if constexpr (SCH == PCLB_SCHEME_MWB) {
-      o = fma2(nkr, limiter2(Dr, sub2(u1, S)), o);
-      o = fma2(nkt, limiter2(Dt, sub2(T1, T2)), o);
+      dc = fma2(nkr, limiter2(Dr, sub2(u1, S)), dc);
+      dc = fma2(nkt, limiter2(Dt, sub2(T1, T2)), dc);
     } else if constexpr (SCH == PCLB_SCHEME_WB) {
-      o = fma2(mul2(bc2(0.5f), nkr), sub2(Dr, sub2(u1, S)), o);
-      o = fma2(mul2(bc2(0.5f), nkt), sub2(Dt, sub2(T1, T2)), o);
+      dc = fma2(mul2(bc2(0.5f), nkr), sub2(Dr, sub2(u1, S)), dc);
+      dc = fma2(mul2(bc2(0.5f), nkt), sub2(Dt, sub2(T1, T2)), dc);
     } else if constexpr (SCH == PCLB_SCHEME_UPWIND2) {
-      o = fma2(mul2(bc2(0.5f), nar), sub2(Dr, sub2(u1, S)), o);
-      o = fma2(mul2(bc2(0.5f), nat), sub2(Dt, sub2(T1, T2)), o);
+      dc = fma2(mul2(bc2(0.5f), nar), sub2(Dr, sub2(u1, S)), dc);
+      dc = fma2(mul2(bc2(0.5f), nat), sub2(Dt, sub2(T1, T2)), dc);
     } else {
       const f2 X = ld2(w - 2 * sr);               // the pair on the downwind side
       const f2 d1 = sr < 0 ? mk2(C.y, X.x) : mk2(X.y, C.x);   // first downwind neighbours
       const f2 Td = ld2(w - st * kWinR);
-      o = fma2(mul2(bc2(0.5f), nkr), sub2(sub2(d1, C), Dr), o);
-      o = fma2(mul2(bc2(0.5f), nkt), sub2(sub2(Td, C), Dt), o);
+      dc = fma2(mul2(bc2(0.5f), nkr), sub2(sub2(d1, C), Dr), dc);
+      dc = fma2(mul2(bc2(0.5f), nkt), sub2(sub2(Td, C), Dt), dc);
     }
-    store(q, o);
+    store(q, add2(fma2(sub2(C, fe), decay, fe), dc));
   };
 
   // Shells run as a loop (keeps the hot body small for the instruction

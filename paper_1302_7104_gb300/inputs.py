@@ -327,10 +327,12 @@ def rm_background(R, TH, amp: float):
 
 def rm_adj(n_r: int = 512, n_theta: int = 1024, steps: int = 2000, cfl: float = STABLE_CFL,
            tau: float = 1e-5, a: Optional[np.ndarray] = None, seed: int = 20130228,
-           r_in: float = 1.0, r_out: float = 3.0, background: float = 0.0) -> Workload:
+           r_in: float = 1.0, r_out: float = 3.0, background: float = 0.0,
+           dt: Optional[float] = None) -> Workload:
     """RM with interface r = 2 + sum_k a_k cos(k theta), k = 1..16.  A nonzero
     ``background`` multiplies rho and T by rm_background (pressure changes
-    slightly; used only by gradient checks)."""
+    slightly; used only by gradient checks).  ``dt`` overrides the CFL-based
+    time step (the paper's RM runs use dt = tau)."""
     if a is None:
         a = rm_amplitudes(seed)
     R, TH = _mesh(n_r, n_theta, r_in, r_out)
@@ -342,7 +344,9 @@ def rm_adj(n_r: int = 512, n_theta: int = 1024, steps: int = 2000, cfl: float = 
         m = rm_background(R, TH, background)
         rho = rho * m
         T = T * m
-    return Workload("rm_adj", n_r, n_theta, r_in, r_out, tau, dt_from_cfl(cfl, n_r, n_theta, r_in, r_out),
+    if dt is None:
+        dt = dt_from_cfl(cfl, n_r, n_theta, r_in, r_out)
+    return Workload("rm_adj", n_r, n_theta, r_in, r_out, tau, dt,
                     steps, rho, u_r, u_th, T, bc_kind=(BC_EXTRAP, BC_DIRICHLET),
                     bc_values=_rm_bc(n_theta, post), smooth=False,
                     extra={"a": np.asarray(a, dtype=np.float64), "seed": seed, "post_shock": post,

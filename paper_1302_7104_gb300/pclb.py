@@ -69,10 +69,10 @@ _SIGS = {
     "pclb_step": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "pclb_step_graph": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "pclb_step_states": (ctypes.c_int, [_vp, _vp, _vp]),
-    "pclb_alu_peaks": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "pclb_moments": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "pclb_noneq": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
     "pclb_set_scheme": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    "pclb_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_uint64]),
     "pclb_diagnostics": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "pclb_status_flags": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int32]),
     "pclb_sync": (ctypes.c_int, [_vp, ctypes.c_int32]),
@@ -179,6 +179,11 @@ class PCLB:
     def set_scheme(self, scheme: int = 0, relaxation: int = 0):
         """Convection scheme (SCHEME_*) and relaxation (RELAX_*) of later steps."""
         _check(lib().pclb_set_scheme(self.ctx, int(scheme), int(relaxation)), self.ctx)
+        return self
+
+    def set_wait_limit(self, limit_ns: int = 2_000_000_000):
+        """Limit of a step kernel's wait for its own window copies (pclb_set_wait_limit)."""
+        _check(lib().pclb_set_wait_limit(self.ctx, int(limit_ns)), self.ctx)
         return self
 
     # -- lifetime ----------------------------------------------------------
@@ -367,17 +372,6 @@ class PCLB:
         _check(lib().pclb_run_host(self.ctx, *[_vp(t.data_ptr()) for t in ins], int(n),
                                    *[_vp(_ptr(t)) for t in outs]), self.ctx)
         return tuple(outs)
-
-
-def alu_peaks(stream=None) -> dict:
-    """Measured arithmetic throughput of the current GPU (pclb_alu_peaks):
-    packed FP32x2 and FP64 fused multiply-add rates in TFLOP/s."""
-    torch = _torch()
-    if stream is None:
-        stream = torch.cuda.current_stream()
-    out = (ctypes.c_double * 2)()
-    _check(lib().pclb_alu_peaks(_vp(stream.cuda_stream), out))
-    return {"ffma2_tflops": out[0], "dfma_tflops": out[1]}
 
 
 def diagnostics_noalloc(w, f, precision: str = "fp32", stream=None) -> np.ndarray:

@@ -2,7 +2,9 @@
 
 FP64: the adjoint step equals the oracle's vector-Jacobian product (built
 column by column from forward-mode derivatives of the oracle's step) within
-1e-12 of its largest entry; on larger grids the transpose identity
+1e-12 of its largest entry; on multi-tile grids (ragged tails, walls of every
+kind, sectors) every entry equals the oracle's entry computed on its own
+(``oracle.adjoint_entries``), and the transpose identity
 <lam, J df> = <J^T lam, df> holds against the oracle's JVP.  FP32: within
 1e-4.  The field VJPs satisfy the same identity against the oracle's JVPs.
 """
@@ -51,6 +53,55 @@ def test_fp64_adjoint_step_equals_oracle_vjp(name):
         got = g.adjoint_step(_dev(f, torch.float64), _dev(lam, torch.float64)).cpu().numpy()
     err = np.max(np.abs(got - want)) / np.max(np.abs(want))
     assert err <= 1e-12, err
+
+
+# Multi-tile grids for entry-by-entry comparison: the adjoint kernel's tiles
+# are 32 (r) x 8 (theta), so these span several tiles with ragged tails in
+# both directions, the seam rows, both walls of every kind and sectors.
+MULTI = {
+    "dirichlet_wall_67x35": lambda: I.random_smooth(67, 35, seed=41, bc_kind=(I.BC_DIRICHLET, I.BC_WALL)),
+    "wall_extrap_sector3_67x35": lambda: I.random_smooth(67, 35, seed=42, n_f=3,
+                                                         bc_kind=(I.BC_WALL, I.BC_EXTRAP)),
+    "extrap_99x21": lambda: I.random_smooth(99, 21, seed=43),
+    "extrap_dirichlet_sector1_70x17": lambda: I.random_smooth(70, 17, seed=44, n_f=1,
+                                                              bc_kind=(I.BC_EXTRAP, I.BC_DIRICHLET)),
+    "rm_noisy_96x40": lambda: I.rm(n_r=96, n_theta=40),
+}
+
+
+def _all_entries(shape):
+    q, t, r = np.meshgrid(*(np.arange(n) for n in shape), indexing="ij")
+    return q.ravel(), t.ravel(), r.ravel()
+
+
+@pytest.mark.parametrize("name", list(MULTI))
+def test_fp64_adjoint_equals_oracle_entry_by_entry_on_multi_tile_grids(name):
+    """Every entry of lam^n -- tile edges, seam rows, wall columns, ragged
+    tails -- against the oracle's entry from forward-mode sweeps over the
+    nodes that read it, within 1e-12 of max|lam^n|."""
+    w = MULTI[name]()
+    f = _state(w, seed=51)
+    lam = np.random.default_rng(52).normal(size=f.shape)
+    with P.PCLB(w, precision="fp64") as g:
+        got = g.adjoint_step(_dev(f, torch.float64), _dev(lam, torch.float64)).cpu().numpy()
+        assert g.status_flags() == 0
+    q, t, r = _all_entries(f.shape)
+    want = O.adjoint_entries(w, f, lam, q, t, r).reshape(f.shape)
+    err = np.abs(got - want) / np.max(np.abs(want))
+    assert err.max() <= 1e-12, (err.max(), np.unravel_index(np.argmax(err), err.shape))
+
+
+@pytest.mark.parametrize("name", ["dirichlet_wall_67x35", "wall_extrap_sector3_67x35"])
+def test_fp32_adjoint_close_to_oracle_entry_by_entry_on_multi_tile_grids(name):
+    w = MULTI[name]()
+    f = _state(w, seed=53).astype(np.float32).astype(np.float64)
+    lam = np.random.default_rng(54).normal(size=f.shape).astype(np.float32).astype(np.float64)
+    with P.PCLB(w, precision="fp32") as g:
+        got = g.adjoint_step(_dev(f, torch.float32), _dev(lam, torch.float32)).double().cpu().numpy()
+    q, t, r = _all_entries(f.shape)
+    want = O.adjoint_entries(w, f, lam, q, t, r).reshape(f.shape)
+    err = np.max(np.abs(got - want)) / np.max(np.abs(want))
+    assert err <= 1e-4, err
 
 
 @pytest.mark.parametrize("shape,bc", [((40, 20), (I.BC_EXTRAP, I.BC_EXTRAP)),

@@ -3,6 +3,8 @@ contexts on one stream, a large grid ragged in both directions (sampled nodes
 against the oracle), a sector of one period with walls on a ragged grid, and
 forward and adjoint steps interleaved on the caller's stream (the adjoint's
 wall work runs on a side stream joined back before the next launch)."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -116,10 +118,12 @@ def test_forward_and_adjoint_interleave_on_the_stream():
 
 
 def test_alu_peaks_are_plausible():
-    """pclb_alu_peaks: packed FP32 and FP64 multiply-add rates within a factor
-    of a few of GB300's nominal rates (152 SMs at up to 2.07 GHz: 80 and
-    1.26 TFLOP/s)."""
-    pk = P.alu_peaks()
+    """The benchmark's multiply-add rate helper: packed FP32 and FP64 rates
+    within a factor of a few of GB300's nominal rates (152 SMs at up to
+    2.07 GHz: 80 and 1.26 TFLOP/s)."""
+    import bench
+    P.lib()   # builds the product and the benchmark helper library
+    pk = bench._alu_peaks(torch.cuda.current_stream())
     assert 20.0 < pk["ffma2_tflops"] < 120.0
     assert 0.3 < pk["dfma_tflops"] < 3.0
 
@@ -158,4 +162,45 @@ def test_misaligned_pointers_are_refused_before_any_launch():
         assert P.lib().pclb_get_f(g.ctx, ctypes.c_void_p(f.data_ptr() + 2)) == 1
         st = g.new_state()
         assert P.lib().pclb_adjoint_state(g.ctx, ctypes.c_void_p(st.data_ptr() + 8)) in (1, 8)
+        assert g.status_flags() == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_window_wait_that_runs_out_reports_timeout(prec):
+    """A step whose wait for its own window copies runs out (limit 0: every
+    tile is given up without waiting) sets PCLB_FLAG_TIMEOUT;
+    pclb_status_flags returns PCLB_ETIMEOUT; the context stays usable: with
+    the default limit restored, a reloaded state steps exactly as a fresh
+    context does.  Nothing faults or hangs: the copies of a tile given up get
+    the default limit to land before its block exits."""
+    w = I.kh(n_r=1024, n_theta=512)
+    dtype = torch.float32 if prec == "fp32" else torch.float64
+    f0 = torch.as_tensor(O.set_state(w), dtype=dtype, device="cuda")
+    with P.PCLB(w, precision=prec) as g:
+        g.set_f(f0).set_wait_limit(0).step(3)
+        flags = ctypes.c_uint32()
+        code = P.lib().pclb_status_flags(g.ctx, ctypes.byref(flags), 1)
+        assert code == 5 and flags.value & P.FLAG_TIMEOUT, (code, flags.value)
+        with pytest.raises(P.PCLBError):
+            g.set_wait_limit(61_000_000_000)          # above the maximum
+        g.set_wait_limit().set_f(f0).step(2)
+        assert g.status_flags() == 0
+        got = g.get_f()
+    with P.PCLB(w, precision=prec) as h:
+        want = h.set_f(f0).step(2).get_f()
+    assert torch.equal(got, want)
+
+
+def test_host_sync_that_runs_out_reports_timeout():
+    """pclb_sync with a limit shorter than the queued work returns
+    PCLB_ETIMEOUT and leaves the work running; a second sync with the default
+    limit waits it out."""
+    w = I.kh(n_r=4096, n_theta=4096)
+    with P.PCLB(w, precision="fp32") as g:
+        g.set_state()
+        g.sync()
+        g.step(30)                                      # about 35 ms of work
+        assert P.lib().pclb_sync(g.ctx, 1) == 5         # PCLB_ETIMEOUT after 1 ms
+        assert "did not finish" in P.lib().pclb_last_error(g.ctx).decode()
+        g.sync()
         assert g.status_flags() == 0
