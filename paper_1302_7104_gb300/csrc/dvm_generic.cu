@@ -486,6 +486,12 @@ cudaError_t gen_step_scheme(const T* f, T* f_out, T* ghost, const StepParams& p,
 }  // namespace
 
 template <class T>
+cudaError_t gen_launch_ghost(const T* f, T* ghost, const StepParams& p, const DvmG& d, cudaStream_t s) {
+  gen_ghost_kernel<T><<<dim3((p.n_theta + kGenThreads - 1) / kGenThreads, 2), kGenThreads, 0, s>>>(f, ghost, p, d);
+  return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t gen_launch_set_state(T* f, const T* rho, const T* ur, const T* ut, const T* temp, const StepParams& p,
                                  const DvmG& d, cudaStream_t s) {
   gen_set_state_kernel<T><<<dim3((p.n_r + kGenThreads - 1) / kGenThreads, p.n_theta), kGenThreads, 0, s>>>(
@@ -570,6 +576,7 @@ cudaError_t gen_launch_diagnostics(const T* f, double* partials, double* out, co
 }
 
 #define PCLB_GEN_INSTANTIATE(T)                                                                               \
+  template cudaError_t gen_launch_ghost<T>(const T*, T*, const StepParams&, const DvmG&, cudaStream_t);        \
   template cudaError_t gen_launch_set_state<T>(T*, const T*, const T*, const T*, const T*, const StepParams&, \
                                                const DvmG&, cudaStream_t);                                    \
   template cudaError_t gen_launch_moments<T>(const T*, T*, T*, T*, T*, const StepParams&, const DvmG&,        \

@@ -295,7 +295,7 @@ pclb_status encode_map(pclb_ctx* ctx, const void* base, int box_rows, CUtensorMa
   if (!enc) return fail(ctx, PCLB_ECUDA, "cuTensorMapEncodeTiled is not available from the CUDA driver");
   if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return fail(ctx, PCLB_EINVAL, "state buffer not 16-byte aligned");
   const size_t es = elem_size(ctx->prec);
-  cuuint64_t dims[3] = {(cuuint64_t)ctx->grid.n_r, (cuuint64_t)ctx->sp.rows, (cuuint64_t)kQ};
+  cuuint64_t dims[3] = {(cuuint64_t)ctx->grid.n_r, (cuuint64_t)ctx->sp.rows, (cuuint64_t)(1 + 4 * ctx->dvm.n_dirs)};
   cuuint64_t strides[2] = {(cuuint64_t)ctx->sp.pitch * es, (cuuint64_t)ctx->sp.pitch * ctx->sp.rows * es};
   cuuint32_t box[3] = {(cuuint32_t)kWinR, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
@@ -386,7 +386,12 @@ pclb_status do_step(pclb_ctx* ctx, int n) {
   for (int i = 0; i < n; ++i) {
     const int src = ctx->cur, dst = 1 - ctx->cur;
     cudaError_t e;
-    if (generic(ctx))
+    if (generic(ctx) && sizeof(T) == 4)
+      e = gen_tiled_step_f32(&ctx->tmap[src], reinterpret_cast<const float*>(fbuf<T>(ctx, src)),
+                             reinterpret_cast<float*>(fbuf<T>(ctx, dst)),
+                             reinterpret_cast<float*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg,
+                             dvmg32(ctx), ctx->stream);
+    else if (generic(ctx))
       e = gen_launch_step<T>(fbuf<T>(ctx, src), fbuf<T>(ctx, dst), reinterpret_cast<T*>(ctx->ws + ctx->lay.gen_ghost),
                              ctx->sp, ctx->dvmg, dvmg32(ctx), ctx->stream);
     else if constexpr (sizeof(T) == 4)
@@ -923,14 +928,17 @@ pclb_status pclb_step_states(pclb_ctx* ctx, const void* f_from, void* f_to) {
   if ((reinterpret_cast<uintptr_t>(f_from) | reinterpret_cast<uintptr_t>(f_to)) % 16 != 0)
     return fail(ctx, PCLB_EINVAL, "state buffers must be 16-byte aligned");
   cudaError_t e;
-  if (generic(ctx)) {
-    e = ctx->prec == PCLB_FP32
-            ? gen_launch_step<float>((const float*)f_from, (float*)f_to,
-                                     reinterpret_cast<float*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg,
-                                     dvmg32(ctx), ctx->stream)
-            : gen_launch_step<double>((const double*)f_from, (double*)f_to,
-                                      reinterpret_cast<double*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg,
-                                      dvmg32(ctx), ctx->stream);
+  if (generic(ctx) && ctx->prec == PCLB_FP32) {
+    CUtensorMap map;
+    pclb_status st = encode_map(ctx, f_from, kTileT32 + 4, &map);
+    if (st != PCLB_OK) return st;
+    e = gen_tiled_step_f32(&map, (const float*)f_from, (float*)f_to,
+                           reinterpret_cast<float*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg, dvmg32(ctx),
+                           ctx->stream);
+  } else if (generic(ctx)) {
+    e = gen_launch_step<double>((const double*)f_from, (double*)f_to,
+                                reinterpret_cast<double*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg,
+                                dvmg32(ctx), ctx->stream);
   } else {
     CUtensorMap map;
     pclb_status st = encode_map(ctx, f_from, ctx->prec == PCLB_FP32 ? kTileT32 + 4 : kWinT, &map);
