@@ -477,19 +477,14 @@ __global__ void gen_diag_final_kernel(const double* partials, int n_blocks, doub
 template <class T, int SCH>
 cudaError_t gen_step_scheme(const T* f, T* f_out, T* ghost, const StepParams& p, const DvmG& d, const DvmG32& d32,
                             cudaStream_t s) {
-  gen_ghost_kernel<T><<<dim3((p.n_theta + kGenThreads - 1) / kGenThreads, 2), kGenThreads, 0, s>>>(f, ghost, p, d);
+  // one thread per wall row, in warps, so that the rows spread over the SMs
+  gen_ghost_kernel<T><<<dim3((p.n_theta + 31) / 32, 2), 32, 0, s>>>(f, ghost, p, d);
   gen_step_kernel<T, SCH><<<dim3((p.n_r + kGenThreads - 1) / kGenThreads, p.n_theta), kGenThreads, 0, s>>>(
       f, f_out, ghost, p, d, d32);
   return cudaGetLastError();
 }
 
 }  // namespace
-
-template <class T>
-cudaError_t gen_launch_ghost(const T* f, T* ghost, const StepParams& p, const DvmG& d, cudaStream_t s) {
-  gen_ghost_kernel<T><<<dim3((p.n_theta + kGenThreads - 1) / kGenThreads, 2), kGenThreads, 0, s>>>(f, ghost, p, d);
-  return cudaGetLastError();
-}
 
 template <class T>
 cudaError_t gen_launch_set_state(T* f, const T* rho, const T* ur, const T* ut, const T* temp, const StepParams& p,
@@ -576,7 +571,6 @@ cudaError_t gen_launch_diagnostics(const T* f, double* partials, double* out, co
 }
 
 #define PCLB_GEN_INSTANTIATE(T)                                                                               \
-  template cudaError_t gen_launch_ghost<T>(const T*, T*, const StepParams&, const DvmG&, cudaStream_t);        \
   template cudaError_t gen_launch_set_state<T>(T*, const T*, const T*, const T*, const T*, const StepParams&, \
                                                const DvmG&, cudaStream_t);                                    \
   template cudaError_t gen_launch_moments<T>(const T*, T*, T*, T*, T*, const StepParams&, const DvmG&,        \

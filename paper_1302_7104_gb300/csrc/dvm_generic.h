@@ -22,12 +22,9 @@ struct DvmG32 {
 
 void fill_dvm_generic32(DvmG32& c, const pclb_dvm& d, const DvmG& g);
 
-// Radial ghost layers of both walls into ghost [side][layer][n_theta][Q].
-template <class T>
-cudaError_t gen_launch_ghost(const T* f, T* ghost, const StepParams& p, const DvmG& d, cudaStream_t s);
-
-// One FP32 step of the N_i = 16 or 24 set with the tiled kernel; tmap
-// describes f (box kWinR x (kTileT32 + 4) x 1 over Q planes).
+// One FP32 step of the N_i = 16 or 24 set: its radial ghost layers into
+// ghost [side][layer][n_theta][Q], then the tiled kernel; tmap describes f
+// (box kWinR x (kTileT32 + 4) x 1 over Q planes).
 cudaError_t gen_tiled_step_f32(const CUtensorMap* tmap, const float* f, float* f_out, float* ghost,
                                const StepParams& p, const DvmG& d, const DvmG32& c, cudaStream_t s);
 

@@ -19,9 +19,10 @@
 //     in r and theta, summed first and added once, with the float Courant
 //     table of the pair; streaming stores, plus the azimuthal ghost rows of
 //     the seam (Eq. 40).
-// The radial ghost nodes (Sec. II C 1) come from the small per-wall buffer
-// the generic ghost kernel writes before the step; tiles at a wall copy them
-// into the window's ghost columns once each pair's planes have landed.
+// The radial ghost nodes (Sec. II C 1) come from a small per-wall buffer that
+// a ghost kernel (one thread per wall row, float-float as the node state)
+// writes before the step; tiles at a wall copy them into the window's ghost
+// columns once each pair's planes have landed.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -39,6 +40,7 @@ namespace {
 constexpr int kTThreads = 16 * kTileT32;            // 256: two nodes each
 constexpr int kTPlane = kWinR * (kTileT32 + 4);     // floats per plane window (800)
 constexpr int kTStages = 4;                         // ring depth (pairs in flight)
+constexpr int kGhostThreads = 32;                   // ghost kernel: one thread per wall row
 static_assert((kTPlane * 4) % 128 == 0, "TMA destinations must stay 128-byte aligned");
 
 template <int ND>
@@ -72,13 +74,13 @@ struct TEq {
   f2 uxE, uyE;          // u / E
 };
 
-// Moments (Eqs. 3-5), temperature and equilibrium factors (Eqs. 10-11) of
-// the two nodes at fn (global, planes `plane` apart).  Returns the pair of
-// physical flags in ok0, ok1.
-template <int ND>
-__device__ __forceinline__ TEq tiled_state(const float* fn, size_t plane, const DvmG32& c, bool& ok0, bool& ok1) {
+// Moments (Eqs. 3-5) of two nodes in float-float: density, velocity and
+// temperature.  ld(q) returns the two nodes' f_q.
+template <int ND, class LD>
+__device__ __forceinline__ void tiled_moments(LD ld, const DvmG32& c, ff2& rho, ff2& ux, ff2& uy, ff2& E) {
   constexpr int H = ND / 2;
-  ff2 rho = ff2_of(ldg2(fn)), jx = ff2_of(bc2(0.f)), jy = jx, e = jx;
+  rho = ff2_of(ld(0));
+  ff2 jx = ff2_of(bc2(0.f)), jy = jx, e = jx;
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     const int k = g == 0 ? 1 : (g == 1 ? 2 : (g == 2 ? 3 : 4));   // g = 1: shells 2 + 3; g = 2: shell 3
@@ -86,10 +88,10 @@ __device__ __forceinline__ TEq tiled_state(const float* fn, size_t plane, const 
 #pragma unroll
     for (int i = 0; i < H; ++i) {
       const int q = 1 + (k - 1) * ND + i;
-      f2 fa = ldg2(fn + (size_t)q * plane), fb = ldg2(fn + (size_t)(q + H) * plane);
+      f2 fa = ld(q), fb = ld(q + H);
       if (g == 1) {
-        fa = add2(fa, ldg2(fn + (size_t)(q + ND) * plane));
-        fb = add2(fb, ldg2(fn + (size_t)(q + ND + H) * plane));
+        fa = add2(fa, ld(q + ND));
+        fb = add2(fb, ld(q + ND + H));
       }
       S = add2(S, add2(fa, fb));
       const f2 dd = sub2(fa, fb);   // the pair has opposite unit vectors
@@ -106,11 +108,16 @@ __device__ __forceinline__ TEq tiled_state(const float* fn, size_t plane, const 
     e = ff2_add(e, ff2_mul(hv, ff2_of(S)));
   }
   const ff2 inv = ff2_recip(rho);
-  const ff2 ux = ff2_mul(jx, inv), uy = ff2_mul(jy, inv);
+  ux = ff2_mul(jx, inv);
+  uy = ff2_mul(jy, inv);
   const ff2 ke = ff2_add(ff2_mul(jx, ux), ff2_mul(jy, uy));   // |j|^2 / rho
-  const ff2 E = ff2_mul(ff2_add(e, ff2_scale(ke, -0.5f)), inv);
-  ok0 = rho.hi.x > 0.f && E.hi.x > 0.f && isfinite(E.hi.x) && isfinite(ux.hi.x) && isfinite(uy.hi.x);
-  ok1 = rho.hi.y > 0.f && E.hi.y > 0.f && isfinite(E.hi.y) && isfinite(ux.hi.y) && isfinite(uy.hi.y);
+  E = ff2_mul(ff2_add(e, ff2_scale(ke, -0.5f)), inv);
+}
+
+// Equilibrium factors (Eqs. 10-11) of two states in float-float, rounded to
+// float once.
+__device__ __forceinline__ TEq tiled_factors(const ff2& rho, const ff2& ux, const ff2& uy, const ff2& E,
+                                             const DvmG32& c) {
   TEq q;
   ff2 sum = ff2_of(bc2(0.f));
 #pragma unroll
@@ -136,8 +143,129 @@ __device__ __forceinline__ TEq tiled_state(const float* fn, size_t plane, const 
   return q;
 }
 
+__device__ __forceinline__ bool phys_x(const ff2& rho, const ff2& ux, const ff2& uy, const ff2& E) {
+  return rho.hi.x > 0.f && E.hi.x > 0.f && isfinite(E.hi.x) && isfinite(ux.hi.x) && isfinite(uy.hi.x);
+}
+__device__ __forceinline__ bool phys_y(const ff2& rho, const ff2& ux, const ff2& uy, const ff2& E) {
+  return rho.hi.y > 0.f && E.hi.y > 0.f && isfinite(E.hi.y) && isfinite(ux.hi.y) && isfinite(uy.hi.y);
+}
+
+// Moments and equilibrium factors of the two radially adjacent nodes at fn
+// (global, planes `plane` apart); the physical flags in ok0, ok1.
+template <int ND>
+__device__ __forceinline__ TEq tiled_state(const float* fn, size_t plane, const DvmG32& c, bool& ok0, bool& ok1) {
+  ff2 rho, ux, uy, E;
+  tiled_moments<ND>([&](int q) { return ldg2(fn + (size_t)q * plane); }, c, rho, ux, uy, E);
+  ok0 = phys_x(rho, ux, uy, E);
+  ok1 = phys_y(rho, ux, uy, E);
+  return tiled_factors(rho, ux, uy, E, c);
+}
+
+// The pair of equilibria f^eq(+-v) of both states (Eq. 10): P(+-x) = ev +- od
+// with x = v.u/E, times w.
+__device__ __forceinline__ void tiled_feq_pair(const TEq& e, f2 w, float vx, float vy, f2& fp, f2& fm) {
+  const f2 x = fma2(bc2(vx), e.uxE, mul2(bc2(vy), e.uyE));
+  const f2 x2 = mul2(x, x);
+  const f2 ev = fma2(x2, fma2(x2, bc2(1.0f / 24.0f), e.a1h), e.a0);
+  const f2 od = mul2(x, fma2(x2, bc2(1.0f / 6.0f), e.a1));
+  const f2 wev = mul2(w, ev);
+  fp = fma2(w, od, wev);
+  fm = fma2(neg2(w), od, wev);
+}
+
+// (v, v) as a float-float pair from a double.
+__device__ __forceinline__ ff2 ff2_from_double(double v) {
+  const float h = (float)v;
+  return ff2{bc2(h), bc2((float)(v - (double)h))};
+}
+
+// Radial ghost layers of wall `side` at row t into ghost [side][layer][n_theta][Q]
+// (Sec. II C 1): Eq. (39) applied twice to the wall node a and the next node
+// b, g0 = 2a - b and g1 = 2 g0 - a = 3a - 2b, for the components the boundary
+// kind extrapolates, the others prescribed; the ghost distribution is the
+// equilibrium of that state, plus the wall node's departure from equilibrium
+// for non-equilibrium ghosts.  All in float-float and float, as the step's
+// node state: the two layers are the two halves of the packed arithmetic.
+template <int ND>
+__global__ void __launch_bounds__(kGhostThreads)
+    tiled_ghost_f32(const float* __restrict__ f, float* __restrict__ ghost, const __grid_constant__ StepParams p,
+                    const __grid_constant__ DvmG d, const __grid_constant__ DvmG32 c) {
+  constexpr int Q = 1 + 4 * ND, H = ND / 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int side = blockIdx.y;
+  if (t >= p.n_theta) return;
+  const size_t plane = (size_t)p.rows * p.pitch;
+  const int ra = side == 0 ? 0 : p.n_r - 1, rb = side == 0 ? 1 : p.n_r - 2;
+  const float* fa = f + (size_t)(t + kGhostRows) * p.pitch + ra;
+  const float* fb = f + (size_t)(t + kGhostRows) * p.pitch + rb;
+  // node a in the low half, node b in the high half
+  ff2 m[4];
+  tiled_moments<ND>([&](int q) { return mk2(__ldg(fa + (size_t)q * plane), __ldg(fb + (size_t)q * plane)); }, c,
+                    m[0], m[1], m[2], m[3]);
+  bool ok = phys_x(m[0], m[1], m[2], m[3]) && phys_y(m[0], m[1], m[2], m[3]);
+  const TEq ea = tiled_factors(m[0], m[1], m[2], m[3], c);
+  ff2 g[4];   // (g0, g1) of rho, u_x, u_y, E
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const ff2 A{bc2(m[i].hi.x), bc2(m[i].lo.x)}, B{bc2(m[i].hi.y), bc2(m[i].lo.y)};
+    g[i] = ff2_add(ff2_mul(A, ff2{mk2(2.f, 3.f), bc2(0.f)}), ff2_mul(B, ff2{mk2(-1.f, -2.f), bc2(0.f)}));
+  }
+  const int kind = p.bc_kind[side] & ~PCLB_BC_NEQ;
+  const bool neq = (p.bc_kind[side] & PCLB_BC_NEQ) != 0;
+  if (kind != PCLB_BC_EXTRAP) {
+    const double cs = p.cos_t[t], sn = p.sin_t[t];
+    ff2 v[4];
+    for (int l = 0; l < 2; ++l) {
+      const double* bv = p.bc_vals + (size_t)((side * 2 + l) * 4) * p.n_theta + t;
+      const double ur = bv[1 * p.n_theta], ut = bv[2 * p.n_theta];
+      const double x[4] = {bv[0], ur * cs - ut * sn, ur * sn + ut * cs, bv[3 * p.n_theta]};
+      for (int i = 0; i < 4; ++i) {
+        const ff2 y = ff2_from_double(x[i]);
+        if (l == 0) v[i] = y; else { v[i].hi.y = y.hi.y; v[i].lo.y = y.lo.y; }
+      }
+    }
+    g[1] = v[1];
+    g[2] = v[2];
+    if (kind == PCLB_BC_DIRICHLET) {
+      g[0] = v[0];
+      g[3] = v[3];
+    }
+  }
+  ok = ok && g[0].hi.x > 0.f && g[3].hi.x > 0.f && g[0].hi.y > 0.f && g[3].hi.y > 0.f;
+  if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
+  const TEq eg = tiled_factors(g[0], g[1], g[2], g[3], c);
+  float* out0 = ghost + ((size_t)(side * 2 + 0) * p.n_theta + t) * Q;
+  float* out1 = ghost + ((size_t)(side * 2 + 1) * p.n_theta + t) * Q;
+  {
+    f2 v = mul2(eg.w[0], eg.a0);
+    if (neq) v = add2(v, bc2(fa[0] - ea.w[0].x * ea.a0.x));
+    out0[0] = v.x;
+    out1[0] = v.y;
+  }
+#pragma unroll 1
+  for (int pr = 0; pr < 4 * H; ++pr) {
+    const int k = 1 + pr / H, q1 = 1 + (k - 1) * ND + pr % H, q2 = q1 + H;
+    const f2 wg = k == 1 ? eg.w[1] : (k == 2 ? eg.w[2] : (k == 3 ? eg.w[3] : eg.w[4]));
+    f2 gp, gm;
+    tiled_feq_pair(eg, wg, c.vx[q1], c.vy[q1], gp, gm);
+    if (neq) {
+      const f2 wa = k == 1 ? ea.w[1] : (k == 2 ? ea.w[2] : (k == 3 ? ea.w[3] : ea.w[4]));
+      f2 ap, am;
+      tiled_feq_pair(ea, wa, c.vx[q1], c.vy[q1], ap, am);
+      gp = add2(gp, bc2(fa[(size_t)q1 * plane] - ap.x));
+      gm = add2(gm, bc2(fa[(size_t)q2 * plane] - am.x));
+    }
+    out0[q1] = gp.x;
+    out1[q1] = gp.y;
+    out0[q2] = gm.x;
+    out1[q2] = gm.y;
+  }
+}
+
+// Three CTAs per SM (at most 85 registers; a few bytes spill in some
+// instantiations): 12% faster than two CTAs at 124 registers.
 template <int ND, int SCH>
-__global__ void __launch_bounds__(kTThreads, 2)
+__global__ void __launch_bounds__(kTThreads, 3)
     tiled_step_f32(const __grid_constant__ CUtensorMap tmap, const float* __restrict__ f, float* __restrict__ f_out,
                    const float* __restrict__ ghost, const __grid_constant__ StepParams p,
                    const __grid_constant__ DvmG d, const __grid_constant__ DvmG32 c) {
@@ -259,12 +387,8 @@ __global__ void __launch_bounds__(kTThreads, 2)
       const f2 nkt = fma2(nat, nat, nat);           // -(a - a^2) with a = -nat
       // equilibrium of the pair (Eq. 10): P(+-x) = ev +- od, x = v.u/E
       const f2 wk = k == 1 ? eq.w[1] : (k == 2 ? eq.w[2] : (k == 3 ? eq.w[3] : eq.w[4]));
-      const f2 x = fma2(bc2(c.vx[q1]), eq.uxE, mul2(bc2(c.vy[q1]), eq.uyE));
-      const f2 x2 = mul2(x, x);
-      const f2 ev = fma2(x2, fma2(x2, bc2(1.0f / 24.0f), eq.a1h), eq.a0);
-      const f2 od = mul2(x, fma2(x2, bc2(1.0f / 6.0f), eq.a1));
-      const f2 wev = mul2(wk, ev);
-      const f2 fe[2] = {fma2(wk, od, wev), fma2(neg2(wk), od, wev)};
+      f2 fe[2];
+      tiled_feq_pair(eq, wk, c.vx[q1], c.vy[q1], fe[0], fe[1]);
 #pragma unroll
       for (int L = 0; L < 2; ++L) {
         const int su = L ? -sr : sr, sv = L ? -stt : stt;
@@ -341,14 +465,19 @@ cudaError_t launch_tiled_nd(const CUtensorMap* tmap, const float* f, float* f_ou
 }  // namespace
 
 // One FP32 step of the N_i = 16 or 24 set: the radial ghost layers, then the
-// tiled kernel over the whole grid.  tmap describes f (box kWinR x
+// tiled kernel over the whole grid (the same stream orders them).  tmap describes f (box kWinR x
 // (kTileT32 + 4) x 1, Q planes).
 cudaError_t gen_tiled_step_f32(const CUtensorMap* tmap, const float* f, float* f_out, float* ghost,
                                const StepParams& p, const DvmG& d, const DvmG32& c, cudaStream_t s) {
-  cudaError_t e = gen_launch_ghost<float>(f, ghost, p, d, s);
-  if (e != cudaSuccess) return e;
-  return d.n_dirs == 16 ? launch_tiled_nd<16>(tmap, f, f_out, ghost, p, d, c, s)
-                        : launch_tiled_nd<24>(tmap, f, f_out, ghost, p, d, c, s);
+  const dim3 ggrid((p.n_theta + kGhostThreads - 1) / kGhostThreads, 2);
+  if (d.n_dirs == 16) {
+    tiled_ghost_f32<16><<<ggrid, kGhostThreads, 0, s>>>(f, ghost, p, d, c);
+    const cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : launch_tiled_nd<16>(tmap, f, f_out, ghost, p, d, c, s);
+  }
+  tiled_ghost_f32<24><<<ggrid, kGhostThreads, 0, s>>>(f, ghost, p, d, c);
+  const cudaError_t e = cudaGetLastError();
+  return e != cudaSuccess ? e : launch_tiled_nd<24>(tmap, f, f_out, ghost, p, d, c, s);
 }
 
 }  // namespace pclb
