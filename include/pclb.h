@@ -216,12 +216,13 @@ pclb_status pclb_moments(pclb_ctx* ctx, void* rho, void* u_r, void* u_theta, voi
  * both relaxations are supported. */
 pclb_status pclb_set_scheme(pclb_ctx* ctx, int32_t scheme, int32_t relaxation);
 
-/* How long a step kernel (pclb_step, pclb_step_graph, pclb_step_states,
- * pclb_run_host) waits for the TMA copies of its own stencil window before
- * it gives the tile up and sets PCLB_FLAG_TIMEOUT; the default is
- * 2000000000 ns (2 s), the maximum 60 s.  A tile given up stores nothing;
+/* How long a step or adjoint kernel (pclb_step, pclb_step_graph,
+ * pclb_step_states, pclb_run_host, pclb_adjoint_state, pclb_adjoint_step)
+ * waits for the TMA copies of its own stencil window before it gives the
+ * tile up and sets PCLB_FLAG_TIMEOUT; the default is
+ * 2000000000 ns (2 s), the maximum 60 s.  A tile given up stores no more;
  * its copies still get the default limit to land before its block exits, so
- * the context stays usable, but the state after such a step is undefined
+ * the context stays usable, but the state (or cotangent) after such a step is undefined
  * (reload it) and pclb_status_flags returns PCLB_ETIMEOUT.  A limit of 0
  * gives every tile up without waiting, which exercises that path.  No paper
  * counterpart: an execution detail.  Drops cached step graphs.  Errors:

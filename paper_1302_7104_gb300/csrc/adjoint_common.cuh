@@ -155,4 +155,11 @@ __device__ __forceinline__ void to_moment_cotangent(T rho, T ux, T uy, T E, cons
   g[3] = G[3] * inv;
 }
 
+// The FP32 pair kernel over tiles a0 .. a0 + na - 1 and b0 .. (nx blocks in
+// r), all theta tiles (adjoint_f32x2.cu).
+cudaError_t launch_adjoint_pairs_f32(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, const float* f,
+                                     const float* lam_in, float* lam_out, const EqParams<float>* ghost,
+                                     const float* gwall, int a0, int na, int b0, int nx, const StepParams& p,
+                                     const DvmConst<float>& d, cudaStream_t s);
+
 }  // namespace pclb

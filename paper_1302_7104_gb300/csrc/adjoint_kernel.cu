@@ -46,11 +46,6 @@ namespace pclb {
 template <class T>
 struct AdjTile;
 template <>
-struct AdjTile<float> {
-  static constexpr int TT = kAdjRows32;
-  static constexpr int min_blocks = 5;   // 5 CTAs of 256 threads per SM: at most 51 registers
-};
-template <>
 struct AdjTile<double> {
   static constexpr int TT = kAdjRows64;
   static constexpr int min_blocks = 3;   // at most 85 registers
@@ -130,17 +125,8 @@ __device__ __forceinline__ Cour<T> courant(const StepParams& p, const DvmConst<T
   return c;
 }
 
-// (rho, u_x, u_y, E) of one node for the cotangent of the equilibrium:
-// float-float moments rounded to float in FP32, double in FP64.
-__device__ __forceinline__ void adj_node_state(const float* f, int plane, const DvmConst<float>& d, float& rho,
-                                               float& ux, float& uy, float& E, bool& ok) {
-  const State32 m = state32(f, plane, d);
-  rho = m.rho.hi + m.rho.lo;
-  ux = m.ux.hi + m.ux.lo;
-  uy = m.uy.hi + m.uy.lo;
-  E = m.E.hi + m.E.lo;
-  ok = m.ok;
-}
+// (rho, u_x, u_y, E) of one node for the cotangent of the equilibrium (FP64;
+// the FP32 pair kernel forms the state of its two nodes in float-float).
 __device__ __forceinline__ void adj_node_state(const double* f, int plane, const DvmConst<double>& d, double& rho,
                                                double& ux, double& uy, double& E, bool& ok) {
   const NodeState<double> m = node_moments(f, plane, d);
@@ -507,7 +493,7 @@ __global__ void __launch_bounds__(AdjSize<T>::threads, AdjTile<T>::min_blocks)
     const int s = pair % S;
     const T* st = ring + s * 4 * PLANE;
     T* pb = prod + (pair & 1) * 2 * PROD;                // this pair's products: [label][...]
-    if (ok) ok = mbar_wait_bounded(&bar[s], (uint32_t)((pair / S) & 1), kDefaultWaitNs);
+    if (ok) ok = p.wait_ns != 0 && mbar_wait_bounded(&bar[s], (uint32_t)((pair / S) & 1), p.wait_ns);
     if (wall_tile) {
       // radial ghost columns of this pair's f planes (f = f^eq of the ghost states)
       if (fills && ok) {
@@ -636,30 +622,39 @@ template <class T>
 cudaError_t launch_adjoint(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, const T* f, const T* lam_in,
                            T* lam_out, const AdjScratch& ws, const StepParams& p, const DvmConst<T>& d,
                            cudaStream_t stream, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
-  static std::atomic<unsigned long long> configured{0};
-  constexpr int smem = AdjSize<T>::smem;
-  {
-    const cudaError_t e = set_smem_once(adjoint_pair_kernel<T>, smem, configured);
-    if (e != cudaSuccess) return e;
-  }
   EqParams<T>* ghost = reinterpret_cast<EqParams<T>*>(ws.ghost);
   T* gwall = reinterpret_cast<T*>(ws.gwall);
-  constexpr int TT = AdjTile<T>::TT;
   const int nt = (p.n_r + kTileR - 1) / kTileR;
   const int t_hi = p.n_r - 33 > 0 ? (p.n_r - 33 + kTileR - 1) / kTileR : 0;   // first tile with r0 >= n_r - 33
   const int b0 = t_hi > 1 ? t_hi : 1;
   const int n_interior = t_hi > 1 ? t_hi - 1 : 0;                              // tiles 1 .. t_hi - 1
-  const unsigned gy = (unsigned)((p.n_theta + TT - 1) / TT);
   cudaError_t e = cudaEventRecord(ev_fork, stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_fork, 0);
   if (e != cudaSuccess) return e;
   adjoint_wall_kernel<T><<<(2 * p.n_theta + 3) / 4, 128, 0, side>>>(f, lam_in, ghost, gwall, p, d);
-  adjoint_pair_kernel<T><<<dim3(1 + (nt - b0), gy), AdjSize<T>::threads, smem, side>>>(
-      *tmap_f, *tmap_l, f, lam_in, lam_out, ghost, gwall, 0, 1, b0, p, d);
-  if (n_interior > 0)
-    adjoint_pair_kernel<T><<<dim3(n_interior, gy), AdjSize<T>::threads, smem, stream>>>(
-        *tmap_f, *tmap_l, f, lam_in, lam_out, ghost, gwall, 1, n_interior, 0, p, d);
-  e = cudaGetLastError();
+  if constexpr (sizeof(T) == 4) {
+    // FP32: the packed two-nodes-per-thread pair kernel (adjoint_f32x2.cu)
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = launch_adjoint_pairs_f32(tmap_f, tmap_l, f, lam_in, lam_out, ghost, gwall, 0, 1, b0, 1 + (nt - b0), p, d,
+                                   side);
+    if (e == cudaSuccess && n_interior > 0)
+      e = launch_adjoint_pairs_f32(tmap_f, tmap_l, f, lam_in, lam_out, ghost, gwall, 1, n_interior, 0, n_interior,
+                                   p, d, stream);
+  } else {
+    static std::atomic<unsigned long long> configured{0};
+    constexpr int smem = AdjSize<T>::smem;
+    e = set_smem_once(adjoint_pair_kernel<T>, smem, configured);
+    if (e != cudaSuccess) return e;
+    constexpr int TT = AdjTile<T>::TT;
+    const unsigned gy = (unsigned)((p.n_theta + TT - 1) / TT);
+    adjoint_pair_kernel<T><<<dim3(1 + (nt - b0), gy), AdjSize<T>::threads, smem, side>>>(
+        *tmap_f, *tmap_l, f, lam_in, lam_out, ghost, gwall, 0, 1, b0, p, d);
+    if (n_interior > 0)
+      adjoint_pair_kernel<T><<<dim3(n_interior, gy), AdjSize<T>::threads, smem, stream>>>(
+          *tmap_f, *tmap_l, f, lam_in, lam_out, ghost, gwall, 1, n_interior, 0, p, d);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
   e = cudaEventRecord(ev_join, side);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev_join, 0);

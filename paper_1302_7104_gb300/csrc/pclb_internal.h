@@ -35,7 +35,7 @@ constexpr int kStepThreads = 256;   // 8 warps; each thread owns 2 nodes (rows w
 constexpr int kPitchAlign = 32;     // row pitch in elements (128 B for float)
 constexpr int kGhostRows = 2;       // azimuthal ghost rows stored on each side
 // Tile rows of the adjoint kernel (its window holds f and lam for all labels).
-constexpr int kAdjRows32 = 8;
+constexpr int kAdjRows32 = 16;
 constexpr int kAdjRows64 = 8;
 // Time a kernel waits for the TMA copies of its own window (mbarrier phase)
 // before it reports PCLB_FLAG_TIMEOUT and gives the tile up; the copies of a

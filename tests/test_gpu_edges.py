@@ -191,6 +191,33 @@ def test_window_wait_that_runs_out_reports_timeout(prec):
     assert torch.equal(got, want)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_adjoint_window_wait_that_runs_out_reports_timeout(prec):
+    """The adjoint kernels give a tile up the same way when the wait for its
+    f and lam windows runs out: PCLB_FLAG_TIMEOUT, PCLB_ETIMEOUT from
+    pclb_status_flags, and with the default limit restored the next adjoint
+    step equals a fresh context's bit for bit."""
+    w = I.kh(n_r=1024, n_theta=512)
+    dtype = torch.float32 if prec == "fp32" else torch.float64
+    f0 = torch.as_tensor(O.set_state(w), dtype=dtype, device="cuda")
+    gen = torch.Generator(device="cpu").manual_seed(11)
+    lam = torch.randn(f0.shape, generator=gen, dtype=torch.float64).to(dtype=dtype, device="cuda")
+    with P.PCLB(w, precision=prec) as g:
+        g.set_wait_limit(0)
+        g.adjoint_step(f0, lam)
+        flags = ctypes.c_uint32()
+        code = P.lib().pclb_status_flags(g.ctx, ctypes.byref(flags), 1)
+        assert code == 5 and flags.value & P.FLAG_TIMEOUT, (code, flags.value)
+        g.set_wait_limit()
+        got = g.adjoint_step(f0, lam)
+        g.sync()
+        assert g.status_flags() == 0
+    with P.PCLB(w, precision=prec) as h:
+        want = h.adjoint_step(f0, lam)
+        h.sync()
+    assert torch.equal(got, want)
+
+
 def test_host_sync_that_runs_out_reports_timeout():
     """pclb_sync with a limit shorter than the queued work returns
     PCLB_ETIMEOUT and leaves the work running; a second sync with the default
