@@ -5,9 +5,12 @@
 // keeps the FP64 path); only the data layout per thread differs:
 //   * tile 32 (r) x 16 (theta), 256 threads; thread (row, 2j) owns the nodes
 //     (2j, 2j + 1) of its row;
-//   * the node cotangent g of both nodes (Eqs. 3-5, 10-11 differentiated)
-//     from f^n and lam^{n+1} read from global memory, float-float moments
-//     rounded once, then the equilibrium cotangent in packed float;
+//   * the node cotangent g of both nodes (Eqs. 3-5, 10-11 differentiated):
+//     the windows of all 33 f planes, then of all 33 lam planes, stream
+//     through a ring of 12 plane slots (two halves of six, one TMA barrier
+//     each) laid over the product buffers, which are free until the pairs
+//     start; the moments in float-float, rounded once, then the equilibrium
+//     cotangent in packed float;
 //   * the pairs of opposite velocities stream their f and lam windows over
 //     [r0-4, r0+36) x [t0-2, t0+18) through a 2-stage TMA ring; per pair,
 //     phase (A) forms lam(n) dM(n)/dD and lam(n) dM(n)/dDp of every node whose
@@ -44,7 +47,11 @@ constexpr int kRingBytes = kAS * 4 * kAPl * 4;  // [stage][f q1, f q2, lam q1, l
 constexpr int kProdBytes = 2 * 2 * kProd * 4;   // [buffer][label][products]
 constexpr int kInvrBytes = kTileR * 4;
 constexpr int kTabBytes = (kTT + 4) * kANP * 16;
-constexpr int kASmem = kRingBytes + kProdBytes + kInvrBytes + kTabBytes + 8 * kAS;
+constexpr int kASmem = kRingBytes + kProdBytes + kInvrBytes + kTabBytes + 8 * (kAS + 2);
+// node phase: 66 plane windows (f then lam) in groups of six through 12 slots
+constexpr int kPSlots = 12, kPGroup = 6, kPBoxes = 2 * kQ, kPGroups = kPBoxes / kPGroup;
+static_assert(kPSlots * kAPl * 4 <= kProdBytes, "node-phase ring inside the product buffers");
+static_assert(kPBoxes % kPGroup == 0 && kPSlots == 2 * kPGroup, "two halves of whole groups");
 static_assert(kTT == 16 && kAThr == 256, "thread layout: 8 warps of two 16-thread rows");
 static_assert((kAPl * 4) % 128 == 0, "TMA destinations must stay 128-byte aligned");
 static_assert(kProdBytes % 16 == 0 && (kRingBytes + kProdBytes + kInvrBytes) % 16 == 0, "float4 table alignment");
@@ -52,7 +59,6 @@ static_assert(kRC % 2 == 0 && kAT % 2 == 0 && kBT % 2 == 0 && kProd % 2 == 0, "8
 
 __device__ __forceinline__ f2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 __device__ __forceinline__ void sts2(float* p, f2 v) { *reinterpret_cast<float2*>(p) = v; }
-__device__ __forceinline__ f2 ldg2(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
 
 // mwb_partials of two nodes: MD = a + K (ar + br (ar - s br)), MDp = -(1 + s)
 // K ar^2 with ar, br = |D|, |Dp| / (|D| + |Dp|) (0 when the sum is below the
@@ -70,121 +76,211 @@ __device__ __forceinline__ void mwb_partials2(f2 a, f2 K, f2 D, f2 Dp, f2& MD, f
   MDp = mul2(neg2(add2(bc2(1.f), s)), mul2(Ka, ar));
 }
 
-// Float-float moments (Eqs. 3-5) and temperature of two nodes, as state32:
-// float shell sums over opposite-direction pairs, shells 2 and 3 added
-// direction by direction first, shell totals combined with error-free
-// transformations.  ld(q) returns both nodes' f_q.
-template <class LD>
-__device__ __forceinline__ void state_pair(LD ld, const DvmConst<float>& d, f2& rho_o, f2& ux_o, f2& uy_o, f2& E_o,
-                                           bool& ok0, bool& ok1) {
-  ff2 rho = ff2_of(ld(0)), jx = ff2_of(bc2(0.f)), jy = jx, e = jx;
-#pragma unroll
-  for (int g = 0; g < 4; ++g) {
-    const int k = g == 0 ? 1 : (g == 1 ? 2 : (g == 2 ? 3 : 4));
-    f2 S = bc2(0.f), X = S, Xl = S, Y = S, Yl = S;
-#pragma unroll
-    for (int i = 0; i < kHalf; ++i) {
-      const int q = 1 + (k - 1) * kNDirs + i;
-      f2 fa = ld(q), fb = ld(q + kHalf);
-      if (g == 1) {
-        const int qa = 1 + 2 * kNDirs + i;   // shell 3 added to shell 2
-        fa = add2(fa, ld(qa));
-        fb = add2(fb, ld(qa + kHalf));
-      }
-      S = add2(S, add2(fa, fb));
-      const f2 dd = sub2(fa, fb);   // the pair has opposite unit vectors
-      X = fma2(bc2(d.cx[q]), dd, X);
-      Xl = fma2(bc2(d.cx_lo[q]), dd, Xl);
-      Y = fma2(bc2(d.cy[q]), dd, Y);
-      Yl = fma2(bc2(d.cy_lo[q]), dd, Yl);
-    }
-    const ff2 sp = g == 2 ? ff2{bc2(d.dv23), bc2(d.dv23_lo)} : ff2{bc2(d.speed[k]), bc2(d.speed_lo[k])};
-    const ff2 hv = g == 2 ? ff2{bc2(d.dh23), bc2(d.dh23_lo)} : ff2{bc2(d.half_v2[k]), bc2(d.half_v2_lo[k])};
-    if (g != 2) rho = ff2_add(rho, ff2_of(S));
-    jx = ff2_add(jx, ff2_mul(sp, ff2{X, Xl}));
-    jy = ff2_add(jy, ff2_mul(sp, ff2{Y, Yl}));
-    e = ff2_add(e, ff2_mul(hv, ff2_of(S)));
-  }
-  const ff2 inv = ff2_recip(rho);
-  const ff2 ux = ff2_mul(jx, inv), uy = ff2_mul(jy, inv);
-  const ff2 ke = ff2_add(ff2_mul(jx, ux), ff2_mul(jy, uy));   // |j|^2 / rho
-  const ff2 E = ff2_mul(ff2_add(e, ff2_scale(ke, -0.5f)), inv);
-  ok0 = rho.hi.x > 0.f && E.hi.x > 0.f && isfinite(e.hi.x) && isfinite(jx.hi.x) && isfinite(jy.hi.x);
-  ok1 = rho.hi.y > 0.f && E.hi.y > 0.f && isfinite(e.hi.y) && isfinite(jx.hi.y) && isfinite(jy.hi.y);
-  rho_o = ff2_round(rho);
-  ux_o = ff2_round(ux);
-  uy_o = ff2_round(uy);
-  E_o = ff2_round(E);
+// Streaming order of the node phase: box b < 33 is f plane pro_f_plane(b),
+// box 33 + c lam plane pro_l_plane(c).  f: the rest plane; shell 1 by pairs
+// of opposite directions; shells 2 and 3 direction by direction (2, its
+// opposite, 3, its opposite); shell 4 by pairs.  lam: the rest plane, then
+// every shell by pairs of opposite directions.
+__host__ __device__ constexpr int pro_f_plane(int b) {
+  return b == 0 ? 0
+         : b <= 8 ? 1 + (b - 1) / 2 + 4 * ((b - 1) % 2)
+         : b <= 24 ? 9 + (b - 9) / 4 + 4 * ((b - 9) % 4)
+                   : 25 + (b - 25) / 2 + 4 * ((b - 25) % 2);
 }
+__host__ __device__ constexpr int pro_l_plane(int c) {
+  return c == 0 ? 0 : 1 + kNDirs * ((c - 1) / kNDirs) + ((c - 1) % kNDirs) / 2 + kHalf * ((c - 1) % 2);
+}
+static_assert(pro_f_plane(2) == 5 && pro_f_plane(11) == 17 && pro_f_plane(12) == 21 && pro_f_plane(13) == 10 &&
+                  pro_f_plane(26) == 29 && pro_f_plane(32) == 32 && pro_l_plane(2) == 5 && pro_l_plane(9) == 9 &&
+                  pro_l_plane(32) == 32,
+              "node-phase plane order");
+
+// Running sums of the node phase for two nodes.
+struct NodeAcc {
+  // moments (Eqs. 3-5) in float-float, float sums of the current shell group
+  // and of shell 3 alone, plane values waiting for the rest of their unit
+  ff2 rho, jx, jy, e;
+  f2 S, X, Xl, Y, Yl, S3, X3, X3l, Y3, Y3l, pa, pb, pc;
+  // the state rounded to float, and the factors of the equilibrium cotangent
+  f2 rh, ux, uy, E;
+  bool ok0, ok1;
+  f2 F[5], Fd[5], invE, s, a0, a1, a1h, uxE, uyE;
+  // G = sum_q lam_q d f^eq_q / d(rho, u, E): totals and the current shell
+  f2 A, Bx, By, Cs, Dx, Fq, Ak, Bxk, Byk, Ck, Dk, lp, l0;
+};
 
 __device__ __forceinline__ f2 recip1_2(f2 x) {
   const f2 r = mk2(recip_fast(x.x), recip_fast(x.y));
   return fma2(r, fma2(neg2(x), r, bc2(1.f)), r);
 }
 
-// eq_cotangent of two nodes: G = sum_q lam_q d f^eq_q / d(rho, u_x, u_y, E)
-// (Eq. 10 with the weights of Eq. 11), opposite velocities of a shell
-// sharing the even and odd parts of P, P_x and P_s.
-template <class LamFn>
-__device__ __forceinline__ void eq_cotangent2(f2 rho, f2 ux, f2 uy, f2 E, const DvmConst<float>& d, LamFn lam,
-                                              f2 G[4]) {
-  f2 F[5], Fd[5];
+// Temperature recovery E = (e - |j|^2 / (2 rho)) / rho in float-float, the
+// state rounded once, then the weights F_k(E), F'_k(E) (Eq. 11) and the
+// polynomial coefficients of Eq. (10) for the cotangent.
+__device__ __forceinline__ void node_state(NodeAcc& a, const DvmConst<float>& d) {
+  const ff2 inv = ff2_recip(a.rho);
+  const ff2 ux = ff2_mul(a.jx, inv), uy = ff2_mul(a.jy, inv);
+  const ff2 ke = ff2_add(ff2_mul(a.jx, ux), ff2_mul(a.jy, uy));   // |j|^2 / rho
+  const ff2 E = ff2_mul(ff2_add(a.e, ff2_scale(ke, -0.5f)), inv);
+  a.ok0 = a.rho.hi.x > 0.f && E.hi.x > 0.f && isfinite(a.e.hi.x) && isfinite(a.jx.hi.x) && isfinite(a.jy.hi.x);
+  a.ok1 = a.rho.hi.y > 0.f && E.hi.y > 0.f && isfinite(a.e.hi.y) && isfinite(a.jx.hi.y) && isfinite(a.jy.hi.y);
+  a.rh = ff2_round(a.rho);
+  a.ux = ff2_round(ux);
+  a.uy = ff2_round(uy);
+  a.E = ff2_round(E);
   f2 Fs = bc2(0.f), Fds = bc2(0.f);
 #pragma unroll
   for (int k = 1; k <= 4; ++k) {
     const float* c = d.Fc[k];
-    F[k] = mul2(E, fma2(E, fma2(E, fma2(E, bc2(c[3]), bc2(c[2])), bc2(c[1])), bc2(c[0])));
-    Fd[k] = fma2(E, fma2(E, fma2(mul2(E, bc2(4.f)), bc2(c[3]), bc2(3.f * c[2])), bc2(2.f * c[1])), bc2(c[0]));
-    Fs = add2(Fs, F[k]);
-    Fds = add2(Fds, Fd[k]);
+    a.F[k] = mul2(a.E, fma2(a.E, fma2(a.E, fma2(a.E, bc2(c[3]), bc2(c[2])), bc2(c[1])), bc2(c[0])));
+    a.Fd[k] = fma2(a.E, fma2(a.E, fma2(mul2(a.E, bc2(4.f)), bc2(c[3]), bc2(3.f * c[2])), bc2(2.f * c[1])), bc2(c[0]));
+    Fs = add2(Fs, a.F[k]);
+    Fds = add2(Fds, a.Fd[k]);
   }
-  F[0] = fma2(bc2(-d.B0), Fs, bc2(1.f));
-  Fd[0] = mul2(bc2(-d.B0), Fds);
-  const f2 invE = recip1_2(E);
-  const f2 s = mul2(fma2(ux, ux, mul2(uy, uy)), invE);
-  const f2 a1 = fma2(bc2(-0.5f), s, bc2(1.f));
-  const f2 a0 = fma2(mul2(bc2(0.125f), s), s, a1);
-  const f2 uxE = mul2(ux, invE), uyE = mul2(uy, invE);
-  const f2 l0 = lam(0);
-  const f2 l0F0 = mul2(l0, F[0]);
-  f2 A = mul2(l0F0, a0), Bx = bc2(0.f), By = bc2(0.f);
-  f2 Cs = mul2(l0F0, fma2(bc2(0.25f), s, bc2(-0.5f))), Dx = bc2(0.f);
-  f2 Fq = mul2(mul2(l0, Fd[0]), a0);
-  const f2 a1h = mul2(bc2(0.5f), a1);
-#pragma unroll
-  for (int k = 1; k <= 4; ++k) {
-    f2 Ak = bc2(0.f), Bxk = Ak, Byk = Ak, Ck = Ak, Dk = Ak;
-#pragma unroll
-    for (int i = 0; i < kHalf; ++i) {
-      const int q = 1 + (k - 1) * kNDirs + i;
-      const f2 vx = bc2(d.vx[q]), vy = bc2(d.vy[q]);
-      const f2 x = fma2(vx, uxE, mul2(vy, uyE));
-      const f2 x2 = mul2(x, x);
-      const f2 Pe = fma2(x2, fma2(x2, bc2(1.0f / 24.0f), a1h), a0);   // P(+-x) = Pe +- Po
-      const f2 Xo = mul2(x, fma2(x2, bc2(1.0f / 6.0f), a1));          // odd part of P and of P_x
-      const f2 Xe = fma2(x2, bc2(0.5f), a1);                           // even part of P_x
-      const f2 Se = fma2(bc2(-0.25f), x2, fma2(bc2(0.25f), s, bc2(-0.5f)));   // P_s(+-x) = Se -+ x/2
-      const f2 lp = lam(q), lm = lam(q + kHalf);
-      const f2 ls = add2(lp, lm), ld = sub2(lp, lm);
-      Ak = fma2(ls, Pe, fma2(ld, Xo, Ak));
-      const f2 lpx = fma2(ld, Xe, mul2(ls, Xo));                     // lp P_x(x) - lm P_x(-x)
-      Bxk = fma2(lpx, vx, Bxk);
-      Byk = fma2(lpx, vy, Byk);
-      Ck = fma2(ls, Se, fma2(mul2(ld, bc2(-0.5f)), x, Ck));
-      Dk = fma2(x, fma2(ls, Xo, mul2(ld, Xe)), Dk);                  // lp x P_x(x) + lm (-x) P_x(-x)
+  a.F[0] = fma2(bc2(-d.B0), Fs, bc2(1.f));
+  a.Fd[0] = mul2(bc2(-d.B0), Fds);
+  a.invE = recip1_2(a.E);
+  a.s = mul2(fma2(a.ux, a.ux, mul2(a.uy, a.uy)), a.invE);
+  a.a1 = fma2(bc2(-0.5f), a.s, bc2(1.f));
+  a.a0 = fma2(mul2(bc2(0.125f), a.s), a.s, a.a1);
+  a.uxE = mul2(a.ux, a.invE);
+  a.uyE = mul2(a.uy, a.invE);
+  a.a1h = mul2(bc2(0.5f), a.a1);
+}
+
+// Box B of the node phase, with v the two nodes' values of its plane.
+template <int B>
+__device__ __forceinline__ void node_box(NodeAcc& a, f2 v, const DvmConst<float>& d) {
+  if constexpr (B == 0) {
+    a.rho = ff2_of(v);
+    a.jx = a.jy = a.e = ff2_of(bc2(0.f));
+    a.S = a.X = a.Xl = a.Y = a.Yl = bc2(0.f);
+    a.S3 = a.X3 = a.X3l = a.Y3 = a.Y3l = bc2(0.f);
+  } else if constexpr (B <= 8 || (B >= 25 && B < kQ)) {
+    // shell 1 or 4: f_a + f_b and (f_a - f_b) c_i of each pair of opposite directions
+    constexpr int base = B <= 8 ? 1 : 25, j = B - base, q = base + j / 2;
+    if constexpr (j % 2 == 0) {
+      a.pa = v;
+    } else {
+      a.S = add2(a.S, add2(a.pa, v));
+      const f2 dd = sub2(a.pa, v);
+      a.X = fma2(bc2(d.cx[q]), dd, a.X);
+      a.Xl = fma2(bc2(d.cx_lo[q]), dd, a.Xl);
+      a.Y = fma2(bc2(d.cy[q]), dd, a.Y);
+      a.Yl = fma2(bc2(d.cy_lo[q]), dd, a.Yl);
     }
-    A = fma2(F[k], Ak, A);
-    Bx = fma2(F[k], Bxk, Bx);
-    By = fma2(F[k], Byk, By);
-    Cs = fma2(F[k], Ck, Cs);
-    Dx = fma2(F[k], Dk, Dx);
-    Fq = fma2(Fd[k], Ak, Fq);
+    if constexpr (B == 8 || B == kQ - 1) {
+      constexpr int k = B == 8 ? 1 : 4;
+      const ff2 sp{bc2(d.speed[k]), bc2(d.speed_lo[k])}, hv{bc2(d.half_v2[k]), bc2(d.half_v2_lo[k])};
+      a.rho = ff2_add(a.rho, ff2_of(a.S));
+      a.jx = ff2_add(a.jx, ff2_mul(sp, ff2{a.X, a.Xl}));
+      a.jy = ff2_add(a.jy, ff2_mul(sp, ff2{a.Y, a.Yl}));
+      a.e = ff2_add(a.e, ff2_mul(hv, ff2_of(a.S)));
+      a.S = a.X = a.Xl = a.Y = a.Yl = bc2(0.f);
+    }
+    if constexpr (B == kQ - 1) node_state(a, d);
+  } else if constexpr (B < 25) {
+    // shells 2 and 3 direction by direction: (f2_a + f3_a) +- (f2_b + f3_b)
+    // with the speed of shell 2, and shell 3 alone for the speed difference
+    constexpr int i = (B - 9) / 4, j = (B - 9) % 4, q = 9 + i, q3 = 17 + i;
+    if constexpr (j == 0) {
+      a.pa = v;
+    } else if constexpr (j == 1) {
+      a.pb = v;
+    } else if constexpr (j == 2) {
+      a.pc = v;
+    } else {
+      const f2 fa = add2(a.pa, a.pc), fb = add2(a.pb, v);
+      a.S = add2(a.S, add2(fa, fb));
+      const f2 dd = sub2(fa, fb);
+      a.X = fma2(bc2(d.cx[q]), dd, a.X);
+      a.Xl = fma2(bc2(d.cx_lo[q]), dd, a.Xl);
+      a.Y = fma2(bc2(d.cy[q]), dd, a.Y);
+      a.Yl = fma2(bc2(d.cy_lo[q]), dd, a.Yl);
+      a.S3 = add2(a.S3, add2(a.pc, v));
+      const f2 d3 = sub2(a.pc, v);
+      a.X3 = fma2(bc2(d.cx[q3]), d3, a.X3);
+      a.X3l = fma2(bc2(d.cx_lo[q3]), d3, a.X3l);
+      a.Y3 = fma2(bc2(d.cy[q3]), d3, a.Y3);
+      a.Y3l = fma2(bc2(d.cy_lo[q3]), d3, a.Y3l);
+    }
+    if constexpr (B == 24) {
+      const ff2 sp{bc2(d.speed[2]), bc2(d.speed_lo[2])}, hv{bc2(d.half_v2[2]), bc2(d.half_v2_lo[2])};
+      a.rho = ff2_add(a.rho, ff2_of(a.S));
+      a.jx = ff2_add(a.jx, ff2_mul(sp, ff2{a.X, a.Xl}));
+      a.jy = ff2_add(a.jy, ff2_mul(sp, ff2{a.Y, a.Yl}));
+      a.e = ff2_add(a.e, ff2_mul(hv, ff2_of(a.S)));
+      const ff2 dv{bc2(d.dv23), bc2(d.dv23_lo)}, dh{bc2(d.dh23), bc2(d.dh23_lo)};
+      a.jx = ff2_add(a.jx, ff2_mul(dv, ff2{a.X3, a.X3l}));
+      a.jy = ff2_add(a.jy, ff2_mul(dv, ff2{a.Y3, a.Y3l}));
+      a.e = ff2_add(a.e, ff2_mul(dh, ff2_of(a.S3)));
+      a.S = a.X = a.Xl = a.Y = a.Yl = bc2(0.f);
+    }
+  } else {
+    constexpr int c = B - kQ;   // lam plane pro_l_plane(c)
+    if constexpr (c == 0) {
+      // rest velocity: x = 0
+      a.l0 = v;
+      const f2 l0F0 = mul2(v, a.F[0]);
+      a.A = mul2(l0F0, a.a0);
+      a.Bx = a.By = a.Dx = bc2(0.f);
+      a.Cs = mul2(l0F0, fma2(bc2(0.25f), a.s, bc2(-0.5f)));
+      a.Fq = mul2(mul2(v, a.Fd[0]), a.a0);
+      a.Ak = a.Bxk = a.Byk = a.Ck = a.Dk = bc2(0.f);
+    } else if constexpr ((c - 1) % 2 == 0) {
+      a.lp = v;
+    } else {
+      // the pair (v, -v) of direction i of shell k shares the even and odd
+      // parts of P, P_x and P_s (x = v.u/E, s = u^2/E)
+      constexpr int k = 1 + (c - 1) / kNDirs, q = pro_l_plane(c - 1);
+      const f2 vx = bc2(d.vx[q]), vy = bc2(d.vy[q]);
+      const f2 x = fma2(vx, a.uxE, mul2(vy, a.uyE));
+      const f2 x2 = mul2(x, x);
+      const f2 Pe = fma2(x2, fma2(x2, bc2(1.0f / 24.0f), a.a1h), a.a0);   // P(+-x) = Pe +- Po
+      const f2 Xo = mul2(x, fma2(x2, bc2(1.0f / 6.0f), a.a1));            // odd part of P and of P_x
+      const f2 Xe = fma2(x2, bc2(0.5f), a.a1);                             // even part of P_x
+      const f2 Se = fma2(bc2(-0.25f), x2, fma2(bc2(0.25f), a.s, bc2(-0.5f)));   // P_s(+-x) = Se -+ x/2
+      const f2 ls = add2(a.lp, v), ld = sub2(a.lp, v);
+      a.Ak = fma2(ls, Pe, fma2(ld, Xo, a.Ak));
+      const f2 lpx = fma2(ld, Xe, mul2(ls, Xo));                       // lp P_x(x) - lm P_x(-x)
+      a.Bxk = fma2(lpx, vx, a.Bxk);
+      a.Byk = fma2(lpx, vy, a.Byk);
+      a.Ck = fma2(ls, Se, fma2(mul2(ld, bc2(-0.5f)), x, a.Ck));
+      a.Dk = fma2(x, fma2(ls, Xo, mul2(ld, Xe)), a.Dk);                // lp x P_x(x) + lm (-x) P_x(-x)
+      if constexpr (c % kNDirs == 0) {
+        a.A = fma2(a.F[k], a.Ak, a.A);
+        a.Bx = fma2(a.F[k], a.Bxk, a.Bx);
+        a.By = fma2(a.F[k], a.Byk, a.By);
+        a.Cs = fma2(a.F[k], a.Ck, a.Cs);
+        a.Dx = fma2(a.F[k], a.Dk, a.Dx);
+        a.Fq = fma2(a.Fd[k], a.Ak, a.Fq);
+        a.Ak = a.Bxk = a.Byk = a.Ck = a.Dk = bc2(0.f);
+      }
+    }
   }
-  G[0] = A;
-  const f2 rE = mul2(rho, invE);
-  G[1] = mul2(rE, fma2(mul2(bc2(2.f), ux), Cs, Bx));
-  G[2] = mul2(rE, fma2(mul2(bc2(2.f), uy), Cs, By));
-  G[3] = mul2(rho, sub2(Fq, mul2(fma2(s, Cs, Dx), invE)));
+}
+
+template <int B, int J>
+__device__ __forceinline__ void node_group_boxes(NodeAcc& a, const float* pring, int o, const DvmConst<float>& d) {
+  node_box<B + J>(a, lds2(pring + ((B + J) % kPSlots) * kAPl + o), d);
+  if constexpr (J + 1 < kPGroup) node_group_boxes<B, J + 1>(a, pring, o, d);
+}
+
+// Groups G .. of the node phase: wait for the group's half of the ring,
+// accumulate its six planes, release the half (the group two ahead refills
+// it).  Returns the group whose copies did not land in time, or kPGroups.
+template <int G, class Refill>
+__device__ __forceinline__ int node_groups(NodeAcc& a, const float* pring, int o, uint64_t* pbar, uint64_t wait_ns,
+                                           const DvmConst<float>& d, Refill refill) {
+  const bool ok = wait_ns != 0 && mbar_wait_bounded(&pbar[G % 2], (uint32_t)((G / 2) & 1), wait_ns);
+  if (ok) node_group_boxes<G * kPGroup, 0>(a, pring, o, d);
+  if (__syncthreads_or(!ok)) return G;
+  if (threadIdx.x == 0 && G + 2 < kPGroups) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    refill(G + 2);
+  }
+  if constexpr (G + 1 < kPGroups) return node_groups<G + 1>(a, pring, o, pbar, wait_ns, d, refill);
+  return kPGroups;
 }
 
 // Cotangent in (rho, u, E) to the cotangent in m = (rho, j_x, j_y, e).
@@ -209,6 +305,7 @@ __global__ void __launch_bounds__(kAThr, 3)
   float* invr = reinterpret_cast<float*>(smem_raw + kRingBytes + kProdBytes);
   float4* ctab = reinterpret_cast<float4*>(smem_raw + kRingBytes + kProdBytes + kInvrBytes);   // [kTT + 4][kANP]
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + kRingBytes + kProdBytes + kInvrBytes + kTabBytes);
+  uint64_t* pbar = bar + kAS;                   // the node phase's two halves
 
   // radial tile: blocks 0 .. na - 1 take tiles a0 .., the rest tiles b0 ..
   const int tx = (int)blockIdx.x < na ? a0 + (int)blockIdx.x : b0 + (int)blockIdx.x - na;
@@ -226,11 +323,26 @@ __global__ void __launch_bounds__(kAThr, 3)
     tma_load_3d(st + 2 * kAPl, &tmap_l, r0 - kLeft, t0, q1, &bar[s]);
     tma_load_3d(st + 3 * kAPl, &tmap_l, r0 - kLeft, t0, q2, &bar[s]);
   };
+  // node-phase group g (boxes 6g .. 6g + 5) into its half of the ring
+  auto issue_group = [&](int g) {
+    mbar_arrive_expect_tx(&pbar[g % 2], (uint32_t)(kPGroup * kAPl * 4));
+    for (int j = 0; j < kPGroup; ++j) {
+      const int b = g * kPGroup + j;
+      float* dst = prod + (b % kPSlots) * kAPl;
+      if (b < kQ)
+        tma_load_3d(dst, &tmap_f, r0 - kLeft, t0, pro_f_plane(b), &pbar[g % 2]);
+      else
+        tma_load_3d(dst, &tmap_l, r0 - kLeft, t0, pro_l_plane(b - kQ), &pbar[g % 2]);
+    }
+  };
   if (tid == 0) {
     tma_prefetch_desc(&tmap_f);
     tma_prefetch_desc(&tmap_l);
-    for (int s = 0; s < kAS; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < kAS + 2; ++s) mbar_init(&bar[s], 1);
     mbar_fence_init();
+    issue_group(0);
+    issue_group(1);
+    for (int s = 0; s < kAS && s < kANP; ++s) issue_pair(s, s);
   }
   if (tid < kTileR) invr[tid] = r0 + tid < p.n_r ? p.inv_r_f[r0 + tid] : 1.f;
   // Courant entries of the stored rows t0 .. t0 + kTT + 3 (theta rows t0 - 2 .. t0 + kTT + 1)
@@ -249,8 +361,6 @@ __global__ void __launch_bounds__(kAThr, 3)
     ctab[w * kANP + pr].w = __int_as_float(__float_as_int(ctab[w * kANP + pr].w) | (m << 2));
   }
   __syncthreads();
-  if (tid == 0)
-    for (int s = 0; s < kAS && s < kANP; ++s) issue_pair(s, s);
 
   // ---- this thread's two nodes ---------------------------------------------
   const int warp = tid >> 5, lane = tid & 31;
@@ -259,38 +369,55 @@ __global__ void __launch_bounds__(kAThr, 3)
   const int t = t0 + rl, r = r0 + j2;
   const bool row_ok = t < p.n_theta;
   const bool v0 = row_ok && r < p.n_r, v1 = row_ok && r + 1 < p.n_r;
-  const int srow = min(t, p.n_theta - 1) + kGhostRows;   // rows past the grid read the last row
+  const int srow = t + kGhostRows;
   const size_t plane_out = (size_t)p.rows * p.pitch;
   const f2 decay = bc2((float)p.decay);
-  f2 gs[4] = {bc2(0.f), bc2(0.f), bc2(0.f), bc2(0.f)};
-  const size_t off = (size_t)srow * p.pitch + r;
+  const int row = rl + 2;                       // window row of this thread's nodes
+  const int o_node = row * kWinR + kLeft + j2;  // first node in a window plane
+  f2 gs[4];
+  f2 lam0;                                      // lam of the rest velocity
   {
-    // (1 - d) g of both nodes from global memory, while the first pairs'
-    // windows land (their copies then mostly hit L2); columns past n_r read
-    // the row's padding (r + 1 < pitch), their results are never stored
-    f2 rho, ux, uy, E;
-    bool ok0, ok1;
-    state_pair([&](int q) { return ldg2(f + off + (size_t)q * plane_out); }, d, rho, ux, uy, E, ok0, ok1);
-    if ((v0 && !ok0) || (v1 && !ok1)) atomicOr(p.status, PCLB_FLAG_NONPHYS);
+    // (1 - d) g of both nodes; rows past the grid see the ghost rows or the
+    // copies' zero fill, columns past n_r zero fill: never stored
+    NodeAcc a;
+    const int bad = node_groups<0>(a, prod, o_node, pbar, p.wait_ns, d, issue_group);
+    if (bad < kPGroups) {
+      // a copy did not land in time: report it and give the copies still in
+      // flight (the group after the one that failed, the first two pairs) a
+      // bounded time to finish before the block exits
+      if (tid == 0) {
+        atomicOr(p.status, PCLB_FLAG_TIMEOUT);
+        mbar_wait_bounded(&pbar[bad % 2], (uint32_t)((bad / 2) & 1), kDefaultWaitNs);
+        if (bad + 1 < kPGroups) mbar_wait_bounded(&pbar[(bad + 1) % 2], (uint32_t)(((bad + 1) / 2) & 1), kDefaultWaitNs);
+        for (int s = 0; s < kAS && s < kANP; ++s) mbar_wait_bounded(&bar[s], 0u, kDefaultWaitNs);
+      }
+      return;
+    }
+    if ((v0 && !a.ok0) || (v1 && !a.ok1)) atomicOr(p.status, PCLB_FLAG_NONPHYS);
     f2 G[4], g[4];
-    eq_cotangent2(rho, ux, uy, E, d, [&](int q) { return ldg2(lam_in + off + (size_t)q * plane_out); }, G);
-    to_moment_cotangent2(rho, ux, uy, E, G, g);
+    G[0] = a.A;
+    const f2 rE = mul2(a.rh, a.invE);
+    G[1] = mul2(rE, fma2(mul2(bc2(2.f), a.ux), a.Cs, a.Bx));
+    G[2] = mul2(rE, fma2(mul2(bc2(2.f), a.uy), a.Cs, a.By));
+    G[3] = mul2(a.rh, sub2(a.Fq, mul2(fma2(a.s, a.Cs, a.Dx), a.invE)));
+    to_moment_cotangent2(a.rh, a.ux, a.uy, a.E, G, g);
+    lam0 = a.l0;
     const f2 omd = sub2(bc2(1.f), decay);
 #pragma unroll
     for (int j = 0; j < 4; ++j) gs[j] = mul2(omd, g[j]);
     // the cotangent the ghost nodes return to the two nodes next to each wall
     if (row_ok && (r < 2 || r + 3 >= p.n_r)) {
       auto wall = [&](int rr) {
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
         auto add = [&](int side, int node) {
-          const float4 w = *reinterpret_cast<const float4*>(gwall + ((size_t)(side * 2 + node) * p.n_theta + t) * 4);
-          a.x += w.x; a.y += w.y; a.z += w.z; a.w += w.w;
+          const float4 x = *reinterpret_cast<const float4*>(gwall + ((size_t)(side * 2 + node) * p.n_theta + t) * 4);
+          w.x += x.x; w.y += x.y; w.z += x.z; w.w += x.w;
         };
         if (rr == 0) add(0, 0);
         if (rr == 1) add(0, 1);
         if (rr == p.n_r - 1) add(1, 0);
         if (rr == p.n_r - 2) add(1, 1);
-        return a;
+        return w;
       };
       const float4 w0 = wall(r), w1 = wall(r + 1);
       gs[0] = add2(gs[0], mk2(w0.x, w1.x));
@@ -299,8 +426,6 @@ __global__ void __launch_bounds__(kAThr, 3)
       gs[3] = add2(gs[3], mk2(w0.w, w1.w));
     }
   }
-  const int row = rl + 2;                      // window row of this thread's nodes
-  const int o_node = row * kWinR + kLeft + j2;  // first node in a window plane
   const int p_rad = rl * kRC + j2 + 2;          // its radial product slot
   const int p_az = kAT + row * kTileR + j2;     // its azimuthal product slot
   const f2 my_invr = lds2(invr + j2);
@@ -324,7 +449,7 @@ __global__ void __launch_bounds__(kAThr, 3)
     }
   };
   // rest velocity: no convection
-  store(0, add2(fma2(decay, ldg2(lam_in + off), gs[0]), mul2(gs[3], bc2(d.half_v2[0]))));
+  store(0, add2(fma2(decay, lam0, gs[0]), mul2(gs[3], bc2(d.half_v2[0]))));
 
   // wall tiles: the ghost states of the rows this thread fills (threads 0..15
   // the inner wall, 32..47 the outer wall, one tile row each)
