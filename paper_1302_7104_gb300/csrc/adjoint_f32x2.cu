@@ -7,10 +7,10 @@
 //     (2j, 2j + 1) of its row;
 //   * the node cotangent g of both nodes (Eqs. 3-5, 10-11 differentiated):
 //     the windows of all 33 f planes, then of all 33 lam planes, stream
-//     through a ring of 12 plane slots (two halves of six, one TMA barrier
-//     each) laid over the product buffers, which are free until the pairs
-//     start; the moments in float-float, rounded once, then the equilibrium
-//     cotangent in packed float;
+//     through 20 plane slots (two halves of ten, one TMA barrier each) laid
+//     over the pair ring and the product buffers, which are free until the
+//     pairs start; the moments in float-float, rounded once, then the
+//     equilibrium cotangent in packed float;
 //   * the pairs of opposite velocities stream their f and lam windows over
 //     [r0-4, r0+36) x [t0-2, t0+18) through a 2-stage TMA ring; per pair,
 //     phase (A) forms lam(n) dM(n)/dD and lam(n) dM(n)/dDp of every node whose
@@ -49,9 +49,19 @@ constexpr int kInvrBytes = kTileR * 4;
 constexpr int kTabBytes = (kTT + 4) * kANP * 16;
 constexpr int kASmem = kRingBytes + kProdBytes + kInvrBytes + kTabBytes + 8 * (kAS + 2);
 // node phase: 66 plane windows (f then lam) in groups of six through 12 slots
-constexpr int kPSlots = 12, kPGroup = 6, kPBoxes = 2 * kQ, kPGroups = kPBoxes / kPGroup;
-static_assert(kPSlots * kAPl * 4 <= kProdBytes, "node-phase ring inside the product buffers");
-static_assert(kPBoxes % kPGroup == 0 && kPSlots == 2 * kPGroup, "two halves of whole groups");
+// node phase: 66 plane windows (f then lam) in groups of ten through 20
+// slots laid over the pair ring and the product buffers, which are free until
+// the pairs start.  Even groups use slots 10..19 (product buffers), odd
+// groups slots 0..9 (the pair ring's stages and two product slots): the last
+// group (six planes) is even, so the pair ring is free for the first two
+// pairs once group 5 has been read.
+constexpr int kPGroup = 10, kPBoxes = 2 * kQ, kPGroups = (kPBoxes + kPGroup - 1) / kPGroup;
+static_assert(2 * kPGroup * kAPl * 4 <= kRingBytes + kProdBytes, "node-phase slots inside ring and products");
+static_assert(kPGroups == 7 && kPGroup * kAPl * 4 >= kRingBytes, "the last group is even; odd groups cover the ring");
+__host__ __device__ constexpr int node_group_size(int g) {
+  return (g + 1) * kPGroup <= kPBoxes ? kPGroup : kPBoxes - g * kPGroup;
+}
+__host__ __device__ constexpr int node_slot(int b) { return (b / kPGroup) % 2 == 0 ? kPGroup + b % kPGroup : b % kPGroup; }
 static_assert(kTT == 16 && kAThr == 256, "thread layout: 8 warps of two 16-thread rows");
 static_assert((kAPl * 4) % 128 == 0, "TMA destinations must stay 128-byte aligned");
 static_assert(kProdBytes % 16 == 0 && (kRingBytes + kProdBytes + kInvrBytes) % 16 == 0, "float4 table alignment");
@@ -61,12 +71,13 @@ __device__ __forceinline__ f2 lds2(const float* p) { return *reinterpret_cast<co
 __device__ __forceinline__ void sts2(float* p, f2 v) { *reinterpret_cast<float2*>(p) = v; }
 
 // mwb_partials of two nodes: MD = a + K (ar + br (ar - s br)), MDp = -(1 + s)
-// K ar^2 with ar, br = |D|, |Dp| / (|D| + |Dp|) (0 when the sum is below the
-// smallest normal) and s the sign of D Dp (0 when either is 0).
+// K ar^2 with ar, br = |D|, |Dp| / max(|D| + |Dp|, smallest normal) (both 0
+// when D = Dp = 0) and s the sign of D Dp (0 when either is 0).  The scalar
+// form takes ar = br = 0 for a subnormal sum; the maximum saves a compare
+// and a select per node and differs only there.
 __device__ __forceinline__ void mwb_partials2(f2 a, f2 K, f2 D, f2 Dp, f2& MD, f2& MDp) {
   const f2 aD = abs2(D), aP = abs2(Dp), n = add2(aD, aP);
-  const f2 rn = mk2(n.x >= smallest_normal<float>() ? recip_fast(n.x) : 0.f,
-                    n.y >= smallest_normal<float>() ? recip_fast(n.y) : 0.f);
+  const f2 rn = mk2(recip_fast(fmaxf(n.x, smallest_normal<float>())), recip_fast(fmaxf(n.y, smallest_normal<float>())));
   const f2 ar = mul2(aD, rn), br = mul2(aP, rn);
   const f2 pr = mul2(D, Dp);
   const f2 s = mk2(fminf(aD.x, aP.x) > 0.f ? copysignf(1.f, pr.x) : 0.f,
@@ -260,26 +271,30 @@ __device__ __forceinline__ void node_box(NodeAcc& a, f2 v, const DvmConst<float>
   }
 }
 
-template <int B, int J>
+template <int B, int J, int N>
 __device__ __forceinline__ void node_group_boxes(NodeAcc& a, const float* pring, int o, const DvmConst<float>& d) {
-  node_box<B + J>(a, lds2(pring + ((B + J) % kPSlots) * kAPl + o), d);
-  if constexpr (J + 1 < kPGroup) node_group_boxes<B, J + 1>(a, pring, o, d);
+  node_box<B + J>(a, lds2(pring + node_slot(B + J) * kAPl + o), d);
+  if constexpr (J + 1 < N) node_group_boxes<B, J + 1, N>(a, pring, o, d);
 }
 
-// Groups G .. of the node phase: wait for the group's half of the ring,
-// accumulate its six planes, release the half (the group two ahead refills
-// it).  Returns the group whose copies did not land in time, or kPGroups.
-template <int G, class Refill>
+// Groups G .. of the node phase: wait for the group's half of the slots,
+// accumulate its planes, release the half (the group two ahead refills it;
+// after the last odd group, the first two pairs take the ring).  Returns the
+// group whose copies did not land in time, or kPGroups.
+template <int G, class Refill, class Prime>
 __device__ __forceinline__ int node_groups(NodeAcc& a, const float* pring, int o, uint64_t* pbar, uint64_t wait_ns,
-                                           const DvmConst<float>& d, Refill refill) {
+                                           const DvmConst<float>& d, Refill refill, Prime prime) {
   const bool ok = wait_ns != 0 && mbar_wait_bounded(&pbar[G % 2], (uint32_t)((G / 2) & 1), wait_ns);
-  if (ok) node_group_boxes<G * kPGroup, 0>(a, pring, o, d);
+  if (ok) node_group_boxes<G * kPGroup, 0, node_group_size(G)>(a, pring, o, d);
   if (__syncthreads_or(!ok)) return G;
-  if (threadIdx.x == 0 && G + 2 < kPGroups) {
+  if (threadIdx.x == 0 && (G + 2 < kPGroups || G == kPGroups - 2)) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    refill(G + 2);
+    if (G + 2 < kPGroups)
+      refill(G + 2);
+    else
+      prime();
   }
-  if constexpr (G + 1 < kPGroups) return node_groups<G + 1>(a, pring, o, pbar, wait_ns, d, refill);
+  if constexpr (G + 1 < kPGroups) return node_groups<G + 1>(a, pring, o, pbar, wait_ns, d, refill, prime);
   return kPGroups;
 }
 
@@ -325,10 +340,11 @@ __global__ void __launch_bounds__(kAThr, 3)
   };
   // node-phase group g (boxes 6g .. 6g + 5) into its half of the ring
   auto issue_group = [&](int g) {
-    mbar_arrive_expect_tx(&pbar[g % 2], (uint32_t)(kPGroup * kAPl * 4));
-    for (int j = 0; j < kPGroup; ++j) {
+    const int nb = node_group_size(g);
+    mbar_arrive_expect_tx(&pbar[g % 2], (uint32_t)(nb * kAPl * 4));
+    for (int j = 0; j < nb; ++j) {
       const int b = g * kPGroup + j;
-      float* dst = prod + (b % kPSlots) * kAPl;
+      float* dst = ring + node_slot(b) * kAPl;
       if (b < kQ)
         tma_load_3d(dst, &tmap_f, r0 - kLeft, t0, pro_f_plane(b), &pbar[g % 2]);
       else
@@ -342,8 +358,10 @@ __global__ void __launch_bounds__(kAThr, 3)
     mbar_fence_init();
     issue_group(0);
     issue_group(1);
-    for (int s = 0; s < kAS && s < kANP; ++s) issue_pair(s, s);
   }
+  auto prime_pairs = [&]() {
+    for (int s = 0; s < kAS && s < kANP; ++s) issue_pair(s, s);
+  };
   if (tid < kTileR) invr[tid] = r0 + tid < p.n_r ? p.inv_r_f[r0 + tid] : 1.f;
   // Courant entries of the stored rows t0 .. t0 + kTT + 3 (theta rows t0 - 2 .. t0 + kTT + 1)
   for (int i = tid; i < (kTT + 4) * kANP; i += kAThr) {
@@ -380,16 +398,17 @@ __global__ void __launch_bounds__(kAThr, 3)
     // (1 - d) g of both nodes; rows past the grid see the ghost rows or the
     // copies' zero fill, columns past n_r zero fill: never stored
     NodeAcc a;
-    const int bad = node_groups<0>(a, prod, o_node, pbar, p.wait_ns, d, issue_group);
+    const int bad = node_groups<0>(a, ring, o_node, pbar, p.wait_ns, d, issue_group, prime_pairs);
     if (bad < kPGroups) {
       // a copy did not land in time: report it and give the copies still in
-      // flight (the group after the one that failed, the first two pairs) a
-      // bounded time to finish before the block exits
+      // flight (the failed group, the one after it, and the first two pairs
+      // once they were issued) a bounded time to finish before the block exits
       if (tid == 0) {
         atomicOr(p.status, PCLB_FLAG_TIMEOUT);
         mbar_wait_bounded(&pbar[bad % 2], (uint32_t)((bad / 2) & 1), kDefaultWaitNs);
         if (bad + 1 < kPGroups) mbar_wait_bounded(&pbar[(bad + 1) % 2], (uint32_t)(((bad + 1) / 2) & 1), kDefaultWaitNs);
-        for (int s = 0; s < kAS && s < kANP; ++s) mbar_wait_bounded(&bar[s], 0u, kDefaultWaitNs);
+        if (bad == kPGroups - 1)
+          for (int s = 0; s < kAS && s < kANP; ++s) mbar_wait_bounded(&bar[s], 0u, kDefaultWaitNs);
       }
       return;
     }
