@@ -6,11 +6,11 @@
 //   * tile 32 (r) x 16 (theta), 256 threads; thread (row, 2j) owns the nodes
 //     (2j, 2j + 1) of its row;
 //   * the node cotangent g of both nodes (Eqs. 3-5, 10-11 differentiated):
-//     the windows of all 33 f planes, then of all 33 lam planes, stream
-//     through 20 plane slots (two halves of ten, one TMA barrier each) laid
-//     over the pair ring and the product buffers, which are free until the
-//     pairs start; the moments in float-float, rounded once, then the
-//     equilibrium cotangent in packed float;
+//     the tile's nodes of all 33 f planes, then of all 33 lam planes, stream
+//     through 30 tile-sized slots (two halves of fifteen, one TMA barrier
+//     each) laid over the pair ring and the product buffers, which are free
+//     until the pairs start; the moments in float-float, rounded once, then
+//     the equilibrium cotangent in packed float;
 //   * the pairs of opposite velocities stream their f and lam windows over
 //     [r0-4, r0+36) x [t0-2, t0+18) through a 2-stage TMA ring; per pair,
 //     phase (A) forms lam(n) dM(n)/dD and lam(n) dM(n)/dDp of every node whose
@@ -49,15 +49,18 @@ constexpr int kInvrBytes = kTileR * 4;
 constexpr int kTabBytes = (kTT + 4) * kANP * 16;
 constexpr int kASmem = kRingBytes + kProdBytes + kInvrBytes + kTabBytes + 8 * (kAS + 2);
 // node phase: 66 plane windows (f then lam) in groups of six through 12 slots
-// node phase: 66 plane windows (f then lam) in groups of ten through 20
-// slots laid over the pair ring and the product buffers, which are free until
-// the pairs start.  Even groups use slots 10..19 (product buffers), odd
-// groups slots 0..9 (the pair ring's stages and two product slots): the last
-// group (six planes) is even, so the pair ring is free for the first two
-// pairs once group 5 has been read.
-constexpr int kPGroup = 10, kPBoxes = 2 * kQ, kPGroups = (kPBoxes + kPGroup - 1) / kPGroup;
-static_assert(2 * kPGroup * kAPl * 4 <= kRingBytes + kProdBytes, "node-phase slots inside ring and products");
-static_assert(kPGroups == 7 && kPGroup * kAPl * 4 >= kRingBytes, "the last group is even; odd groups cover the ring");
+// node phase: 66 tile boxes (32 x 16 nodes of one plane, f then lam) in
+// groups of fifteen through 30 slots laid over the pair ring and the product
+// buffers, which are free until the pairs start.  Even groups use slots
+// 15..29 (product buffers), odd groups slots 0..14 (the pair ring's stages
+// and the start of the product buffers): the last group (six planes) is
+// even, so the pair ring is free for the first two pairs once group 3 has
+// been read.
+constexpr int kNPl = kTileR * kTT;               // floats per node-phase box
+constexpr int kPGroup = 15, kPBoxes = 2 * kQ, kPGroups = (kPBoxes + kPGroup - 1) / kPGroup;
+static_assert(2 * kPGroup * kNPl * 4 <= kRingBytes + kProdBytes, "node-phase slots inside ring and products");
+static_assert(kPGroups == 5 && kPGroup * kNPl * 4 >= kRingBytes, "the last group is even; odd groups cover the ring");
+static_assert((kNPl * 4) % 128 == 0, "TMA destinations must stay 128-byte aligned");
 __host__ __device__ constexpr int node_group_size(int g) {
   return (g + 1) * kPGroup <= kPBoxes ? kPGroup : kPBoxes - g * kPGroup;
 }
@@ -273,7 +276,7 @@ __device__ __forceinline__ void node_box(NodeAcc& a, f2 v, const DvmConst<float>
 
 template <int B, int J, int N>
 __device__ __forceinline__ void node_group_boxes(NodeAcc& a, const float* pring, int o, const DvmConst<float>& d) {
-  node_box<B + J>(a, lds2(pring + node_slot(B + J) * kAPl + o), d);
+  node_box<B + J>(a, lds2(pring + node_slot(B + J) * kNPl + o), d);
   if constexpr (J + 1 < N) node_group_boxes<B, J + 1, N>(a, pring, o, d);
 }
 
@@ -311,6 +314,7 @@ __device__ __forceinline__ void to_moment_cotangent2(f2 rho, f2 ux, f2 uy, f2 E,
 
 __global__ void __launch_bounds__(kAThr, 3)
     adjoint_pair_f32x2(const __grid_constant__ CUtensorMap tmap_f, const __grid_constant__ CUtensorMap tmap_l,
+                       const __grid_constant__ CUtensorMap tmap_fn, const __grid_constant__ CUtensorMap tmap_ln,
                        const float* __restrict__ f, const float* __restrict__ lam_in, float* __restrict__ lam_out,
                        const EqParams<float>* __restrict__ ghost, const float* __restrict__ gwall, int a0, int na,
                        int b0, const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<float> d) {
@@ -341,19 +345,21 @@ __global__ void __launch_bounds__(kAThr, 3)
   // node-phase group g (boxes 6g .. 6g + 5) into its half of the ring
   auto issue_group = [&](int g) {
     const int nb = node_group_size(g);
-    mbar_arrive_expect_tx(&pbar[g % 2], (uint32_t)(nb * kAPl * 4));
+    mbar_arrive_expect_tx(&pbar[g % 2], (uint32_t)(nb * kNPl * 4));
     for (int j = 0; j < nb; ++j) {
       const int b = g * kPGroup + j;
-      float* dst = ring + node_slot(b) * kAPl;
+      float* dst = ring + node_slot(b) * kNPl;
       if (b < kQ)
-        tma_load_3d(dst, &tmap_f, r0 - kLeft, t0, pro_f_plane(b), &pbar[g % 2]);
+        tma_load_3d(dst, &tmap_fn, r0, t0 + kGhostRows, pro_f_plane(b), &pbar[g % 2]);
       else
-        tma_load_3d(dst, &tmap_l, r0 - kLeft, t0, pro_l_plane(b - kQ), &pbar[g % 2]);
+        tma_load_3d(dst, &tmap_ln, r0, t0 + kGhostRows, pro_l_plane(b - kQ), &pbar[g % 2]);
     }
   };
   if (tid == 0) {
     tma_prefetch_desc(&tmap_f);
     tma_prefetch_desc(&tmap_l);
+    tma_prefetch_desc(&tmap_fn);
+    tma_prefetch_desc(&tmap_ln);
     for (int s = 0; s < kAS + 2; ++s) mbar_init(&bar[s], 1);
     mbar_fence_init();
     issue_group(0);
@@ -398,7 +404,7 @@ __global__ void __launch_bounds__(kAThr, 3)
     // (1 - d) g of both nodes; rows past the grid see the ghost rows or the
     // copies' zero fill, columns past n_r zero fill: never stored
     NodeAcc a;
-    const int bad = node_groups<0>(a, ring, o_node, pbar, p.wait_ns, d, issue_group, prime_pairs);
+    const int bad = node_groups<0>(a, ring, rl * kTileR + j2, pbar, p.wait_ns, d, issue_group, prime_pairs);
     if (bad < kPGroups) {
       // a copy did not land in time: report it and give the copies still in
       // flight (the failed group, the one after it, and the first two pairs
@@ -642,7 +648,8 @@ __global__ void __launch_bounds__(kAThr, 3)
 
 }  // namespace
 
-cudaError_t launch_adjoint_pairs_f32(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, const float* f,
+cudaError_t launch_adjoint_pairs_f32(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, const CUtensorMap* tmap_fn,
+                                     const CUtensorMap* tmap_ln, const float* f,
                                      const float* lam_in, float* lam_out, const EqParams<float>* ghost,
                                      const float* gwall, int a0, int na, int b0, int nx, const StepParams& p,
                                      const DvmConst<float>& d, cudaStream_t s) {
@@ -652,8 +659,8 @@ cudaError_t launch_adjoint_pairs_f32(const CUtensorMap* tmap_f, const CUtensorMa
     if (e != cudaSuccess) return e;
   }
   const dim3 grid((unsigned)nx, (unsigned)((p.n_theta + kTT - 1) / kTT));
-  adjoint_pair_f32x2<<<grid, kAThr, kASmem, s>>>(*tmap_f, *tmap_l, f, lam_in, lam_out, ghost, gwall, a0, na, b0, p,
-                                                 d);
+  adjoint_pair_f32x2<<<grid, kAThr, kASmem, s>>>(*tmap_f, *tmap_l, *tmap_fn, *tmap_ln, f, lam_in, lam_out, ghost, gwall,
+                                                 a0, na, b0, p, d);
   return cudaGetLastError();
 }
 

@@ -619,7 +619,8 @@ __global__ void __launch_bounds__(AdjSize<T>::threads, AdjTile<T>::min_blocks)
 // tile 0 and the tiles with r0 >= n_r - 33; they run on the side stream after
 // the wall kernel while the interior tiles run on the main stream.
 template <class T>
-cudaError_t launch_adjoint(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, const T* f, const T* lam_in,
+cudaError_t launch_adjoint(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, const CUtensorMap* tmap_fn,
+                           const CUtensorMap* tmap_ln, const T* f, const T* lam_in,
                            T* lam_out, const AdjScratch& ws, const StepParams& p, const DvmConst<T>& d,
                            cudaStream_t stream, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
   EqParams<T>* ghost = reinterpret_cast<EqParams<T>*>(ws.ghost);
@@ -636,10 +637,12 @@ cudaError_t launch_adjoint(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l,
     // FP32: the packed two-nodes-per-thread pair kernel (adjoint_f32x2.cu)
     e = cudaGetLastError();
     if (e == cudaSuccess)
-      e = launch_adjoint_pairs_f32(tmap_f, tmap_l, f, lam_in, lam_out, ghost, gwall, 0, 1, b0, 1 + (nt - b0), p, d,
+      e = launch_adjoint_pairs_f32(tmap_f, tmap_l, tmap_fn, tmap_ln, f, lam_in, lam_out, ghost, gwall, 0, 1, b0,
+                                   1 + (nt - b0), p, d,
                                    side);
     if (e == cudaSuccess && n_interior > 0)
-      e = launch_adjoint_pairs_f32(tmap_f, tmap_l, f, lam_in, lam_out, ghost, gwall, 1, n_interior, 0, n_interior,
+      e = launch_adjoint_pairs_f32(tmap_f, tmap_l, tmap_fn, tmap_ln, f, lam_in, lam_out, ghost, gwall, 1, n_interior,
+                                   0, n_interior,
                                    p, d, stream);
   } else {
     static std::atomic<unsigned long long> configured{0};
@@ -675,10 +678,12 @@ AdjScratch adjoint_scratch(unsigned char* base, int n_theta, int elem) {
   return s;
 }
 
-template cudaError_t launch_adjoint<float>(const CUtensorMap*, const CUtensorMap*, const float*, const float*, float*,
+template cudaError_t launch_adjoint<float>(const CUtensorMap*, const CUtensorMap*, const CUtensorMap*,
+                                           const CUtensorMap*, const float*, const float*, float*,
                                            const AdjScratch&, const StepParams&, const DvmConst<float>&, cudaStream_t,
                                            cudaStream_t, cudaEvent_t, cudaEvent_t);
-template cudaError_t launch_adjoint<double>(const CUtensorMap*, const CUtensorMap*, const double*, const double*,
+template cudaError_t launch_adjoint<double>(const CUtensorMap*, const CUtensorMap*, const CUtensorMap*,
+                                            const CUtensorMap*, const double*, const double*,
                                             double*, const AdjScratch&, const StepParams&, const DvmConst<double>&,
                                             cudaStream_t, cudaStream_t, cudaEvent_t, cudaEvent_t);
 

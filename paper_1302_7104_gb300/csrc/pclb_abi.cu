@@ -43,7 +43,8 @@ cudaError_t launch_diagnostics(const T*, double*, double*, const StepParams&, co
 template <class T>
 cudaError_t launch_noneq(const T*, T*, int, const StepParams&, const DvmConst<T>&, cudaStream_t);
 template <class T>
-cudaError_t launch_adjoint(const CUtensorMap*, const CUtensorMap*, const T*, const T*, T*, const AdjScratch&,
+cudaError_t launch_adjoint(const CUtensorMap*, const CUtensorMap*, const CUtensorMap*, const CUtensorMap*, const T*,
+                           const T*, T*, const AdjScratch&,
                            const StepParams&, const DvmConst<T>&, cudaStream_t, cudaStream_t, cudaEvent_t,
                            cudaEvent_t);
 template <class T>
@@ -289,15 +290,16 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
 }
 
 // TMA descriptor of one stored distribution (f or lam layout) at `base`,
-// with a box of kWinR columns by box_rows rows and one label.
-pclb_status encode_map(pclb_ctx* ctx, const void* base, int box_rows, CUtensorMap* out) {
+// with a box of box_cols columns (kWinR: a stencil window) by box_rows rows
+// and one label.
+pclb_status encode_map(pclb_ctx* ctx, const void* base, int box_rows, CUtensorMap* out, int box_cols = kWinR) {
   auto enc = get_encode_fn();
   if (!enc) return fail(ctx, PCLB_ECUDA, "cuTensorMapEncodeTiled is not available from the CUDA driver");
   if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return fail(ctx, PCLB_EINVAL, "state buffer not 16-byte aligned");
   const size_t es = elem_size(ctx->prec);
   cuuint64_t dims[3] = {(cuuint64_t)ctx->grid.n_r, (cuuint64_t)ctx->sp.rows, (cuuint64_t)(1 + 4 * ctx->dvm.n_dirs)};
   cuuint64_t strides[2] = {(cuuint64_t)ctx->sp.pitch * es, (cuuint64_t)ctx->sp.pitch * ctx->sp.rows * es};
-  cuuint32_t box[3] = {(cuuint32_t)kWinR, (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(out, ctx->prec == PCLB_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                    3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -307,6 +309,13 @@ pclb_status encode_map(pclb_ctx* ctx, const void* base, int box_rows, CUtensorMa
 }
 
 int adj_box_rows(const pclb_ctx* ctx) { return (ctx->prec == PCLB_FP64 ? kAdjRows64 : kAdjRows32) + 4; }
+
+// The node-phase descriptor of the FP32 adjoint: one tile, kTileR x kAdjRows32
+// (unused for FP64).
+pclb_status encode_node_map(pclb_ctx* ctx, const void* base, CUtensorMap* out) {
+  if (ctx->prec != PCLB_FP32) return PCLB_OK;
+  return encode_map(ctx, base, kAdjRows32, out, kTileR);
+}
 
 pclb_status make_tmap(pclb_ctx* ctx, int which) {
   return encode_map(ctx, ctx->ws + ctx->lay.f[which], ctx->prec == PCLB_FP32 ? kTileT32 + 4 : kWinT,
@@ -405,7 +414,7 @@ pclb_status do_step(pclb_ctx* ctx, int n) {
 }
 
 template <class T>
-pclb_status do_adjoint(pclb_ctx* ctx, const CUtensorMap* tmap_f, const void* f) {
+pclb_status do_adjoint(pclb_ctx* ctx, const CUtensorMap* tmap_f, const CUtensorMap* tmap_fn, const void* f) {
   if (!ctx->side) {
     // created on first use: the side stream (highest priority, so that the
     // wall tiles are scheduled as soon as their inputs are ready) and the
@@ -419,7 +428,8 @@ pclb_status do_adjoint(pclb_ctx* ctx, const CUtensorMap* tmap_f, const void* f) 
   }
   const int src = ctx->cur_lam, dst = 1 - ctx->cur_lam;
   const AdjScratch ws = adjoint_scratch(ctx->ws + ctx->lay.adj_scratch, ctx->grid.n_theta, (int)sizeof(T));
-  cudaError_t e = launch_adjoint<T>(tmap_f, &ctx->tmap_adj[3 + src], reinterpret_cast<const T*>(f),
+  cudaError_t e = launch_adjoint<T>(tmap_f, &ctx->tmap_adj[3 + src], tmap_fn, &ctx->tmap_node[3 + src],
+                                    reinterpret_cast<const T*>(f),
                                     reinterpret_cast<const T*>(ctx->ws + ctx->lay.lam[src]),
                                     reinterpret_cast<T*>(ctx->ws + ctx->lay.lam[dst]), ws, ctx->sp, dvm_of<T>(ctx),
                                     ctx->stream, ctx->side, ctx->ev_fork, ctx->ev_join);
@@ -826,6 +836,7 @@ pclb_status pclb_create(const pclb_grid* grid, const pclb_dvm* dvm, double tau, 
   for (int w = 0; w < 7; ++w) {
     pclb_status s2 = w < 2 ? make_tmap(ctx, w)
                            : encode_map(ctx, ctx->ws + adj_bufs[w - 2], adj_box_rows(ctx), &ctx->tmap_adj[w - 2]);
+    if (s2 == PCLB_OK && w >= 2) s2 = encode_node_map(ctx, ctx->ws + adj_bufs[w - 2], &ctx->tmap_node[w - 2]);
     if (s2 != PCLB_OK) {
       std::snprintf(g_err, sizeof(g_err), "%s", ctx->err);
       delete ctx;
@@ -1222,19 +1233,22 @@ pclb_status pclb_adjoint_state(pclb_ctx* ctx, const void* f_state) {
     return fail(ctx, PCLB_EINVAL, "f_state must be 16-byte aligned");
   if (adjoint_supported(ctx) != PCLB_OK) return PCLB_EUNSUPPORTED;
   if (!ctx->has_lam) return fail(ctx, PCLB_ESTATE, "no adjoint variable: call pclb_lambda_set or pclb_moments_vjp");
-  const CUtensorMap* map;
-  CUtensorMap local;
+  const CUtensorMap *map, *node_map;
+  CUtensorMap local, local_node;
   const void* f = f_state;
   if (f_state == nullptr) {
     if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
     map = &ctx->tmap_adj[ctx->cur];
+    node_map = &ctx->tmap_node[ctx->cur];
     f = ctx->ws + ctx->lay.f[ctx->cur];
   } else {
     pclb_status st = encode_map(ctx, f_state, adj_box_rows(ctx), &local);
+    if (st == PCLB_OK) st = encode_node_map(ctx, f_state, &local_node);
     if (st != PCLB_OK) return st;
     map = &local;
+    node_map = &local_node;
   }
-  return ctx->prec == PCLB_FP32 ? do_adjoint<float>(ctx, map, f) : do_adjoint<double>(ctx, map, f);
+  return ctx->prec == PCLB_FP32 ? do_adjoint<float>(ctx, map, node_map, f) : do_adjoint<double>(ctx, map, node_map, f);
 }
 
 pclb_status pclb_adjoint_step(pclb_ctx* ctx, const void* f_n, const void* lam_np1, void* lam_n) {
@@ -1249,8 +1263,8 @@ pclb_status pclb_adjoint_step(pclb_ctx* ctx, const void* f_n, const void* lam_np
   if (e != cudaSuccess) return cuda_fail(ctx, e, "state unpack launch");
   pclb_status st = pclb_lambda_set(ctx, lam_np1);
   if (st != PCLB_OK) return st;
-  st = ctx->prec == PCLB_FP32 ? do_adjoint<float>(ctx, &ctx->tmap_adj[2], adj)
-                               : do_adjoint<double>(ctx, &ctx->tmap_adj[2], adj);
+  st = ctx->prec == PCLB_FP32 ? do_adjoint<float>(ctx, &ctx->tmap_adj[2], &ctx->tmap_node[2], adj)
+                               : do_adjoint<double>(ctx, &ctx->tmap_adj[2], &ctx->tmap_node[2], adj);
   if (st != PCLB_OK) return st;
   return pclb_lambda_get(ctx, lam_n);
 }

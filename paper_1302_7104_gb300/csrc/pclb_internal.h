@@ -190,6 +190,7 @@ struct pclb_ctx {
   bool has_state;
   CUtensorMap tmap[2];        // TMA descriptors of the two f buffers
   CUtensorMap tmap_adj[5];    // adjoint-window descriptors: f[0], f[1], adj_f, lam[0], lam[1]
+  CUtensorMap tmap_node[5];   // FP32 adjoint node-phase descriptors (tile boxes) of the same buffers
   int cur_lam;                // which lam buffer holds the adjoint variable
   bool has_lam;
   pclb::StepParams sp;
