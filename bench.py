@@ -359,7 +359,7 @@ def run_ours(args):
                    "reverse_step_ms": t_rev * 1e3, "reverse_ratio_to_forward": t_rev / per_launch,
                    "roofline": {"bound": "hbm", "achieved": alg / t_adj / 1e9, "peak": hbm, "unit": "GB/s",
                                 "frac": alg / t_adj / 1e9 / hbm, "alg_bytes_per_launch": alg,
-                                "kernel": "pclb::adjoint_pair_kernel<float> (+ adjoint_wall_kernel on a side stream)"}}
+                                "kernel": "pclb::adjoint_pair_f32x2 (+ adjoint_wall_kernel on a side stream)"}}
         del state
 
     # non-equilibrium manifestations (Sec. IV), all four groups, on the same state
