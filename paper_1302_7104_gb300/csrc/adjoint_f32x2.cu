@@ -312,6 +312,55 @@ __device__ __forceinline__ void to_moment_cotangent2(f2 rho, f2 ux, f2 uy, f2 E,
   g[3] = mul2(G[3], inv);
 }
 
+// Phase (A) for one label at this thread's two nodes, its upwind offsets U
+// (columns) and V (window rows) as constants: the products of the MWB
+// partials in r and theta; returns lam of the two nodes.
+template <int U, int V>
+__device__ __forceinline__ f2 products_label(const float* w, const float* wl, float* P, int p_rad, int p_az, f2 a_r,
+                                             f2 k_r, f2 a_t, f2 k_t) {
+  const f2 C = lds2(w);
+  const f2 S2 = lds2(w + 2 * U);                            // f(n + 2u) of both nodes
+  const f2 u1 = U > 0 ? mk2(C.y, S2.x) : mk2(S2.y, C.x);     // f(n + u)
+  f2 MD, MP;
+  mwb_partials2(a_r, k_r, sub2(C, u1), sub2(u1, S2), MD, MP);
+  const f2 lam = lds2(wl);
+  sts2(P + kAR + p_rad, mul2(lam, MD));
+  sts2(P + kBR + p_rad, mul2(lam, MP));
+  const f2 T1 = lds2(w + V), T2 = lds2(w + 2 * V);
+  mwb_partials2(a_t, k_t, sub2(C, T1), sub2(T1, T2), MD, MP);
+  sts2(P + p_az, mul2(lam, MD));
+  sts2(P + p_az + (kBT - kAT), mul2(lam, MP));
+  return lam;
+}
+
+// Phase (A) for both labels of a pair: q1's upwind offsets UR, VT, q2's the
+// opposite ones.
+template <int UR, int VT>
+__device__ __forceinline__ void products_pair(const float* sf, const float* sl, float* pb, int o, int p_rad, int p_az,
+                                              f2 a_r, f2 k_r, f2 a_t, f2 k_t, f2 lam_c[2]) {
+  lam_c[0] = products_label<UR, VT>(sf + o, sl + o, pb, p_rad, p_az, a_r, k_r, a_t, k_t);
+  lam_c[1] = products_label<-UR, -VT>(sf + kAPl + o, sl + kAPl + o, pb + kProd, p_rad, p_az, a_r, k_r, a_t, k_t);
+}
+
+// Radial gather of one label at the two nodes (upwind offset U): A(c) -
+// A(c - u) + B(c - u) - B(c - 2u).
+template <int U>
+__device__ __forceinline__ f2 gather_radial2(const float* P, int p_rad) {
+  const f2 A0 = lds2(P + kAR + p_rad), B0 = lds2(P + kBR + p_rad);
+  const f2 An = lds2(P + kAR + p_rad - 2 * U), Bn = lds2(P + kBR + p_rad - 2 * U);
+  const f2 Au = U > 0 ? mk2(An.y, A0.x) : mk2(A0.y, An.x);
+  const f2 Bu = U > 0 ? mk2(Bn.y, B0.x) : mk2(B0.y, Bn.x);
+  return sub2(add2(sub2(A0, Au), Bu), Bn);
+}
+
+// Azimuthal gather of one label where the rows -2 .. +2 around the node all
+// have their upwind side on one side: the readers of the node at +W, +2W.
+template <int W>
+__device__ __forceinline__ f2 gather_az2(const float* P) {
+  constexpr int DB = kBT - kAT;
+  return sub2(sub2(add2(lds2(P), lds2(P + DB + W)), lds2(P + W)), lds2(P + DB + 2 * W));
+}
+
 __global__ void __launch_bounds__(kAThr, 3)
     adjoint_pair_f32x2(const __grid_constant__ CUtensorMap tmap_f, const __grid_constant__ CUtensorMap tmap_l,
                        const __grid_constant__ CUtensorMap tmap_fn, const __grid_constant__ CUtensorMap tmap_ln,
@@ -517,29 +566,17 @@ __global__ void __launch_bounds__(kAThr, 3)
     const float* sl = st + 2 * kAPl;               // lam q1, lam q2 at + kAPl
     const float4 ce = ctab[row * kANP + pair];
     const int fl_c = __float_as_int(ce.w);
-    const int ur = (fl_c & 1) ? 1 : -1;            // q1 reads n + 1, n + 2 in r
-    const int vt = (fl_c & 2) ? kWinR : -kWinR;    // q1 reads the rows above (+) or below (-)
     const f2 a_r = bc2(ce.x), k_r = bc2(ce.y);
     const f2 a_t = mul2(bc2(ce.z), my_invr), k_t = fma2(neg2(a_t), a_t, a_t);
     f2 lam_c[2];
-#pragma unroll
-    for (int L = 0; L < 2; ++L) {
-      const int u = L ? -ur : ur, v = L ? -vt : vt;
-      const float* w = sf + L * kAPl + o_node;
-      const f2 C = lds2(w);
-      const f2 S2 = lds2(w + 2 * u);               // f(n + 2u) of both nodes
-      const f2 u1 = u > 0 ? mk2(C.y, S2.x) : mk2(S2.y, C.x);   // f(n + u)
-      f2 MD, MP;
-      mwb_partials2(a_r, k_r, sub2(C, u1), sub2(u1, S2), MD, MP);
-      const f2 lam = lds2(sl + L * kAPl + o_node);
-      lam_c[L] = lam;
-      float* P = pb + L * kProd;
-      sts2(P + kAR + p_rad, mul2(lam, MD));
-      sts2(P + kBR + p_rad, mul2(lam, MP));
-      const f2 T1 = lds2(w + v), T2 = lds2(w + 2 * v);
-      mwb_partials2(a_t, k_t, sub2(C, T1), sub2(T1, T2), MD, MP);
-      sts2(P + p_az, mul2(lam, MD));
-      sts2(P + p_az + (kBT - kAT), mul2(lam, MP));
+    // bit 0: q1 reads n + 1, n + 2 in r; bit 1: q1 reads the rows above.  The
+    // two rows of a warp nearly always agree (a label's upwind side changes
+    // at a few theta rows only), so the branch is uniform in practice.
+    switch (fl_c & 3) {
+      case 0: products_pair<-1, -kWinR>(sf, sl, pb, o_node, p_rad, p_az, a_r, k_r, a_t, k_t, lam_c); break;
+      case 1: products_pair<1, -kWinR>(sf, sl, pb, o_node, p_rad, p_az, a_r, k_r, a_t, k_t, lam_c); break;
+      case 2: products_pair<-1, kWinR>(sf, sl, pb, o_node, p_rad, p_az, a_r, k_r, a_t, k_t, lam_c); break;
+      default: products_pair<1, kWinR>(sf, sl, pb, o_node, p_rad, p_az, a_r, k_r, a_t, k_t, lam_c); break;
     }
     if (tid < 64) {
       // halo rows (window rows 0, 1, kTT + 2, kTT + 3), the label whose
@@ -594,27 +631,22 @@ __global__ void __launch_bounds__(kAThr, 3)
     // n = c - u and -M_Dp of n = c - 2u
     if (v0 || v1) {
       f2 acc[2];
-#pragma unroll
-      for (int L = 0; L < 2; ++L) {
-        const float* P = pb + L * kProd;
-        const int u = L ? -ur : ur;
-        const f2 A0 = lds2(P + kAR + p_rad), B0 = lds2(P + kBR + p_rad);
-        const f2 An = lds2(P + kAR + p_rad - 2 * u), Bn = lds2(P + kBR + p_rad - 2 * u);
-        // A(c - u), B(c - u), B(c - 2u) of both nodes
-        const f2 Au = u > 0 ? mk2(An.y, A0.x) : mk2(A0.y, An.x);
-        const f2 Bu = u > 0 ? mk2(Bn.y, B0.x) : mk2(B0.y, Bn.x);
-        acc[L] = sub2(add2(sub2(A0, Au), Bu), Bn);
+      if (fl_c & 1) {
+        acc[0] = gather_radial2<1>(pb, p_rad);
+        acc[1] = gather_radial2<-1>(pb + kProd, p_rad);
+      } else {
+        acc[0] = gather_radial2<-1>(pb, p_rad);
+        acc[1] = gather_radial2<1>(pb + kProd, p_rad);
       }
       const int tneg = fl_c >> 2;                  // bit o: row o - 2 has v_theta < 0 for q1
       constexpr int DB = kBT - kAT;
-      if (tneg == 0 || tneg == 31) {
-        const int V = tneg == 0 ? kTileR : -kTileR;   // q1's readers at +V, +2V; q2's at -V, -2V
-#pragma unroll
-        for (int L = 0; L < 2; ++L) {
-          const int W = L ? -V : V;
-          const float* P = pb + L * kProd + p_az;
-          acc[L] = add2(acc[L], sub2(sub2(add2(lds2(P), lds2(P + DB + W)), lds2(P + W)), lds2(P + DB + 2 * W)));
-        }
+      if (tneg == 0) {
+        // q1's readers at +V, +2V, q2's at -V, -2V (V = one row)
+        acc[0] = add2(acc[0], gather_az2<kTileR>(pb + p_az));
+        acc[1] = add2(acc[1], gather_az2<-kTileR>(pb + kProd + p_az));
+      } else if (tneg == 31) {
+        acc[0] = add2(acc[0], gather_az2<-kTileR>(pb + p_az));
+        acc[1] = add2(acc[1], gather_az2<kTileR>(pb + kProd + p_az));
       } else {
 #pragma unroll
         for (int L = 0; L < 2; ++L) {
