@@ -76,15 +76,19 @@ __device__ __forceinline__ void sts2(float* p, f2 v) { *reinterpret_cast<float2*
 // mwb_partials of two nodes: MD = a + K (ar + br (ar - s br)), MDp = -(1 + s)
 // K ar^2 with ar, br = |D|, |Dp| / max(|D| + |Dp|, smallest normal) (both 0
 // when D = Dp = 0) and s the sign of D Dp (0 when either is 0).  The scalar
-// form takes ar = br = 0 for a subnormal sum; the maximum saves a compare
-// and a select per node and differs only there.
+// form takes ar = br = 0 for a subnormal sum and tests min(|D|, |Dp|) > 0
+// for s; the maximum and the clamped product below save compares and
+// selects per node and differ only where |D| or |Dp| is subnormal.
 __device__ __forceinline__ void mwb_partials2(f2 a, f2 K, f2 D, f2 Dp, f2& MD, f2& MDp) {
   const f2 aD = abs2(D), aP = abs2(Dp), n = add2(aD, aP);
   const f2 rn = mk2(recip_fast(fmaxf(n.x, smallest_normal<float>())), recip_fast(fmaxf(n.y, smallest_normal<float>())));
   const f2 ar = mul2(aD, rn), br = mul2(aP, rn);
   const f2 pr = mul2(D, Dp);
-  const f2 s = mk2(fminf(aD.x, aP.x) > 0.f ? copysignf(1.f, pr.x) : 0.f,
-                   fminf(aD.y, aP.y) > 0.f ? copysignf(1.f, pr.y) : 0.f);
+  // s = sign(D Dp), 0 when either is 0: min(|D|, |Dp|) scaled by 2^126 and
+  // clamped to 1 carries the zero test (the sign of a product is exact even
+  // where it underflows)
+  const f2 zb = mul2(mk2(fminf(aD.x, aP.x), fminf(aD.y, aP.y)), bc2(8.507059173023462e37f));
+  const f2 s = mk2(copysignf(fminf(zb.x, 1.f), pr.x), copysignf(fminf(zb.y, 1.f), pr.y));
   const f2 Ka = mul2(K, ar);
   MD = fma2(K, fma2(br, fma2(neg2(s), br, ar), ar), a);
   MDp = mul2(neg2(add2(bc2(1.f), s)), mul2(Ka, ar));
@@ -342,6 +346,27 @@ __device__ __forceinline__ void products_pair(const float* sf, const float* sl, 
   lam_c[1] = products_label<-UR, -VT>(sf + kAPl + o, sl + kAPl + o, pb + kProd, p_rad, p_az, a_r, k_r, a_t, k_t);
 }
 
+// Products of one halo row (window row rr) at the node pair jj, jj + 1, for
+// the label whose upwind side points into the tile: V = +row for the rows
+// below the tile, -row for those above.
+template <int V>
+__device__ __forceinline__ void halo_row(const float* sf, const float* sl, float* pb, const float4* ctab,
+                                         const float* invr, int pair, int rr, int jj) {
+  const float4 eh = ctab[rr * kANP + pair];
+  const bool q1_up_pos = (__float_as_int(eh.w) & 2) != 0;
+  const int L = (V > 0) == q1_up_pos ? 0 : 1;
+  const f2 ath = mul2(bc2(eh.z), lds2(invr + jj)), kth = fma2(neg2(ath), ath, ath);
+  const int o = rr * kWinR + kLeft + jj;
+  const float* w = sf + L * kAPl + o;
+  const f2 C = lds2(w), T1 = lds2(w + V), T2 = lds2(w + 2 * V);
+  f2 MD, MP;
+  mwb_partials2(ath, kth, sub2(C, T1), sub2(T1, T2), MD, MP);
+  const f2 lam = lds2(sl + L * kAPl + o);
+  float* P = pb + L * kProd + kAT + rr * kTileR + jj;
+  sts2(P, mul2(lam, MD));
+  sts2(P + (kBT - kAT), mul2(lam, MP));
+}
+
 // Radial gather of one label at the two nodes (upwind offset U): A(c) -
 // A(c - u) + B(c - u) - B(c - 2u).
 template <int U>
@@ -580,24 +605,13 @@ __global__ void __launch_bounds__(kAThr, 3)
     }
     if (tid < 64) {
       // halo rows (window rows 0, 1, kTT + 2, kTT + 3), the label whose
-      // upwind side points into the tile: rows below it are read by the
-      // label with its upwind side at +theta
-      const int hrow = tid >> 4, jj = 2 * (tid & 15);
-      const int rr = hrow < 2 ? hrow : kTT + hrow;
-      const float4 eh = ctab[rr * kANP + pair];
-      const bool q1_up_pos = (__float_as_int(eh.w) & 2) != 0;
-      const int L = (hrow < 2) == q1_up_pos ? 0 : 1;
-      const int v = hrow < 2 ? kWinR : -kWinR;
-      const f2 ath = mul2(bc2(eh.z), lds2(invr + jj)), kth = fma2(neg2(ath), ath, ath);
-      const int o = rr * kWinR + kLeft + jj;
-      const float* w = sf + L * kAPl + o;
-      const f2 C = lds2(w), T1 = lds2(w + v), T2 = lds2(w + 2 * v);
-      f2 MD, MP;
-      mwb_partials2(ath, kth, sub2(C, T1), sub2(T1, T2), MD, MP);
-      const f2 lam = lds2(sl + L * kAPl + o);
-      float* P = pb + L * kProd + kAT + rr * kTileR + jj;
-      sts2(P, mul2(lam, MD));
-      sts2(P + (kBT - kAT), mul2(lam, MP));
+      // upwind side points into the tile: warp 0 the rows below the tile
+      // (read by the label with its upwind side at +theta), warp 1 the rows
+      // above it
+      if (tid < 32)
+        halo_row<kWinR>(sf, sl, pb, ctab, invr, pair, tid >> 4, 2 * (tid & 15));
+      else
+        halo_row<-kWinR>(sf, sl, pb, ctab, invr, pair, kTT + 2 + ((tid >> 4) & 1), 2 * (tid & 15));
     } else if (tid < 96) {
       // halo columns: per tile row and label the two columns whose upwind
       // stencils reach the tile, -2, -1 (upwind at larger r) or 32, 33
