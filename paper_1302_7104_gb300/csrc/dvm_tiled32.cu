@@ -262,6 +262,40 @@ __global__ void __launch_bounds__(kGhostThreads)
   }
 }
 
+// One label of a pair at the thread's two nodes with its upwind offsets as
+// constants (SU: columns, SV: rows): the relaxation minus the convection
+// increments in r and theta, summed first and added once.  The two rows of a
+// warp share the offsets nearly everywhere (a label's upwind side changes at
+// a few theta rows only), so the dispatch below is uniform in practice.
+template <int SCH, int SU, int SV, class Store>
+__device__ __forceinline__ void tupd(const float* w, f2 nar, f2 nkr, f2 nat, f2 nkt, f2 fe, f2 decay, int q, Store& store) {
+  const f2 C = lds2(w);
+  const f2 S = lds2(w + 2 * SU);
+  const f2 T1 = lds2(w + SV * kWinR);
+  const f2 T2 = lds2(w + 2 * SV * kWinR);
+  const f2 u1 = SU < 0 ? mk2(S.y, C.x) : mk2(C.y, S.x);
+  const f2 Dr = sub2(C, u1), Dt = sub2(C, T1);
+  f2 dc = mul2(nar, Dr);
+  dc = fma2(nat, Dt, dc);
+  if constexpr (SCH == PCLB_SCHEME_MWB) {
+    dc = fma2(nkr, limiter2_t(Dr, sub2(u1, S)), dc);
+    dc = fma2(nkt, limiter2_t(Dt, sub2(T1, T2)), dc);
+  } else if constexpr (SCH == PCLB_SCHEME_WB) {
+    dc = fma2(mul2(bc2(0.5f), nkr), sub2(Dr, sub2(u1, S)), dc);
+    dc = fma2(mul2(bc2(0.5f), nkt), sub2(Dt, sub2(T1, T2)), dc);
+  } else if constexpr (SCH == PCLB_SCHEME_UPWIND2) {
+    dc = fma2(mul2(bc2(0.5f), nar), sub2(Dr, sub2(u1, S)), dc);
+    dc = fma2(mul2(bc2(0.5f), nat), sub2(Dt, sub2(T1, T2)), dc);
+  } else {
+    const f2 X = lds2(w - 2 * SU);
+    const f2 d1 = SU < 0 ? mk2(C.y, X.x) : mk2(X.y, C.x);
+    const f2 Td = lds2(w - SV * kWinR);
+    dc = fma2(mul2(bc2(0.5f), nkr), sub2(sub2(d1, C), Dr), dc);
+    dc = fma2(mul2(bc2(0.5f), nkt), sub2(sub2(Td, C), Dt), dc);
+  }
+  store(q, add2(fma2(sub2(C, fe), decay, fe), dc));
+}
+
 // Three CTAs per SM (at most 85 registers; a few bytes spill in some
 // instantiations): 12% faster than two CTAs at 124 registers.
 template <int ND, int SCH>
@@ -380,8 +414,6 @@ __global__ void __launch_bounds__(kTThreads, 3)
     if (ok) {
       const float4 tb = tab[pr * kTileT32 + rl];
       const int fl = __float_as_int(tb.w);
-      const int sr = (fl & 1) ? 1 : -1;            // q1: upwind at larger r
-      const int stt = (fl & 2) ? 1 : -1;           // q1: upwind at larger theta
       const f2 nar = bc2(-tb.x), nkr = bc2(-tb.y);
       const f2 nat = mul2(bc2(-tb.z), invr);
       const f2 nkt = fma2(nat, nat, nat);           // -(a - a^2) with a = -nat
@@ -389,35 +421,26 @@ __global__ void __launch_bounds__(kTThreads, 3)
       const f2 wk = k == 1 ? eq.w[1] : (k == 2 ? eq.w[2] : (k == 3 ? eq.w[3] : eq.w[4]));
       f2 fe[2];
       tiled_feq_pair(eq, wk, c.vx[q1], c.vy[q1], fe[0], fe[1]);
-#pragma unroll
-      for (int L = 0; L < 2; ++L) {
-        const int su = L ? -sr : sr, sv = L ? -stt : stt;
-        const float* w = st + L * kTPlane + row * kWinR + col;
-        const f2 C = lds2(w);
-        const f2 S = lds2(w + 2 * su);              // (j-2, j-1) or (j+2, j+3)
-        const f2 T1 = lds2(w + sv * kWinR);
-        const f2 T2 = lds2(w + 2 * sv * kWinR);
-        const f2 u1 = su < 0 ? mk2(S.y, C.x) : mk2(C.y, S.x);   // first upwind neighbours
-        const f2 Dr = sub2(C, u1), Dt = sub2(C, T1);
-        f2 dc = mul2(nar, Dr);
-        dc = fma2(nat, Dt, dc);
-        if constexpr (SCH == PCLB_SCHEME_MWB) {
-          dc = fma2(nkr, limiter2_t(Dr, sub2(u1, S)), dc);
-          dc = fma2(nkt, limiter2_t(Dt, sub2(T1, T2)), dc);
-        } else if constexpr (SCH == PCLB_SCHEME_WB) {
-          dc = fma2(mul2(bc2(0.5f), nkr), sub2(Dr, sub2(u1, S)), dc);
-          dc = fma2(mul2(bc2(0.5f), nkt), sub2(Dt, sub2(T1, T2)), dc);
-        } else if constexpr (SCH == PCLB_SCHEME_UPWIND2) {
-          dc = fma2(mul2(bc2(0.5f), nar), sub2(Dr, sub2(u1, S)), dc);
-          dc = fma2(mul2(bc2(0.5f), nat), sub2(Dt, sub2(T1, T2)), dc);
-        } else {
-          const f2 X = lds2(w - 2 * su);            // the pair on the downwind side
-          const f2 d1 = su < 0 ? mk2(C.y, X.x) : mk2(X.y, C.x);   // first downwind neighbours
-          const f2 Td = lds2(w - sv * kWinR);
-          dc = fma2(mul2(bc2(0.5f), nkr), sub2(sub2(d1, C), Dr), dc);
-          dc = fma2(mul2(bc2(0.5f), nkt), sub2(sub2(Td, C), Dt), dc);
-        }
-        store(L ? q2 : q1, add2(fma2(sub2(C, fe[L]), decay, fe[L]), dc));
+      const float* w0 = st + row * kWinR + col;
+      const float* w1 = w0 + kTPlane;
+      // bit 0: q1's upwind side at larger r; bit 1: at larger theta (q2 the opposite)
+      switch (fl & 3) {
+        case 0:
+          tupd<SCH, -1, -1>(w0, nar, nkr, nat, nkt, fe[0], decay, q1, store);
+          tupd<SCH, 1, 1>(w1, nar, nkr, nat, nkt, fe[1], decay, q2, store);
+          break;
+        case 1:
+          tupd<SCH, 1, -1>(w0, nar, nkr, nat, nkt, fe[0], decay, q1, store);
+          tupd<SCH, -1, 1>(w1, nar, nkr, nat, nkt, fe[1], decay, q2, store);
+          break;
+        case 2:
+          tupd<SCH, -1, 1>(w0, nar, nkr, nat, nkt, fe[0], decay, q1, store);
+          tupd<SCH, 1, -1>(w1, nar, nkr, nat, nkt, fe[1], decay, q2, store);
+          break;
+        default:
+          tupd<SCH, 1, 1>(w0, nar, nkr, nat, nkt, fe[0], decay, q1, store);
+          tupd<SCH, -1, -1>(w1, nar, nkr, nat, nkt, fe[1], decay, q2, store);
+          break;
       }
     }
     // the stage of this pair is read by every thread before it is refilled;
