@@ -122,11 +122,13 @@ typedef struct {
 /* Discrete velocity model (Sec. II A): N_k = 4 shells of n_dirs directions
  * plus the rest velocity, Q = 1 + 4 n_dirs labels.  n_dirs = 8 (the octagon)
  * runs the tuned kernels and every entry point.  n_dirs = 16 and 24 (Table I,
- * rows 2-3; B from that table) run generic kernels for the forward path only:
- * pclb_set_state, pclb_set_f, pclb_get_f, pclb_step (every scheme and
- * relaxation), pclb_moments, pclb_diagnostics, pclb_run_host and the state
- * save / load calls; the reverse-mode entry points, pclb_noneq and
- * pclb_diagnostics_noalloc return PCLB_EUNSUPPORTED for them. */
+ * rows 2-3; B from that table) run the forward path only (in FP32 a tiled
+ * step kernel that streams the opposite-velocity plane pairs, in FP64 and for
+ * the field operations generic kernels): pclb_set_state, pclb_set_f,
+ * pclb_get_f, pclb_step (every scheme and relaxation), pclb_moments,
+ * pclb_diagnostics, pclb_run_host and the state save / load calls; the
+ * reverse-mode entry points, pclb_noneq and pclb_diagnostics_noalloc return
+ * PCLB_EUNSUPPORTED for them. */
 typedef struct {
   int32_t n_dirs;    /* N_i: 8, 16 or 24 */
   double speeds[5];  /* v_0 .. v_4; the paper uses 0, 1, 2.92, 2.99, 4.49 */
