@@ -11,8 +11,9 @@
 //     transformations), then the temperature and the equilibrium factors
 //     (Eqs. 10-11) in float-float, rounded to float once;
 //   * the pairs of opposite velocities (q, q + N_i/2) of each shell then
-//     stream through a ring of shared-memory stages filled by TMA (the two
-//     planes' windows over [r0-4, r0+36) x [t0-2, t0+18)), the copies of the
+//     stream, two pairs per stage, through a ring of four shared-memory
+//     stages filled by TMA (each plane's window over [r0-4, r0+36) x
+//     [t0-2, t0+18)), the copies of the
 //     first pairs landing while the moments are formed (and finding the
 //     tile's lines in L2);
 //   * per pair, the relaxation (Eq. 19 or 18) minus the convection increments
@@ -39,14 +40,15 @@ namespace {
 
 constexpr int kTThreads = 16 * kTileT32;            // 256: two nodes each
 constexpr int kTPlane = kWinR * (kTileT32 + 4);     // floats per plane window (800)
-constexpr int kTStages = 4;                         // ring depth (pairs in flight)
+constexpr int kTStages = 4;                         // ring depth (stages in flight)
+constexpr int kTPPS = 2;                            // pairs per stage: one wait and one barrier per two pairs
 constexpr int kGhostThreads = 32;                   // ghost kernel: one thread per wall row
 static_assert((kTPlane * 4) % 128 == 0, "TMA destinations must stay 128-byte aligned");
 
 template <int ND>
 struct TiledSize {
   static constexpr int Q = 1 + 4 * ND, H = ND / 2, NP = 4 * H;   // labels, pairs per shell, pairs
-  static constexpr int ring_bytes = kTStages * 2 * kTPlane * 4;
+  static constexpr int ring_bytes = kTStages * kTPPS * 2 * kTPlane * 4;
   static constexpr int tab_bytes = NP * kTileT32 * 16;           // one float4 per (pair, row)
   static constexpr int smem = ring_bytes + tab_bytes + 8 * kTStages + 64;
 };
@@ -314,19 +316,24 @@ __global__ void __launch_bounds__(kTThreads, 3)
   const int t0 = blockIdx.y * kTileT32;
   const int tid = threadIdx.x;
 
-  // the two planes of pair pr into stage s (thread 0)
-  auto issue = [&](int pr, int s) {
-    const int q1 = 1 + (pr / H) * ND + pr % H;
-    float* st = ring + s * 2 * kTPlane;
-    mbar_arrive_expect_tx(&full[s], (uint32_t)(2 * kTPlane * 4));
-    tma_load_3d(st, &tmap, r0 - kLeft, t0, q1, &full[s]);
-    tma_load_3d(st + kTPlane, &tmap, r0 - kLeft, t0, q1 + H, &full[s]);
+  // the planes of the kTPPS pairs of stage group sg into stage s (thread 0)
+  auto issue = [&](int sg, int s) {
+    float* st = ring + s * kTPPS * 2 * kTPlane;
+    mbar_arrive_expect_tx(&full[s], (uint32_t)(kTPPS * 2 * kTPlane * 4));
+    for (int pp = 0; pp < kTPPS; ++pp) {
+      const int pr = sg * kTPPS + pp;
+      const int q1 = 1 + (pr / H) * ND + pr % H;
+      tma_load_3d(st + pp * 2 * kTPlane, &tmap, r0 - kLeft, t0, q1, &full[s]);
+      tma_load_3d(st + pp * 2 * kTPlane + kTPlane, &tmap, r0 - kLeft, t0, q1 + H, &full[s]);
+    }
   };
+  constexpr int NS = NP / kTPPS;
+  static_assert(NP % kTPPS == 0, "whole stages");
   if (tid == 0) {
     tma_prefetch_desc(&tmap);
     for (int s = 0; s < kTStages; ++s) mbar_init(&full[s], 1);
     mbar_fence_init();
-    for (int s = 0; s < kTStages && s < NP; ++s) issue(s, s);
+    for (int s = 0; s < kTStages && s < NS; ++s) issue(s, s);
   }
   for (int i = tid; i < NP * kTileT32; i += kTThreads) {   // Courant entries: [pair][row]
     const int pr = i / kTileT32, rl = i % kTileT32;
@@ -392,70 +399,77 @@ __global__ void __launch_bounds__(kTThreads, 3)
   const int row = rl + 2, col = kLeft + j2;
   bool ok = true;
 #pragma unroll 1
-  for (int pr = 0; pr < NP; ++pr) {
-    const int s = pr % kTStages;
-    if (ok) ok = p.wait_ns != 0 && mbar_wait_bounded(&full[s], (uint32_t)((pr / kTStages) & 1), p.wait_ns);
-    float* st = ring + s * 2 * kTPlane;
-    const int k = 1 + pr / H, i = pr % H;
-    const int q1 = 1 + (k - 1) * ND + i, q2 = q1 + H;
+  for (int sg = 0; sg < NS; ++sg) {
+    const int s = sg % kTStages;
+    if (ok) ok = p.wait_ns != 0 && mbar_wait_bounded(&full[s], (uint32_t)((sg / kTStages) & 1), p.wait_ns);
+    float* stg = ring + s * kTPPS * 2 * kTPlane;
     if (inner || outer) {
-      // 2 walls x 2 labels x 2 layers x 16 rows
-      if (ok && tid < 128) {
-        const int side = tid >> 6, L = (tid >> 5) & 1, layer = (tid >> 4) & 1, rr = tid & 15;
+      // per pair: 2 walls x 2 labels x 2 layers x 16 rows
+      for (int it = tid; it < kTPPS * 128 && ok; it += kTThreads) {
+        const int P = it >> 7, side = (it >> 6) & 1, L = (it >> 5) & 1, layer = (it >> 4) & 1, rr = it & 15;
+        const int pr = sg * kTPPS + P;
+        const int q1 = 1 + (pr / H) * ND + pr % H, q2 = q1 + H;
         const int tt = t0 + rr;
         if ((side == 0 ? inner : outer) && tt < p.n_theta) {
           const int cg = side == 0 ? kLeft - 1 - layer : cw_out + 1 + layer;
           if (cg >= 0 && cg < kWinR)
-            st[L * kTPlane + (rr + 2) * kWinR + cg] = ghost[((size_t)(side * 2 + layer) * p.n_theta + tt) * Q + (L ? q2 : q1)];
+            stg[P * 2 * kTPlane + L * kTPlane + (rr + 2) * kWinR + cg] =
+                ghost[((size_t)(side * 2 + layer) * p.n_theta + tt) * Q + (L ? q2 : q1)];
         }
       }
       __syncthreads();
     }
     if (ok) {
-      const float4 tb = tab[pr * kTileT32 + rl];
-      const int fl = __float_as_int(tb.w);
-      const f2 nar = bc2(-tb.x), nkr = bc2(-tb.y);
-      const f2 nat = mul2(bc2(-tb.z), invr);
-      const f2 nkt = fma2(nat, nat, nat);           // -(a - a^2) with a = -nat
-      // equilibrium of the pair (Eq. 10): P(+-x) = ev +- od, x = v.u/E
-      const f2 wk = k == 1 ? eq.w[1] : (k == 2 ? eq.w[2] : (k == 3 ? eq.w[3] : eq.w[4]));
-      f2 fe[2];
-      tiled_feq_pair(eq, wk, c.vx[q1], c.vy[q1], fe[0], fe[1]);
-      const float* w0 = st + row * kWinR + col;
-      const float* w1 = w0 + kTPlane;
-      // bit 0: q1's upwind side at larger r; bit 1: at larger theta (q2 the opposite)
-      switch (fl & 3) {
-        case 0:
-          tupd<SCH, -1, -1>(w0, nar, nkr, nat, nkt, fe[0], decay, q1, store);
-          tupd<SCH, 1, 1>(w1, nar, nkr, nat, nkt, fe[1], decay, q2, store);
-          break;
-        case 1:
-          tupd<SCH, 1, -1>(w0, nar, nkr, nat, nkt, fe[0], decay, q1, store);
-          tupd<SCH, -1, 1>(w1, nar, nkr, nat, nkt, fe[1], decay, q2, store);
-          break;
-        case 2:
-          tupd<SCH, -1, 1>(w0, nar, nkr, nat, nkt, fe[0], decay, q1, store);
-          tupd<SCH, 1, -1>(w1, nar, nkr, nat, nkt, fe[1], decay, q2, store);
-          break;
-        default:
-          tupd<SCH, 1, 1>(w0, nar, nkr, nat, nkt, fe[0], decay, q1, store);
-          tupd<SCH, -1, -1>(w1, nar, nkr, nat, nkt, fe[1], decay, q2, store);
-          break;
+#pragma unroll
+      for (int pp = 0; pp < kTPPS; ++pp) {
+        const int pr = sg * kTPPS + pp;
+        const int k = 1 + pr / H, i = pr % H;
+        const int q1 = 1 + (k - 1) * ND + i, q2 = q1 + H;
+        const float4 tb = tab[pr * kTileT32 + rl];
+        const int fl = __float_as_int(tb.w);
+        const f2 nar = bc2(-tb.x), nkr = bc2(-tb.y);
+        const f2 nat = mul2(bc2(-tb.z), invr);
+        const f2 nkt = fma2(nat, nat, nat);           // -(a - a^2) with a = -nat
+        // equilibrium of the pair (Eq. 10): P(+-x) = ev +- od, x = v.u/E
+        const f2 wk = k == 1 ? eq.w[1] : (k == 2 ? eq.w[2] : (k == 3 ? eq.w[3] : eq.w[4]));
+        f2 fe[2];
+        tiled_feq_pair(eq, wk, c.vx[q1], c.vy[q1], fe[0], fe[1]);
+        const float* w0 = stg + pp * 2 * kTPlane + row * kWinR + col;
+        const float* w1 = w0 + kTPlane;
+        // bit 0: q1's upwind side at larger r; bit 1: at larger theta (q2 the opposite)
+        switch (fl & 3) {
+          case 0:
+            tupd<SCH, -1, -1>(w0, nar, nkr, nat, nkt, fe[0], decay, q1, store);
+            tupd<SCH, 1, 1>(w1, nar, nkr, nat, nkt, fe[1], decay, q2, store);
+            break;
+          case 1:
+            tupd<SCH, 1, -1>(w0, nar, nkr, nat, nkt, fe[0], decay, q1, store);
+            tupd<SCH, -1, 1>(w1, nar, nkr, nat, nkt, fe[1], decay, q2, store);
+            break;
+          case 2:
+            tupd<SCH, -1, 1>(w0, nar, nkr, nat, nkt, fe[0], decay, q1, store);
+            tupd<SCH, 1, -1>(w1, nar, nkr, nat, nkt, fe[1], decay, q2, store);
+            break;
+          default:
+            tupd<SCH, 1, 1>(w0, nar, nkr, nat, nkt, fe[0], decay, q1, store);
+            tupd<SCH, -1, -1>(w1, nar, nkr, nat, nkt, fe[1], decay, q2, store);
+            break;
+        }
       }
     }
-    // the stage of this pair is read by every thread before it is refilled;
-    // a copy that did not land in time stops the tile
+    // the stage is read by every thread before it is refilled; a copy that
+    // did not land in time stops the tile
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(p.status, PCLB_FLAG_TIMEOUT);
-        for (int pp = pr; pp < pr + kTStages && pp < NP; ++pp)
-          mbar_wait_bounded(&full[pp % kTStages], (uint32_t)((pp / kTStages) & 1), kDefaultWaitNs);
+        for (int gg = sg; gg < sg + kTStages && gg < NS; ++gg)
+          mbar_wait_bounded(&full[gg % kTStages], (uint32_t)((gg / kTStages) & 1), kDefaultWaitNs);
       }
       return;
     }
-    if (tid == 0 && pr + kTStages < NP) {
+    if (tid == 0 && sg + kTStages < NS) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(pr + kTStages, s);
+      issue(sg + kTStages, s);
     }
   }
 }

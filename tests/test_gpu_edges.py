@@ -218,6 +218,27 @@ def test_adjoint_window_wait_that_runs_out_reports_timeout(prec):
     assert torch.equal(got, want)
 
 
+@pytest.mark.parametrize("n_dirs", [16, 24])
+def test_tiled_step_wait_that_runs_out_reports_timeout(n_dirs):
+    """The FP32 step of the 16- and 24-direction sets (plane pairs streamed
+    through a TMA ring) gives a tile up the same way when a wait runs out:
+    PCLB_FLAG_TIMEOUT, PCLB_ETIMEOUT, and with the default limit restored a
+    reloaded state steps bit for bit like a fresh context."""
+    w = I.random_smooth(200, 96, seed=31, n_dirs=n_dirs, n_f=n_dirs)
+    f0 = torch.as_tensor(O.set_state(w), dtype=torch.float32, device="cuda")
+    with P.PCLB(w, precision="fp32") as g:
+        g.set_f(f0).set_wait_limit(0).step(2)
+        flags = ctypes.c_uint32()
+        code = P.lib().pclb_status_flags(g.ctx, ctypes.byref(flags), 1)
+        assert code == 5 and flags.value & P.FLAG_TIMEOUT, (code, flags.value)
+        g.set_wait_limit().set_f(f0).step(3)
+        assert g.status_flags() == 0
+        got = g.get_f()
+    with P.PCLB(w, precision="fp32") as h:
+        want = h.set_f(f0).step(3).get_f()
+    assert torch.equal(got, want)
+
+
 def test_host_sync_that_runs_out_reports_timeout():
     """pclb_sync with a limit shorter than the queued work returns
     PCLB_ETIMEOUT and leaves the work running; a second sync with the default
