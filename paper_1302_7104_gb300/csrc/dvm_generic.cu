@@ -1,14 +1,11 @@
-// The step and its field kernels for the larger velocity sets of Table I,
-// N_i = 16 and 24 directions per shell (Q = 65, 97): the same model (Eqs. 2-5,
-// 10-11, 19 or 18, 28 or the other convection schemes, 38-40), one thread per
-// node, stencil values read from global memory (L1/L2).  The field kernels and
-// the FP64 step form the moments, the temperature and the equilibrium factors
-// in double.  The FP32 step does no FP64 arithmetic (GB300 runs it at 1/64 of
-// the FP32 rate): float shell sums with float-float unit vectors, combined,
-// and the temperature and weights evaluated, in float-float, as the tuned FP32
-// kernel does.  The per-velocity work (equilibrium polynomial, relaxation,
-// convection) runs in the storage type.  These sets serve the paper's
-// velocity-set comparison; the tuned TMA kernels cover N_i = 8.
+// The FP64 step and the field kernels (both precisions) for the larger
+// velocity sets of Table I, N_i = 16 and 24 directions per shell (Q = 65,
+// 97): the same model (Eqs. 2-5, 10-11, 19 or 18, 28 or the other convection
+// schemes, 38-40), one thread per node, stencil values read from global
+// memory (L1/L2), the moments, the temperature and the equilibrium factors in
+// double.  These sets serve the paper's velocity-set comparison; their FP32
+// step is the tiled kernel of dvm_tiled32.cu, the tuned TMA kernels cover
+// N_i = 8.
 //
 // Radial ghost nodes (Sec. II C 1) are formed once per wall row by
 // gen_ghost_kernel into a small buffer [side][layer][n_theta][Q] (f = f^eq of
@@ -105,73 +102,6 @@ __device__ __forceinline__ GenEqC<C> gen_eq_c(const GenEq& e) {
   return c;
 }
 
-// FP32 storage: the node's moments (Eqs. 3-5), temperature and equilibrium
-// factors (Eqs. 10-11) in float-float, rounded to float once.  Per shell,
-// float sums over opposite-direction pairs (f_a + f_b, and f_a - f_b times the
-// float-float unit vector); shells 2 and 3 (nearly equal speeds, equilibrium
-// weights of opposite sign) are added direction by direction first so that
-// their large contributions cancel before rounding, and shell 3 enters once
-// more with the speed differences; the shell totals are combined with
-// error-free transformations.  Returns whether the state is physical.
-__device__ bool gen_node_f32(const float* f, size_t plane, const DvmG& d, const DvmG32& c, GenEqC<float>& out) {
-  const int nd = d.n_dirs, h = nd / 2;
-  ff rho = ff_of(f[0]), jx = ff_of(0.f), jy = ff_of(0.f), e = ff_of(0.f);
-#pragma unroll
-  for (int g = 0; g < 4; ++g) {
-    const int k = g == 0 ? 1 : (g == 1 ? 2 : (g == 2 ? 3 : 4));   // g = 1: shells 2 + 3; g = 2: shell 3
-    float S = 0.f, X = 0.f, Xl = 0.f, Y = 0.f, Yl = 0.f;
-    for (int i = 0; i < h; ++i) {
-      const int q = 1 + (k - 1) * nd + i;
-      float fa = f[(size_t)q * plane], fb = f[(size_t)(q + h) * plane];
-      if (g == 1) {
-        fa += f[(size_t)(q + nd) * plane];
-        fb += f[(size_t)(q + nd + h) * plane];
-      }
-      S += fa + fb;
-      const float dd = fa - fb;   // the pair has opposite unit vectors
-      X = fmaf(c.cxh[i], dd, X);
-      Xl = fmaf(c.cxl[i], dd, Xl);
-      Y = fmaf(c.cyh[i], dd, Y);
-      Yl = fmaf(c.cyl[i], dd, Yl);
-    }
-    const ff sp = g == 2 ? ff{c.dv23h, c.dv23l} : ff{c.sph[k], c.spl[k]};
-    const ff hv = g == 2 ? ff{c.dh23h, c.dh23l} : ff{c.hvh[k], c.hvl[k]};
-    if (g != 2) rho = ff_add(rho, ff_of(S));
-    jx = ff_add(jx, ff_mul(sp, ff{X, Xl}));
-    jy = ff_add(jy, ff_mul(sp, ff{Y, Yl}));
-    e = ff_add(e, ff_mul(hv, ff_of(S)));
-  }
-  const ff inv = ff_recip(rho);
-  const ff ux = ff_mul(jx, inv), uy = ff_mul(jy, inv);
-  const ff ke = ff_add(ff_mul(jx, ux), ff_mul(jy, uy));   // |j|^2 / rho
-  const ff E = ff_mul(ff_add(e, ff_scale(ke, -0.5f)), inv);
-  const bool ok = rho.hi > 0.f && E.hi > 0.f && isfinite(e.hi) && isfinite(jx.hi) && isfinite(jy.hi);
-  ff sum = ff_of(0.f);
-#pragma unroll
-  for (int k = 1; k <= 4; ++k) {
-    ff a{c.Fch[k][3], c.Fcl[k][3]};
-#pragma unroll
-    for (int n = 2; n >= 0; --n) a = ff_mul_add(a, E, ff{c.Fch[k][n], c.Fcl[k][n]});
-    a = ff_mul(a, E);   // F_k(E)
-    sum = ff_add(sum, a);
-    const ff w = ff_mul(rho, a);
-    out.w[k] = w.hi + w.lo;
-  }
-  const ff w0 = ff_mul(rho, ff_add(ff_of(1.f), ff_mul(ff{-c.B0h, -c.B0l}, sum)));
-  out.w[0] = w0.hi + w0.lo;
-  const ff invE = ff_recip(E);
-  const ff uxE = ff_mul(ux, invE), uyE = ff_mul(uy, invE);
-  const ff u2E = ff_add(ff_mul(ux, uxE), ff_mul(uy, uyE));   // u^2 / E
-  const ff a1 = ff_add(ff_of(1.f), ff_scale(u2E, -0.5f));
-  const ff a0 = ff_add(a1, ff_scale(ff_mul(u2E, u2E), 0.125f));
-  out.a1 = a1.hi + a1.lo;
-  out.a0 = a0.hi + a0.lo;
-  out.a1h = 0.5f * out.a1;
-  out.uxE = uxE.hi + uxE.lo;
-  out.uyE = uyE.hi + uyE.lo;
-  return ok;
-}
-
 // f^eq of velocity (vx, vy) of shell k, Eq. (10), as even and odd parts in x
 // = v.u/E: P(x) = ev + od, P(-x) = ev - od (the opposite velocity).
 template <class C>
@@ -183,37 +113,21 @@ __device__ __forceinline__ void gen_feq_pair(const GenEqC<C>& e, C vx, C vy, int
   fm = e.w[k] * (ev - od);
 }
 
-template <class C>
-__device__ __forceinline__ C smallest_normal_c();
-template <>
-__device__ __forceinline__ float smallest_normal_c<float>() { return FLT_MIN; }
-template <>
-__device__ __forceinline__ double smallest_normal_c<double>() { return DBL_MIN; }
-
 // Convection increment in upwind form from a = |C|, K = a (1 - a), the node
 // value f0, its upwind neighbours u1, u2 and (Lax-Wendroff) the downwind one d1.
-// The limiter ratio |D| / (|D| + |Dp|) takes the hardware reciprocal in FP32
-// (as the tuned kernel does) and the correctly rounded quotient in FP64.
-template <int SCH, class C>
-__device__ __forceinline__ C gen_convect(C a, C K, C f0, C u1, C u2, C d1) {
-  const C D = f0 - u1, Dp = u1 - u2;
+// The limiter ratio |D| / (|D| + |Dp|) with the correctly rounded quotient
+// (0 when the sum is below the smallest normal number).
+template <int SCH>
+__device__ __forceinline__ double gen_convect(double a, double K, double f0, double u1, double u2, double d1) {
+  const double D = f0 - u1, Dp = u1 - u2;
   if (SCH == PCLB_SCHEME_MWB) {
-    const C den = fabs(D) + fabs(Dp);
-    C h = C(0);
-    if (den >= smallest_normal_c<C>()) {
-      if constexpr (sizeof(C) == 4) {
-        float rden;
-        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rden) : "f"(den));
-        h = fabsf(D) * rden * (D - Dp);
-      } else {
-        h = fabs(D) * (D - Dp) / den;
-      }
-    }
+    const double den = fabs(D) + fabs(Dp);
+    const double h = den >= DBL_MIN ? fabs(D) * (D - Dp) / den : 0.0;
     return a * D + K * h;
   }
-  if (SCH == PCLB_SCHEME_WB) return a * D + C(0.5) * K * (D - Dp);
-  if (SCH == PCLB_SCHEME_UPWIND2) return a * D + C(0.5) * a * (D - Dp);
-  return a * D + C(0.5) * K * ((d1 - f0) - D);
+  if (SCH == PCLB_SCHEME_WB) return a * D + 0.5 * K * (D - Dp);
+  if (SCH == PCLB_SCHEME_UPWIND2) return a * D + 0.5 * a * (D - Dp);
+  return a * D + 0.5 * K * ((d1 - f0) - D);
 }
 
 // Store of label q at interior node (t, r), and of the azimuthal ghost rows
@@ -331,34 +245,25 @@ __global__ void __launch_bounds__(kGenThreads)
   if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
 }
 
-// One step (Eq. 38) at node (t, r): moments and equilibrium factors (in
-// double for FP64 storage, in float-float for FP32), then per pair of
-// opposite velocities (sharing the Courant entry and the even and odd parts
-// of the equilibrium polynomial) the relaxation (decay d = exp(-dt/tau) or
-// 1 - dt/tau) minus the convection increments in r and theta, in the storage
-// type T (for FP32 with the float Courant table and velocities).
-template <class T, int SCH>
+// One FP64 step (Eq. 38) at node (t, r): moments and equilibrium factors in
+// double, then per pair of opposite velocities (sharing the Courant entry
+// and the even and odd parts of the equilibrium polynomial) the relaxation
+// (decay d = exp(-dt/tau) or 1 - dt/tau) minus the convection increments in r
+// and theta.
+template <int SCH>
 __global__ void __launch_bounds__(kGenThreads)
-    gen_step_kernel(const T* __restrict__ f, T* __restrict__ f_out, const T* __restrict__ ghost,
-                    const __grid_constant__ StepParams p, const __grid_constant__ DvmG d,
-                    const __grid_constant__ DvmG32 d32) {
-  constexpr bool kF32 = sizeof(T) == 4;
+    gen_step_kernel(const double* __restrict__ f, double* __restrict__ f_out, const double* __restrict__ ghost,
+                    const __grid_constant__ StepParams p, const __grid_constant__ DvmG d) {
+  using T = double;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
   if (r >= p.n_r) return;
   const size_t plane = (size_t)p.rows * p.pitch;
   const int srow = t + kGhostRows;
   const T* fn = f + (size_t)srow * p.pitch + r;
-  GenEqC<T> e;
-  bool ok;
-  if constexpr (kF32) {
-    ok = gen_node_f32(fn, plane, d, d32, e);
-  } else {
-    const GenState m = gen_moments_node(fn, plane, d);
-    ok = m.ok;
-    e = gen_eq_c<T>(gen_eq(m.rho, m.ux, m.uy, m.E, d));
-  }
-  if (!ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
+  const GenState m = gen_moments_node(fn, plane, d);
+  const GenEqC<T> e = gen_eq_c<T>(gen_eq(m.rho, m.ux, m.uy, m.E, d));
+  if (!m.ok) atomicOr(p.status, PCLB_FLAG_NONPHYS);
   const T decay = (T)p.decay;
   // value of label q (plane fq) at radial index rr of row t (a ghost layer
   // outside the grid)
@@ -390,36 +295,21 @@ __global__ void __launch_bounds__(kGenThreads)
   for (int k = 1; k <= 4; ++k)
     for (int i = 0; i < half; ++i) {
       const int q1 = 1 + (k - 1) * d.n_dirs + i, q2 = q1 + half;
-      T ar, kr, at;
-      int fl;
-      if constexpr (kF32) {
-        const float4 ce = p.courant[(size_t)srow * npairs + (k - 1) * half + i];
-        ar = ce.x;
-        kr = ce.y;
-        at = ce.z * inv_r;
-        fl = __float_as_int(ce.w);
-      } else {
-        const double* ce = p.courant64 + ((size_t)srow * npairs + (k - 1) * half + i) * 4;
-        ar = ce[0];
-        kr = ce[1];
-        at = ce[2] * inv_r;
-        fl = (int)ce[3];
-      }
+      const double* ce = p.courant64 + ((size_t)srow * npairs + (k - 1) * half + i) * 4;
+      const T ar = ce[0], kr = ce[1], at = ce[2] * inv_r;
+      const int fl = (int)ce[3];
       const T kt = at - at * at;
       const int sr = (fl & 1) ? 1 : -1;   // v_r < 0 for q1: upwind at larger r
       const int st = (fl & 2) ? 1 : -1;   // v_theta < 0 for q1: upwind at larger theta
       T fe[2];
-      if constexpr (kF32)
-        gen_feq_pair<T>(e, d32.vx[q1], d32.vy[q1], k, fe[0], fe[1]);
-      else
-        gen_feq_pair<T>(e, d.vx[q1], d.vy[q1], k, fe[0], fe[1]);
+      gen_feq_pair<T>(e, d.vx[q1], d.vy[q1], k, fe[0], fe[1]);
       for (int L = 0; L < 2; ++L) {
         const int q = L ? q2 : q1, s_r = L ? -sr : sr, s_t = L ? -st : st;
         const T* fq = fn + (size_t)q * plane;
         const T a = fq[0];
-        const T cr = gen_convect<SCH, T>(ar, kr, a, fr(fq, q, r + s_r), fr(fq, q, r + 2 * s_r),
-                                         lw ? fr(fq, q, r - s_r) : T(0));
-        const T ct = gen_convect<SCH, T>(at, kt, a, ft(fq, s_t), ft(fq, 2 * s_t), lw ? ft(fq, -s_t) : T(0));
+        const T cr = gen_convect<SCH>(ar, kr, a, fr(fq, q, r + s_r), fr(fq, q, r + 2 * s_r),
+                                      lw ? fr(fq, q, r - s_r) : T(0));
+        const T ct = gen_convect<SCH>(at, kt, a, ft(fq, s_t), ft(fq, 2 * s_t), lw ? ft(fq, -s_t) : T(0));
         put(q, fe[L] + (a - fe[L]) * decay - cr - ct);
       }
     }
@@ -474,13 +364,13 @@ __global__ void gen_diag_final_kernel(const double* partials, int n_blocks, doub
   out[7] = 0.0;
 }
 
-template <class T, int SCH>
-cudaError_t gen_step_scheme(const T* f, T* f_out, T* ghost, const StepParams& p, const DvmG& d, const DvmG32& d32,
+template <int SCH>
+cudaError_t gen_step_scheme(const double* f, double* f_out, double* ghost, const StepParams& p, const DvmG& d,
                             cudaStream_t s) {
   // one thread per wall row, in warps, so that the rows spread over the SMs
-  gen_ghost_kernel<T><<<dim3((p.n_theta + 31) / 32, 2), 32, 0, s>>>(f, ghost, p, d);
-  gen_step_kernel<T, SCH><<<dim3((p.n_r + kGenThreads - 1) / kGenThreads, p.n_theta), kGenThreads, 0, s>>>(
-      f, f_out, ghost, p, d, d32);
+  gen_ghost_kernel<double><<<dim3((p.n_theta + 31) / 32, 2), 32, 0, s>>>(f, ghost, p, d);
+  gen_step_kernel<SCH><<<dim3((p.n_r + kGenThreads - 1) / kGenThreads, p.n_theta), kGenThreads, 0, s>>>(
+      f, f_out, ghost, p, d);
   return cudaGetLastError();
 }
 
@@ -515,14 +405,13 @@ cudaError_t gen_launch_unpack(const T* in, T* f, const StepParams& p, const DvmG
   return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t gen_launch_step(const T* f, T* f_out, T* ghost, const StepParams& p, const DvmG& d, const DvmG32& d32,
-                            cudaStream_t s) {
+cudaError_t gen_launch_step_f64(const double* f, double* f_out, double* ghost, const StepParams& p, const DvmG& d,
+                                cudaStream_t s) {
   switch (p.scheme) {
-    case PCLB_SCHEME_WB: return gen_step_scheme<T, PCLB_SCHEME_WB>(f, f_out, ghost, p, d, d32, s);
-    case PCLB_SCHEME_LW: return gen_step_scheme<T, PCLB_SCHEME_LW>(f, f_out, ghost, p, d, d32, s);
-    case PCLB_SCHEME_UPWIND2: return gen_step_scheme<T, PCLB_SCHEME_UPWIND2>(f, f_out, ghost, p, d, d32, s);
-    default: return gen_step_scheme<T, PCLB_SCHEME_MWB>(f, f_out, ghost, p, d, d32, s);
+    case PCLB_SCHEME_WB: return gen_step_scheme<PCLB_SCHEME_WB>(f, f_out, ghost, p, d, s);
+    case PCLB_SCHEME_LW: return gen_step_scheme<PCLB_SCHEME_LW>(f, f_out, ghost, p, d, s);
+    case PCLB_SCHEME_UPWIND2: return gen_step_scheme<PCLB_SCHEME_UPWIND2>(f, f_out, ghost, p, d, s);
+    default: return gen_step_scheme<PCLB_SCHEME_MWB>(f, f_out, ghost, p, d, s);
   }
 }
 
@@ -577,8 +466,6 @@ cudaError_t gen_launch_diagnostics(const T* f, double* partials, double* out, co
                                              cudaStream_t);                                                   \
   template cudaError_t gen_launch_pack<T>(const T*, T*, const StepParams&, const DvmG&, cudaStream_t);        \
   template cudaError_t gen_launch_unpack<T>(const T*, T*, const StepParams&, const DvmG&, cudaStream_t);      \
-  template cudaError_t gen_launch_step<T>(const T*, T*, T*, const StepParams&, const DvmG&, const DvmG32&,    \
-                                          cudaStream_t);                                                      \
   template cudaError_t gen_launch_diagnostics<T>(const T*, double*, double*, const StepParams&, const DvmG&,  \
                                                  double, double, double, cudaStream_t);
 PCLB_GEN_INSTANTIATE(float)

@@ -1,5 +1,6 @@
-// Float tables of the N_i = 16 and 24 velocity sets (Table I) for the FP32
-// generic step, beside the double constants of DvmG.
+// Float tables of the N_i = 16 and 24 velocity sets (Table I) for their FP32
+// step (dvm_tiled32.cu), beside the double constants of DvmG; and the entry
+// points of the steps of these sets.
 #pragma once
 
 #include "pclb.h"
@@ -21,6 +22,11 @@ struct DvmG32 {
 };
 
 void fill_dvm_generic32(DvmG32& c, const pclb_dvm& d, const DvmG& g);
+
+// One FP64 step of the N_i = 16 or 24 set (dvm_generic.cu): the radial ghost
+// layers into ghost [side][layer][n_theta][Q], then one thread per node.
+cudaError_t gen_launch_step_f64(const double* f, double* f_out, double* ghost, const StepParams& p, const DvmG& d,
+                                cudaStream_t s);
 
 // One FP32 step of the N_i = 16 or 24 set: its radial ghost layers into
 // ghost [side][layer][n_theta][Q], then the tiled kernel; tmap describes f

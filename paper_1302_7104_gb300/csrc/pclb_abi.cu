@@ -57,8 +57,6 @@ cudaError_t gen_launch_pack(const T*, T*, const StepParams&, const DvmG&, cudaSt
 template <class T>
 cudaError_t gen_launch_unpack(const T*, T*, const StepParams&, const DvmG&, cudaStream_t);
 template <class T>
-cudaError_t gen_launch_step(const T*, T*, T*, const StepParams&, const DvmG&, const DvmG32&, cudaStream_t);
-template <class T>
 cudaError_t gen_launch_diagnostics(const T*, double*, double*, const StepParams&, const DvmG&, double, double,
                                    double, cudaStream_t);
 template <class T>
@@ -395,15 +393,16 @@ pclb_status do_step(pclb_ctx* ctx, int n) {
   for (int i = 0; i < n; ++i) {
     const int src = ctx->cur, dst = 1 - ctx->cur;
     cudaError_t e;
-    if (generic(ctx) && sizeof(T) == 4)
-      e = gen_tiled_step_f32(&ctx->tmap[src], reinterpret_cast<const float*>(fbuf<T>(ctx, src)),
-                             reinterpret_cast<float*>(fbuf<T>(ctx, dst)),
-                             reinterpret_cast<float*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg,
-                             dvmg32(ctx), ctx->stream);
-    else if (generic(ctx))
-      e = gen_launch_step<T>(fbuf<T>(ctx, src), fbuf<T>(ctx, dst), reinterpret_cast<T*>(ctx->ws + ctx->lay.gen_ghost),
-                             ctx->sp, ctx->dvmg, dvmg32(ctx), ctx->stream);
-    else if constexpr (sizeof(T) == 4)
+    if (generic(ctx)) {
+      if constexpr (sizeof(T) == 4)
+        e = gen_tiled_step_f32(&ctx->tmap[src], fbuf<float>(ctx, src), fbuf<float>(ctx, dst),
+                               reinterpret_cast<float*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg,
+                               dvmg32(ctx), ctx->stream);
+      else
+        e = gen_launch_step_f64(fbuf<double>(ctx, src), fbuf<double>(ctx, dst),
+                                reinterpret_cast<double*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg,
+                                ctx->stream);
+    } else if constexpr (sizeof(T) == 4)
       e = launch_step_f32(&ctx->tmap[src], fbuf<float>(ctx, dst), ctx->sp, ctx->dvm32, ctx->stream);
     else
       e = launch_step<T>(&ctx->tmap[src], fbuf<T>(ctx, dst), ctx->sp, dvm_of<T>(ctx), ctx->stream);
@@ -947,9 +946,9 @@ pclb_status pclb_step_states(pclb_ctx* ctx, const void* f_from, void* f_to) {
                            reinterpret_cast<float*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg, dvmg32(ctx),
                            ctx->stream);
   } else if (generic(ctx)) {
-    e = gen_launch_step<double>((const double*)f_from, (double*)f_to,
-                                reinterpret_cast<double*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg,
-                                dvmg32(ctx), ctx->stream);
+    e = gen_launch_step_f64((const double*)f_from, (double*)f_to,
+                            reinterpret_cast<double*>(ctx->ws + ctx->lay.gen_ghost), ctx->sp, ctx->dvmg,
+                            ctx->stream);
   } else {
     CUtensorMap map;
     pclb_status st = encode_map(ctx, f_from, ctx->prec == PCLB_FP32 ? kTileT32 + 4 : kWinT, &map);
