@@ -126,8 +126,8 @@ typedef struct {
  * step kernel that streams the opposite-velocity plane pairs, in FP64 and for
  * the field operations generic kernels): pclb_set_state, pclb_set_f,
  * pclb_get_f, pclb_step (every scheme and relaxation), pclb_moments,
- * pclb_diagnostics, pclb_run_host and the state save / load calls; the
- * reverse-mode entry points, pclb_noneq and pclb_diagnostics_noalloc return
+ * pclb_diagnostics, pclb_noneq, pclb_run_host and the state save / load
+ * calls; the reverse-mode entry points and pclb_diagnostics_noalloc return
  * PCLB_EUNSUPPORTED for them. */
 typedef struct {
   int32_t n_dirs;    /* N_i: 8, 16 or 24 */

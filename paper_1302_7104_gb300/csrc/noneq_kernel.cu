@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
+#include "dvm_generic.h"
 #include "f32_state.cuh"
 #include "pclb_internal.h"
 
@@ -156,6 +157,107 @@ __global__ void __launch_bounds__(kNeqThreads)
     ++slot;
   }
 }
+
+// The same for the N_i = 16 and 24 sets of Table I (Q = 65, 97, built to
+// reproduce the same equilibrium moments, Eqs. 6-9): the node's moments in
+// double (one pass over its Q values), the central moments in the storage
+// type with the velocities of the set (float tables for FP32).
+template <class T>
+__global__ void __launch_bounds__(kNeqThreads)
+    noneq_gen_kernel(const T* __restrict__ f, T* __restrict__ out, int groups, const __grid_constant__ StepParams p,
+                     const __grid_constant__ DvmG d, const __grid_constant__ DvmG32 c) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  if (r >= p.n_r || t >= p.n_theta) return;
+  const size_t plane = (size_t)p.rows * p.pitch;
+  const T* fn = f + (size_t)(t + kGhostRows) * p.pitch + r;
+  // rho, rho u, rho (E + u^2/2) (Eqs. 3-5), then u and E
+  double s0 = 0.0, sx = 0.0, sy = 0.0, se = 0.0;
+  for (int q = 0; q < d.q; ++q) {
+    const double v = (double)fn[(size_t)q * plane];
+    s0 += v;
+    sx = fma(d.vx[q], v, sx);
+    sy = fma(d.vy[q], v, sy);
+    se = fma(d.half_v2[d.shell[q]], v, se);
+  }
+  const double uxd = sx / s0, uyd = sy / s0;
+  const double E = (se - 0.5 * (sx * uxd + sy * uyd)) / s0;
+  if (!(s0 > 0.0 && E > 0.0 && isfinite(E) && isfinite(uxd) && isfinite(uyd))) atomicOr(p.status, PCLB_FLAG_NONPHYS);
+  const double rE = s0 * E, rE2 = 2.0 * s0 * E * E;
+  const T rho = (T)s0, ux = (T)uxd, uy = (T)uyd;
+  const T cs = (T)p.cos_t[t], sn = (T)p.sin_t[t];
+  const T u_r = ux * cs + uy * sn, u_t = uy * cs - ux * sn;
+
+  // central moments of f
+  T A[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) A[k] = T(0);
+  for (int q = 0; q < d.q; ++q) {
+    const T w = fn[(size_t)q * plane];
+    T vx, vy;
+    if constexpr (sizeof(T) == 4) {
+      vx = c.vx[q];
+      vy = c.vy[q];
+    } else {
+      vx = d.vx[q];
+      vy = d.vy[q];
+    }
+    const T cr = vx * cs + vy * sn - u_r, ct = vy * cs - vx * sn - u_t;
+    const T h = T(0.5) * (cr * cr + ct * ct);
+    const T wr = w * cr, wt = w * ct;
+    const T wrr = wr * cr, wrt = wr * ct, wtt = wt * ct;
+    A[0] += wrr;
+    A[1] += wrt;
+    A[2] += wtt;
+    A[3] += wrr * cr;
+    A[4] += wrr * ct;
+    A[5] += wrt * ct;
+    A[6] += wtt * ct;
+    A[7] += h * wr;
+    A[8] += h * wt;
+    A[9] += h * wrr;
+    A[10] += h * wrt;
+    A[11] += h * wtt;
+  }
+  // central departures: minus the equilibrium's (rho E I, 0, 0, 2 rho E^2 I)
+  T D[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) D[k] = A[k];
+  D[0] = (T)((double)A[0] - rE);
+  D[2] = (T)((double)A[2] - rE);
+  D[9] = (T)((double)A[9] - rE2);
+  D[11] = (T)((double)A[11] - rE2);
+
+  const size_t nodes = (size_t)p.n_theta * p.n_r, n = (size_t)t * p.n_r + r;
+  int slot = 0;
+  T out_g[12];
+#pragma unroll 1
+  for (int g = 0; g < 4; ++g) {
+    if (!(groups & (1 << g))) continue;
+    if (g == 0) plain_from_central<T>(rho, u_r, u_t, A, out_g);
+    else if (g == 1) plain_from_central<T>(T(0), u_r, u_t, D, out_g);
+    else if (g == 2)
+      for (int k = 0; k < 12; ++k) out_g[k] = A[k];
+    else
+      for (int k = 0; k < 12; ++k) out_g[k] = D[k];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[(size_t)(slot * 12 + k) * nodes + n] = out_g[k];
+    ++slot;
+  }
+}
+
+template <class T>
+cudaError_t launch_noneq_gen(const T* f, T* out, int groups, const StepParams& p, const DvmG& d, const DvmG32& c,
+                             cudaStream_t s) {
+  dim3 grid((p.n_r + kNeqThreads - 1) / kNeqThreads, p.n_theta);
+  noneq_gen_kernel<T><<<grid, kNeqThreads, 0, s>>>(f, out, groups, p, d, c);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_noneq_gen<float>(const float*, float*, int, const StepParams&, const DvmG&, const DvmG32&,
+                                             cudaStream_t);
+template cudaError_t launch_noneq_gen<double>(const double*, double*, int, const StepParams&, const DvmG&,
+                                              const DvmG32&, cudaStream_t);
 
 template <class T>
 cudaError_t launch_noneq(const T* f, T* out, int groups, const StepParams& p, const DvmConst<T>& d,

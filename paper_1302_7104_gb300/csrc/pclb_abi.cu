@@ -43,6 +43,8 @@ cudaError_t launch_diagnostics(const T*, double*, double*, const StepParams&, co
 template <class T>
 cudaError_t launch_noneq(const T*, T*, int, const StepParams&, const DvmConst<T>&, cudaStream_t);
 template <class T>
+cudaError_t launch_noneq_gen(const T*, T*, int, const StepParams&, const DvmG&, const DvmG32&, cudaStream_t);
+template <class T>
 cudaError_t launch_adjoint(const CUtensorMap*, const CUtensorMap*, const CUtensorMap*, const CUtensorMap*, const T*,
                            const T*, T*, const AdjScratch&,
                            const StepParams&, const DvmConst<T>&, cudaStream_t, cudaStream_t, cudaEvent_t,
@@ -78,7 +80,7 @@ struct HostCtx : pclb_ctx {
   std::vector<double> cos_t, sin_t, inv_r, bc_vals;
   std::vector<float> courant, inv_r_f, cs_ff;
   std::vector<double> courant64;
-  DvmG32 dvmg32;   // N_i = 16, 24: float tables of the FP32 generic step
+  DvmG32 dvmg32;   // N_i = 16, 24: float tables of the FP32 step and field kernels
 };
 
 const DvmG32& dvmg32(const pclb_ctx* c) { return static_cast<const HostCtx*>(c)->dvmg32; }
@@ -1028,12 +1030,17 @@ pclb_status pclb_moments(pclb_ctx* ctx, void* rho, void* u_r, void* u_theta, voi
 pclb_status pclb_noneq(pclb_ctx* ctx, int32_t groups, void* out) {
   if (!ctx) return fail(nullptr, PCLB_EINVAL, "ctx must not be NULL");
   if (misaligned(ctx, {out})) return misaligned_fail(ctx);
-  if (generic(ctx)) return fail(ctx, PCLB_EUNSUPPORTED, "pclb_noneq implements n_dirs = 8 only");
   if (groups < 1 || groups > 15) return fail(ctx, PCLB_EINVAL, "groups = %d must be in 1..15", (int)groups);
   if (!out) return fail(ctx, PCLB_EINVAL, "out must not be NULL");
   if (!ctx->has_state) return fail(ctx, PCLB_ESTATE, "no state: call pclb_set_state or pclb_set_f first");
   cudaError_t e;
-  if (ctx->prec == PCLB_FP32)
+  if (generic(ctx))
+    e = ctx->prec == PCLB_FP32
+            ? launch_noneq_gen<float>(fbuf<float>(ctx, ctx->cur), (float*)out, groups, ctx->sp, ctx->dvmg,
+                                      dvmg32(ctx), ctx->stream)
+            : launch_noneq_gen<double>(fbuf<double>(ctx, ctx->cur), (double*)out, groups, ctx->sp, ctx->dvmg,
+                                       dvmg32(ctx), ctx->stream);
+  else if (ctx->prec == PCLB_FP32)
     e = launch_noneq<float>(fbuf<float>(ctx, ctx->cur), (float*)out, groups, ctx->sp, ctx->dvm32, ctx->stream);
   else
     e = launch_noneq<double>(fbuf<double>(ctx, ctx->cur), (double*)out, groups, ctx->sp, ctx->dvm64,

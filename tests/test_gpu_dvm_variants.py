@@ -122,7 +122,7 @@ def test_uniform_state_stays_uniform_and_conserves(n_dirs):
     assert np.allclose(d1[:4], d0[:4], rtol=1e-13, atol=1e-15)
 
 
-def test_reverse_mode_and_noneq_refuse_larger_sets():
+def test_reverse_mode_refuses_larger_sets():
     w = CASES["n16_circle"]()
     with P.PCLB(w, precision="fp64") as g:
         g.set_state()
@@ -130,9 +130,6 @@ def test_reverse_mode_and_noneq_refuse_larger_sets():
         with pytest.raises(P.PCLBError) as e:
             g.moments_vjp(torch.ones_like(rho))
         assert e.value.code == 8                      # PCLB_EUNSUPPORTED
-        with pytest.raises(P.PCLBError) as e:
-            g.noneq()
-        assert e.value.code == 8
 
 
 @pytest.mark.parametrize("n_dirs", [16, 24])

@@ -7,7 +7,8 @@ absolute moment sum_q |f_q| |c_q|^k of the same order k (k = 2 for M_2, 3 for
 M_3 and M_{3,1}, 4 for M_{4,2}; c = v, or v - u for the central groups): a
 sum of 33 rounded products is accurate to a few units of rounding of that
 size, however much the terms cancel (near equilibrium the central third
-moments and all departures are small differences of large terms).  FP64:
+moments and all departures are small differences of large terms); the same
+for the 65 and 97 products of the larger velocity sets.  FP64:
 1e-14 of it.  FP32 (inputs rounded to float, the oracle run on the rounded
 values, the equilibrium evaluated in float as the step does): 5e-7.  At
 equilibrium the departures vanish to the same rounding on the GPU."""
@@ -29,6 +30,9 @@ CASES = {
     "sector_nf1": lambda: I.random_smooth(35, 17, seed=3, n_f=1),
     "rm": lambda: I.rm(n_r=96, n_theta=64),
     "kh": lambda: I.kh(n_r=64, n_theta=96),
+    # the 16- and 24-direction sets of Table I (Q = 65, 97)
+    "n16_ragged": lambda: I.random_smooth(37, 19, seed=5, n_dirs=16, n_f=16),
+    "n24_sector": lambda: I.random_smooth(33, 12, seed=6, n_dirs=24, n_f=5),
 }
 
 
