@@ -102,7 +102,9 @@ typedef enum {
  * macroscopic state, the departure f - f^eq of the wall node (the
  * non-equilibrium microscopic boundary of Sec. II C 1, in the form of the
  * extrapolation scheme it cites: the non-equilibrium part of the nearest
- * fluid node).  The adjoint entry points refuse it (PCLB_EUNSUPPORTED). */
+ * fluid node).  The adjoint entry points differentiate it too (the ghosts'
+ * cotangent reaches the wall node's f directly and through its own
+ * equilibrium). */
 #define PCLB_BC_NEQ 8
 
 /* Device status bits accumulated by the kernels (pclb_status_flags). */

@@ -161,7 +161,8 @@ __device__ __forceinline__ void to_moment_cotangent(T rho, T ux, T uy, T E, cons
 cudaError_t launch_adjoint_pairs_f32(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, const CUtensorMap* tmap_fn,
                                      const CUtensorMap* tmap_ln, const float* f,
                                      const float* lam_in, float* lam_out, const EqParams<float>* ghost,
-                                     const float* gwall, int a0, int na, int b0, int nx, const StepParams& p,
+                                     const float* gwall, const float* gdir, int a0, int na, int b0, int nx,
+                                     const StepParams& p,
                                      const DvmConst<float>& d, cudaStream_t s);
 
 }  // namespace pclb

@@ -390,7 +390,8 @@ __global__ void __launch_bounds__(kAThr, 3)
     adjoint_pair_f32x2(const __grid_constant__ CUtensorMap tmap_f, const __grid_constant__ CUtensorMap tmap_l,
                        const __grid_constant__ CUtensorMap tmap_fn, const __grid_constant__ CUtensorMap tmap_ln,
                        const float* __restrict__ f, const float* __restrict__ lam_in, float* __restrict__ lam_out,
-                       const EqParams<float>* __restrict__ ghost, const float* __restrict__ gwall, int a0, int na,
+                       const EqParams<float>* __restrict__ ghost, const float* __restrict__ gwall,
+                       const float* __restrict__ gdir, int a0, int na,
                        int b0, const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<float> d) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* ring = reinterpret_cast<float*>(smem_raw);
@@ -557,7 +558,8 @@ __global__ void __launch_bounds__(kAThr, 3)
   const bool wall_tile = inner || outer;
   const int gside = tid >> 5, grow = tid & 31;
   const bool fills = wall_tile && tid < 64 && grow < kTT && t0 + grow < p.n_theta && (gside == 0 ? inner : outer);
-  const EqParams<float>* eg = ghost + (size_t)(gside * 2) * p.n_theta + t0 + grow;   // layer l at + l n_theta
+  const EqParams<float>* eg = ghost + (size_t)(gside * 3) * p.n_theta + t0 + grow;   // layer l at + l n_theta
+  const bool gneq = (p.bc_kind[gside & 1] & PCLB_BC_NEQ) != 0;   // its ghosts carry the wall node's departure
 
   bool ok = true;
   int brk = kANP;                                // the pair at which a wait timed out
@@ -571,16 +573,23 @@ __global__ void __launch_bounds__(kAThr, 3)
     float* pb = prod + (pair & 1) * 2 * kProd;     // this pair's products: [label][...]
     if (ok) ok = p.wait_ns != 0 && mbar_wait_bounded(&bar[s], (uint32_t)((pair / kAS) & 1), p.wait_ns);
     if (wall_tile) {
-      // radial ghost columns of this pair's f planes (f = f^eq of the ghost states)
+      // radial ghost columns of this pair's f planes (f = f^eq of the ghost
+      // states, plus the wall node's departure for non-equilibrium ghosts)
       if (fills && ok) {
         float* fw = st + (2 + grow) * kWinR;
         const int c0 = gside == 0 ? kLeft : cw_out, stp = gside == 0 ? 1 : -1;
+        float dep1 = 0.f, dep2 = 0.f;   // the wall node's departure f_q - f^eq_q
+        if (gneq) {
+          const EqParams<float> ea = eg[(size_t)2 * p.n_theta];
+          dep1 = fw[c0] - feq_q<float>(ea, d.vx[q1], d.vy[q1], k);
+          dep2 = fw[kAPl + c0] - feq_q<float>(ea, d.vx[q2], d.vy[q2], k);
+        }
         for (int l = 0; l < 2; ++l) {
           const int c = c0 - stp * (1 + l);
           if (c < 0 || c >= kWinR) continue;
           const EqParams<float> e = eg[(size_t)l * p.n_theta];
-          fw[c] = feq_q<float>(e, d.vx[q1], d.vy[q1], k);
-          fw[kAPl + c] = feq_q<float>(e, d.vx[q2], d.vy[q2], k);
+          fw[c] = feq_q<float>(e, d.vx[q1], d.vy[q1], k) + dep1;
+          fw[kAPl + c] = feq_q<float>(e, d.vx[q2], d.vy[q2], k) + dep2;
         }
       }
       __syncthreads();
@@ -676,8 +685,20 @@ __global__ void __launch_bounds__(kAThr, 3)
       }
       const f2 A = fma2(gs[3], bc2(d.half_v2[k]), gs[0]);
       const f2 B = fma2(gs[1], bc2(d.vx[q1]), mul2(gs[2], bc2(d.vy[q1])));
-      store(q1, sub2(fma2(decay, lam_c[0], add2(A, B)), acc[0]));
-      store(q2, sub2(fma2(decay, lam_c[1], sub2(A, B)), acc[1]));
+      f2 o1 = sub2(fma2(decay, lam_c[0], add2(A, B)), acc[0]);
+      f2 o2 = sub2(fma2(decay, lam_c[1], sub2(A, B)), acc[1]);
+      if (wall_tile) {
+        // non-equilibrium ghosts hand their cotangent straight to f_q of the wall node
+        for (int sd = 0; sd < 2; ++sd) {
+          if (!(p.bc_kind[sd] & PCLB_BC_NEQ)) continue;
+          const int rw = sd == 0 ? 0 : p.n_r - 1;
+          const float* gd = gdir + ((size_t)sd * p.n_theta + t) * kQ;
+          if (r == rw) { o1.x += gd[q1]; o2.x += gd[q2]; }
+          if (r + 1 == rw) { o1.y += gd[q1]; o2.y += gd[q2]; }
+        }
+      }
+      store(q1, o1);
+      store(q2, o2);
     }
   }
   if (brk < kANP && tid == 0) {
@@ -697,7 +718,8 @@ __global__ void __launch_bounds__(kAThr, 3)
 cudaError_t launch_adjoint_pairs_f32(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, const CUtensorMap* tmap_fn,
                                      const CUtensorMap* tmap_ln, const float* f,
                                      const float* lam_in, float* lam_out, const EqParams<float>* ghost,
-                                     const float* gwall, int a0, int na, int b0, int nx, const StepParams& p,
+                                     const float* gwall, const float* gdir, int a0, int na, int b0, int nx,
+                                     const StepParams& p,
                                      const DvmConst<float>& d, cudaStream_t s) {
   static std::atomic<unsigned long long> configured{0};
   {
@@ -706,6 +728,7 @@ cudaError_t launch_adjoint_pairs_f32(const CUtensorMap* tmap_f, const CUtensorMa
   }
   const dim3 grid((unsigned)nx, (unsigned)((p.n_theta + kTT - 1) / kTT));
   adjoint_pair_f32x2<<<grid, kAThr, kASmem, s>>>(*tmap_f, *tmap_l, *tmap_fn, *tmap_ln, f, lam_in, lam_out, ghost, gwall,
+                                                 gdir,
                                                  a0, na, b0, p, d);
   return cudaGetLastError();
 }

@@ -234,7 +234,7 @@ __device__ __forceinline__ T adj_feq(const EqParams<T>& e, const DvmConst<T>& d,
 template <class T>
 __global__ void __launch_bounds__(128)
     adjoint_wall_kernel(const T* __restrict__ f, const T* __restrict__ lam, EqParams<T>* __restrict__ ghost,
-                        T* __restrict__ gwall, const __grid_constant__ StepParams p,
+                        T* __restrict__ gwall, T* __restrict__ gdir, const __grid_constant__ StepParams p,
                         const __grid_constant__ DvmConst<T> d) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -272,15 +272,23 @@ __global__ void __launch_bounds__(128)
   }
   const EqParams<T> e0 = eq_params<T>(grho[0], gux[0], guy[0], gE[0], d);
   const EqParams<T> e1 = eq_params<T>(grho[1], gux[1], guy[1], gE[1], d);
+  const bool neq = (p.bc_kind[side] & PCLB_BC_NEQ) != 0;
+  // non-equilibrium ghosts also carry the wall node's departure f_q(a) -
+  // f^eq_q(a): its equilibrium parameters go to the third slot
+  const EqParams<T> ea = eq_params<T>(a.rho_d, a.ux, a.uy, a.E_d, d);
   if (lane == 0) {
     if (!(grho[0] > 0.0 && grho[1] > 0.0 && gE[0] > 0.0 && gE[1] > 0.0)) atomicOr(p.status, PCLB_FLAG_NONPHYS);
-    ghost[(size_t)(side * 2 + 0) * p.n_theta + t] = e0;
-    ghost[(size_t)(side * 2 + 1) * p.n_theta + t] = e1;
+    ghost[(size_t)(side * 3 + 0) * p.n_theta + t] = e0;
+    ghost[(size_t)(side * 3 + 1) * p.n_theta + t] = e1;
+    ghost[(size_t)(side * 3 + 2) * p.n_theta + t] = ea;
+    gdir[((size_t)side * p.n_theta + t) * kQ] = T(0);   // the rest velocity reads no ghost
   }
-  // per layer: the sums A, Bx, By, Cs, Dx, Fq of eq_cotangent over this lane's pair
-  T c[2][6];
+  // per layer: the sums A, Bx, By, Cs, Dx, Fq of eq_cotangent over this
+  // lane's pair; layer 2: those at the wall node's own state for the
+  // departure of non-equilibrium ghosts
+  T c[3][6];
 #pragma unroll
-  for (int l = 0; l < 2; ++l)
+  for (int l = 0; l < 3; ++l)
 #pragma unroll
     for (int j = 0; j < 6; ++j) c[l][j] = T(0);
   constexpr int half = kNDirs / 2;
@@ -297,7 +305,10 @@ __global__ void __launch_bounds__(128)
       lg[L][0] = lg[L][1] = T(0);
       if (cr.up_r == out) {
         const T f_a = fa[(size_t)q * plane], f_b = fb[(size_t)q * plane];
-        const T g0 = adj_feq<T>(e0, d, q), g1 = adj_feq<T>(e1, d, q);
+        // the ghost values as the step forms them (plus the departure f_q(a)
+        // - f^eq_q(a) for non-equilibrium ghosts)
+        const T dep = neq ? f_a - adj_feq<T>(ea, d, q) : T(0);
+        const T g0 = adj_feq<T>(e0, d, q) + dep, g1 = adj_feq<T>(e1, d, q) + dep;
         T MDa, MPa, MDb, MPb;
         mwb_partials<T>(cr.a_r, cr.k_r, f_a - g0, g0 - g1, MDa, MPa);
         mwb_partials<T>(cr.a_r, cr.k_r, f_b - f_a, f_a - g0, MDb, MPb);
@@ -306,9 +317,15 @@ __global__ void __launch_bounds__(128)
         lg[L][1] = lam_a * MPa;
       }
     }
+    // the ghost values' cotangents flow, for non-equilibrium ghosts, straight
+    // to f_q(a) (coefficient 1) and, with the opposite sign, through f^eq_q(a)
+    gdir[((size_t)side * p.n_theta + t) * kQ + q1] = lg[0][0] + lg[0][1];
+    gdir[((size_t)side * p.n_theta + t) * kQ + q1 + half] = lg[1][0] + lg[1][1];
+    const T lneq[2] = {neq ? -(lg[0][0] + lg[0][1]) : T(0), neq ? -(lg[1][0] + lg[1][1]) : T(0)};
 #pragma unroll
-    for (int l = 0; l < 2; ++l) {
-      const T E = (T)gE[l], ux = gux[l], uy = guy[l];
+    for (int l = 0; l < 3; ++l) {
+      const T E = l < 2 ? (T)gE[l] : a.E, ux = l < 2 ? gux[l] : a.ux, uy = l < 2 ? guy[l] : a.uy;
+      const T lp = l < 2 ? lg[0][l] : lneq[0], lm = l < 2 ? lg[1][l] : lneq[1];
       const T* cf = d.Fc[k];
       const T F = E * (cf[0] + E * (cf[1] + E * (cf[2] + E * cf[3])));
       const T Fd = cf[0] + E * (T(2) * cf[1] + E * (T(3) * cf[2] + E * T(4) * cf[3]));
@@ -317,22 +334,24 @@ __global__ void __launch_bounds__(128)
       const T a1 = T(1) - T(0.5) * s;
       const T a0 = a1 + T(0.125) * s * s;
       T Ak = 0, Bxk = 0, Byk = 0, Ck = 0, Dk = 0;
-      pair_terms<T>(d.vx[q1], d.vy[q1], ux * invE, uy * invE, s, a0, a1, lg[0][l], lg[1][l], Ak, Bxk, Byk, Ck, Dk);
+      pair_terms<T>(d.vx[q1], d.vy[q1], ux * invE, uy * invE, s, a0, a1, lp, lm, Ak, Bxk, Byk, Ck, Dk);
       c[l][0] = F * Ak; c[l][1] = F * Bxk; c[l][2] = F * Byk; c[l][3] = F * Ck; c[l][4] = F * Dk; c[l][5] = Fd * Ak;
     }
   }
 #pragma unroll
-  for (int l = 0; l < 2; ++l)
+  for (int l = 0; l < 3; ++l)
 #pragma unroll
     for (int j = 0; j < 6; ++j)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) c[l][j] += __shfl_xor_sync(0xffffffffu, c[l][j], o);
   if (lane != 0) return;
-  T Gl[2][4];
+  T Gl[3][4];
 #pragma unroll
-  for (int l = 0; l < 2; ++l) {
-    // G of eq_cotangent at the ghost state (the rest velocity returns nothing)
-    const T rho = (T)grho[l], E = (T)gE[l], ux = gux[l], uy = guy[l];
+  for (int l = 0; l < 3; ++l) {
+    // G of eq_cotangent at the ghost state, and at the wall node's state for
+    // the departure (the rest velocity returns nothing)
+    const T rho = l < 2 ? (T)grho[l] : a.rho, E = l < 2 ? (T)gE[l] : a.E;
+    const T ux = l < 2 ? gux[l] : a.ux, uy = l < 2 ? guy[l] : a.uy;
     const T invE = recip1(E);
     const T s = (ux * ux + uy * uy) * invE;
     Gl[l][0] = c[l][0];
@@ -346,7 +365,7 @@ __global__ void __launch_bounds__(128)
   T Ga[4], Gb[4];
   for (int j = 0; j < 4; ++j) {
     const bool ext = (j == 0 || j == 3) ? ext_rho_E : ext_u;
-    Ga[j] = ext ? T(2) * Gl[0][j] + T(3) * Gl[1][j] : T(0);
+    Ga[j] = (ext ? T(2) * Gl[0][j] + T(3) * Gl[1][j] : T(0)) + (neq ? Gl[2][j] : T(0));
     Gb[j] = ext ? -Gl[0][j] - T(2) * Gl[1][j] : T(0);
   }
   T ga[4], gb[4];
@@ -365,8 +384,9 @@ template <class T>
 __global__ void __launch_bounds__(AdjSize<T>::threads, AdjTile<T>::min_blocks)
     adjoint_pair_kernel(const __grid_constant__ CUtensorMap tmap_f, const __grid_constant__ CUtensorMap tmap_l,
                         const T* __restrict__ f, const T* __restrict__ lam_in, T* __restrict__ lam_out,
-                        const EqParams<T>* __restrict__ ghost, const T* __restrict__ gwall, int a0, int na,
-                        int b0, const __grid_constant__ StepParams p, const __grid_constant__ DvmConst<T> d) {
+                        const EqParams<T>* __restrict__ ghost, const T* __restrict__ gwall,
+                        const T* __restrict__ gdir, int a0, int na, int b0, const __grid_constant__ StepParams p,
+                        const __grid_constant__ DvmConst<T> d) {
   constexpr int TT = AdjTile<T>::TT;
   constexpr int PLANE = AdjSize<T>::plane;
   constexpr int NP = AdjSize<T>::npairs, RC = AdjSize<T>::rcols, PROD = AdjSize<T>::prod;
@@ -481,7 +501,8 @@ __global__ void __launch_bounds__(AdjSize<T>::threads, AdjTile<T>::min_blocks)
   const bool wall_tile = inner || outer;
   const int gside = rowl == 0 ? 0 : 1;
   const bool fills = wall_tile && rowl < 2 && lane < TT && t0 + lane < p.n_theta && (gside == 0 ? inner : outer);
-  const EqParams<T>* eg = ghost + (size_t)(gside * 2) * p.n_theta + t0 + lane;   // layer l at + l n_theta
+  const EqParams<T>* eg = ghost + (size_t)(gside * 3) * p.n_theta + t0 + lane;   // layer l at + l n_theta
+  const bool gneq = (p.bc_kind[gside] & PCLB_BC_NEQ) != 0;   // its ghosts carry the wall node's departure
 
   bool ok = true;
   int brk = NP;                                         // the pair at which a wait timed out
@@ -495,16 +516,23 @@ __global__ void __launch_bounds__(AdjSize<T>::threads, AdjTile<T>::min_blocks)
     T* pb = prod + (pair & 1) * 2 * PROD;                // this pair's products: [label][...]
     if (ok) ok = p.wait_ns != 0 && mbar_wait_bounded(&bar[s], (uint32_t)((pair / S) & 1), p.wait_ns);
     if (wall_tile) {
-      // radial ghost columns of this pair's f planes (f = f^eq of the ghost states)
+      // radial ghost columns of this pair's f planes (f = f^eq of the ghost
+      // states, plus the wall node's departure for non-equilibrium ghosts)
       if (fills && ok) {
         T* fw = const_cast<T*>(st) + (2 + lane) * kWinR;
         const int c0 = gside == 0 ? kLeft : cw_out, stp = gside == 0 ? 1 : -1;
+        T dep1 = T(0), dep2 = T(0);
+        if (gneq) {
+          const EqParams<T> ea = eg[(size_t)2 * p.n_theta];
+          dep1 = fw[c0] - adj_feq<T>(ea, d, q1);
+          dep2 = fw[PLANE + c0] - adj_feq<T>(ea, d, q2);
+        }
         for (int l = 0; l < 2; ++l) {
           const int c = c0 - stp * (1 + l);
           if (c < 0 || c >= kWinR) continue;
           const EqParams<T> e = eg[(size_t)l * p.n_theta];
-          fw[c] = adj_feq<T>(e, d, q1);
-          fw[PLANE + c] = adj_feq<T>(e, d, q2);
+          fw[c] = adj_feq<T>(e, d, q1) + dep1;
+          fw[PLANE + c] = adj_feq<T>(e, d, q2) + dep2;
         }
       }
       __syncthreads();
@@ -599,8 +627,17 @@ __global__ void __launch_bounds__(AdjSize<T>::threads, AdjTile<T>::min_blocks)
         gather_azimuthal_mixed<T, PROD, BT - AT>(pb, p_az, tneg, acc);
       const T A = gs[0] + gs[3] * d.half_v2[k];
       const T B = gs[1] * d.vx[q1] + gs[2] * d.vy[q1];
-      store(q1, decay * lam_c[0] + (A + B) - acc[0]);
-      store(q2, decay * lam_c[1] + (A - B) - acc[1]);
+      T o1 = decay * lam_c[0] + (A + B) - acc[0], o2 = decay * lam_c[1] + (A - B) - acc[1];
+      if (wall_tile) {
+        // non-equilibrium ghosts hand their cotangent straight to f_q of the wall node
+        for (int sd = 0; sd < 2; ++sd)
+          if ((p.bc_kind[sd] & PCLB_BC_NEQ) && r == (sd == 0 ? 0 : p.n_r - 1)) {
+            o1 += gdir[((size_t)sd * p.n_theta + t) * kQ + q1];
+            o2 += gdir[((size_t)sd * p.n_theta + t) * kQ + q2];
+          }
+      }
+      store(q1, o1);
+      store(q2, o2);
     }
   }
   if (brk < NP && tid == 0) {
@@ -632,16 +669,18 @@ cudaError_t launch_adjoint(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l,
   cudaError_t e = cudaEventRecord(ev_fork, stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_fork, 0);
   if (e != cudaSuccess) return e;
-  adjoint_wall_kernel<T><<<(2 * p.n_theta + 3) / 4, 128, 0, side>>>(f, lam_in, ghost, gwall, p, d);
+  // per-label cotangents of non-equilibrium ghosts: [side][n_theta][Q] after gwall
+  T* gdir = reinterpret_cast<T*>(ws.gwall + (((size_t)16 * p.n_theta * sizeof(T) + 255) & ~(size_t)255));
+  adjoint_wall_kernel<T><<<(2 * p.n_theta + 3) / 4, 128, 0, side>>>(f, lam_in, ghost, gwall, gdir, p, d);
   if constexpr (sizeof(T) == 4) {
     // FP32: the packed two-nodes-per-thread pair kernel (adjoint_f32x2.cu)
     e = cudaGetLastError();
     if (e == cudaSuccess)
-      e = launch_adjoint_pairs_f32(tmap_f, tmap_l, tmap_fn, tmap_ln, f, lam_in, lam_out, ghost, gwall, 0, 1, b0,
+      e = launch_adjoint_pairs_f32(tmap_f, tmap_l, tmap_fn, tmap_ln, f, lam_in, lam_out, ghost, gwall, gdir, 0, 1, b0,
                                    1 + (nt - b0), p, d,
                                    side);
     if (e == cudaSuccess && n_interior > 0)
-      e = launch_adjoint_pairs_f32(tmap_f, tmap_l, tmap_fn, tmap_ln, f, lam_in, lam_out, ghost, gwall, 1, n_interior,
+      e = launch_adjoint_pairs_f32(tmap_f, tmap_l, tmap_fn, tmap_ln, f, lam_in, lam_out, ghost, gwall, gdir, 1, n_interior,
                                    0, n_interior,
                                    p, d, stream);
   } else {
@@ -652,10 +691,10 @@ cudaError_t launch_adjoint(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l,
     constexpr int TT = AdjTile<T>::TT;
     const unsigned gy = (unsigned)((p.n_theta + TT - 1) / TT);
     adjoint_pair_kernel<T><<<dim3(1 + (nt - b0), gy), AdjSize<T>::threads, smem, side>>>(
-        *tmap_f, *tmap_l, f, lam_in, lam_out, ghost, gwall, 0, 1, b0, p, d);
+        *tmap_f, *tmap_l, f, lam_in, lam_out, ghost, gwall, gdir, 0, 1, b0, p, d);
     if (n_interior > 0)
       adjoint_pair_kernel<T><<<dim3(n_interior, gy), AdjSize<T>::threads, smem, stream>>>(
-          *tmap_f, *tmap_l, f, lam_in, lam_out, ghost, gwall, 1, n_interior, 0, p, d);
+          *tmap_f, *tmap_l, f, lam_in, lam_out, ghost, gwall, gdir, 1, n_interior, 0, p, d);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
@@ -665,16 +704,19 @@ cudaError_t launch_adjoint(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l,
 }
 
 size_t adjoint_scratch_bytes(int n_theta, int elem) {
-  // ghost: 2 x 2 EqParams (10 values) per row; gwall: 2 x 2 x 4 per row
-  const size_t b = (size_t)4 * n_theta * 10 * elem, c = (size_t)16 * n_theta * elem;
+  // ghost: 2 x 3 EqParams (10 values) per row (two ghost layers and the wall
+  // node); gwall: 2 x 2 x 4 per row; the non-equilibrium ghosts' per-label
+  // cotangents: 2 x Q per row
+  const size_t b = (size_t)6 * n_theta * 10 * elem, c = (size_t)16 * n_theta * elem;
+  const size_t g = (size_t)2 * n_theta * kQ * elem;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  return up(b) + up(c);
+  return up(b) + up(c) + up(g);
 }
 
 AdjScratch adjoint_scratch(unsigned char* base, int n_theta, int elem) {
   AdjScratch s;
   s.ghost = base;
-  s.gwall = base + (((size_t)4 * n_theta * 10 * elem + 255) & ~(size_t)255);
+  s.gwall = base + (((size_t)6 * n_theta * 10 * elem + 255) & ~(size_t)255);
   return s;
 }
 

@@ -1202,8 +1202,6 @@ pclb_status pclb_lambda_get(pclb_ctx* ctx, void* lam) {
 // the MWB increments.
 static pclb_status adjoint_supported(pclb_ctx* ctx) {
   if (generic(ctx)) return fail(ctx, PCLB_EUNSUPPORTED, "reverse mode implements n_dirs = 8 only");
-  if ((ctx->bc_kind[0] | ctx->bc_kind[1]) & PCLB_BC_NEQ)
-    return fail(ctx, PCLB_EUNSUPPORTED, "the adjoint does not support PCLB_BC_NEQ boundaries");
   if (ctx->scheme != PCLB_SCHEME_MWB)
     return fail(ctx, PCLB_EUNSUPPORTED, "the adjoint supports the MWB scheme only (scheme %d)", ctx->scheme);
   return PCLB_OK;

@@ -1,5 +1,6 @@
 """The boundary options beyond the basic ones on the GPU: the non-equilibrium
-ghost nodes (PCLB_BC_NEQ, Sec. II C 1) against the oracle, and the
+ghost nodes (PCLB_BC_NEQ, Sec. II C 1) against the oracle, in the step and
+in its adjoint, and the
 rotational-flow test of Sec. III A (rotating cylinders on one sector with the
 rotated-label azimuthal boundary) against the oracle and against the steady
 Navier-Stokes profile u_theta = A r + B / r."""
@@ -73,11 +74,25 @@ def test_couette_steady_state_on_gpu():
     assert np.max(np.abs(ur)) <= 0.01 * umax
 
 
-def test_adjoint_refuses_neq_boundaries():
-    w = CASES["extrap_neq"]()
-    with P.PCLB(w, precision="fp64") as g:
-        g.set_state()
-        f = g.get_f()
-        with pytest.raises(P.PCLBError) as e:
-            g.adjoint_step(f, torch.zeros_like(f))
-        assert e.value.code == 8   # PCLB_EUNSUPPORTED
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_with_neq_boundaries_matches_oracle(name, prec, tol):
+    """The adjoint step with non-equilibrium ghost nodes, every entry against
+    the oracle's forward-mode derivative: the ghosts' cotangent reaches the
+    wall node's f_q directly and, with the opposite sign, through its own
+    equilibrium, besides the path through the extrapolated ghost state."""
+    w = CASES[name]()
+    f = _noisy(w)
+    lam = np.random.default_rng(12).normal(size=f.shape)
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    if prec == "fp32":
+        f = f.astype(np.float32).astype(np.float64)
+        lam = lam.astype(np.float32).astype(np.float64)
+    with P.PCLB(w, precision=prec) as g:
+        got = g.adjoint_step(torch.as_tensor(f, dtype=dtype, device="cuda"),
+                             torch.as_tensor(lam, dtype=dtype, device="cuda")).double().cpu().numpy()
+        assert g.status_flags() == 0
+    q, t, r = (a.ravel() for a in np.meshgrid(*(np.arange(n) for n in f.shape), indexing="ij"))
+    want = O.adjoint_entries(w, f, lam, q, t, r).reshape(f.shape)
+    err = np.abs(got - want) / np.max(np.abs(want))
+    assert err.max() <= tol, (err.max(), np.unravel_index(np.argmax(err), err.shape))
