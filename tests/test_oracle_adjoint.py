@@ -17,7 +17,8 @@ def _state(n_r=6, n_t=8, seed=3, bc=(I.BC_EXTRAP, I.BC_EXTRAP)):
     return w, f
 
 
-@pytest.mark.parametrize("bc", [(I.BC_EXTRAP, I.BC_EXTRAP), (I.BC_DIRICHLET, I.BC_WALL)])
+@pytest.mark.parametrize("bc", [(I.BC_EXTRAP, I.BC_EXTRAP), (I.BC_DIRICHLET, I.BC_WALL),
+                                (I.BC_EXTRAP | I.BC_NEQ, I.BC_WALL | I.BC_NEQ)])
 def test_jvp_matches_central_differences(bc):
     w, f = _state(bc=bc)
     rng = np.random.default_rng(0)
@@ -43,10 +44,12 @@ def test_adjoint_is_the_transpose_of_the_jvp():
         assert lhs == pytest.approx(rhs, rel=1e-12, abs=1e-12 * np.abs(lhs).max())
 
 
-def test_adjoint_matches_finite_difference_gradient():
+@pytest.mark.parametrize("bc", [(I.BC_EXTRAP, I.BC_EXTRAP), (I.BC_DIRICHLET | I.BC_NEQ, I.BC_EXTRAP | I.BC_NEQ)])
+def test_adjoint_matches_finite_difference_gradient(bc):
     # d/d f_j of <lam, step(f)> by central differences on a few entries,
-    # including entries next to the walls (ghost extrapolation feeds back)
-    w, f = _state(n_r=5, n_t=6, seed=8)
+    # including entries next to the walls (ghost extrapolation feeds back;
+    # non-equilibrium ghosts also carry the wall node's own f - f^eq, Sec. II C)
+    w, f = _state(n_r=5, n_t=6, seed=8, bc=bc)
     rng = np.random.default_rng(2)
     lam = rng.normal(size=f.shape)
     adj = O.adjoint_step(w, f, lam)
@@ -105,3 +108,4 @@ def test_fields_jvp_matches_central_differences():
     plus, minus = O.fields(w, f + eps * df), O.fields(w, f - eps * df)
     for a, b, j in zip(plus, minus, jv):
         assert np.max(np.abs((a - b) / (2 * eps) - j)) <= 1e-7 * max(np.max(np.abs(j)), 1e-12)
+

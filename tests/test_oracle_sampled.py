@@ -27,6 +27,9 @@ CASES = [
     ("rm", lambda: I.rm(n_r=16, n_theta=8)),
     ("sector", lambda: I.random_smooth(6, 5, seed=4, n_f=1)),
     ("three_rows", lambda: I.random_smooth(5, 3, seed=5)),
+    # non-equilibrium ghosts: the ghosts also carry the wall node's f - f^eq
+    ("neq_extrap_wall", lambda: I.random_smooth(6, 5, seed=6, bc_kind=(I.BC_EXTRAP | I.BC_NEQ, I.BC_WALL | I.BC_NEQ))),
+    ("neq_wall_dirichlet", lambda: I.random_smooth(5, 6, seed=7, bc_kind=(I.BC_WALL, I.BC_DIRICHLET | I.BC_NEQ))),
 ]
 
 
