@@ -1198,8 +1198,9 @@ pclb_status pclb_lambda_get(pclb_ctx* ctx, void* lam) {
   return e == cudaSuccess ? PCLB_OK : cuda_fail(ctx, e, "lambda pack launch");
 }
 
-// The adjoint differentiates the ghost nodes as f = f^eq of their state and
-// the MWB increments.
+// The adjoint differentiates the MWB increments and the ghost nodes of every
+// wall kind (f = f^eq of the ghost state, plus the wall node's departure for
+// non-equilibrium ghosts); the comparison schemes are forward-only.
 static pclb_status adjoint_supported(pclb_ctx* ctx) {
   if (generic(ctx)) return fail(ctx, PCLB_EUNSUPPORTED, "reverse mode implements n_dirs = 8 only");
   if (ctx->scheme != PCLB_SCHEME_MWB)
