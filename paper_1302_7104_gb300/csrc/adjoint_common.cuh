@@ -157,12 +157,13 @@ __device__ __forceinline__ void to_moment_cotangent(T rho, T ux, T uy, T E, cons
 
 // The FP32 pair kernel over tiles a0 .. a0 + na - 1 and b0 .. (nx blocks in
 // r), all theta tiles (adjoint_f32x2.cu); tmap_fn, tmap_ln: descriptors of f
-// and lam with one tile per box, for its node phase.
+// and lam with one tile per box, for its node phase.  walls: the tiles may
+// include wall tiles (radial tile 0 or r0 >= n_r - 33); false only for a
+// launch of interior tiles, which then runs the instance without wall code.
 cudaError_t launch_adjoint_pairs_f32(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, const CUtensorMap* tmap_fn,
                                      const CUtensorMap* tmap_ln, const float* f,
                                      const float* lam_in, float* lam_out, const EqParams<float>* ghost,
                                      const float* gwall, const float* gdir, int a0, int na, int b0, int nx,
-                                     const StepParams& p,
-                                     const DvmConst<float>& d, cudaStream_t s);
+                                     bool walls, const StepParams& p, const DvmConst<float>& d, cudaStream_t s);
 
 }  // namespace pclb

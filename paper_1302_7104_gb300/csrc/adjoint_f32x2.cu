@@ -386,6 +386,10 @@ __device__ __forceinline__ f2 gather_az2(const float* P) {
   return sub2(sub2(add2(lds2(P), lds2(P + DB + W)), lds2(P + W)), lds2(P + DB + 2 * W));
 }
 
+// WALLS: the launch may contain wall tiles (the tiles of radial index 0 and
+// those within 33 columns of n_r); the interior launch is the instance
+// without any wall code.
+template <bool WALLS>
 __global__ void __launch_bounds__(kAThr, 3)
     adjoint_pair_f32x2(const __grid_constant__ CUtensorMap tmap_f, const __grid_constant__ CUtensorMap tmap_l,
                        const __grid_constant__ CUtensorMap tmap_fn, const __grid_constant__ CUtensorMap tmap_ln,
@@ -555,7 +559,7 @@ __global__ void __launch_bounds__(kAThr, 3)
   // the inner wall, 32..47 the outer wall, one tile row each)
   const int cw_out = p.n_r - 1 - r0 + kLeft;
   const bool inner = r0 == 0, outer = cw_out <= kLeft + kTileR;
-  const bool wall_tile = inner || outer;
+  const bool wall_tile = WALLS && (inner || outer);
   const int gside = tid >> 5, grow = tid & 31;
   const bool fills = wall_tile && tid < 64 && grow < kTT && t0 + grow < p.n_theta && (gside == 0 ? inner : outer);
   const EqParams<float>* eg = ghost + (size_t)(gside * 3) * p.n_theta + t0 + grow;   // layer l at + l n_theta
@@ -713,24 +717,33 @@ __global__ void __launch_bounds__(kAThr, 3)
   }
 }
 
+template <bool WALLS>
+cudaError_t launch_pairs(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, const CUtensorMap* tmap_fn,
+                                const CUtensorMap* tmap_ln, const float* f, const float* lam_in, float* lam_out,
+                                const EqParams<float>* ghost, const float* gwall, const float* gdir, int a0, int na,
+                                int b0, int nx, const StepParams& p, const DvmConst<float>& d, cudaStream_t s) {
+  static std::atomic<unsigned long long> configured{0};   // per instance and device
+  {
+    const cudaError_t e = set_smem_once(adjoint_pair_f32x2<WALLS>, kASmem, configured);
+    if (e != cudaSuccess) return e;
+  }
+  const dim3 grid((unsigned)nx, (unsigned)((p.n_theta + kTT - 1) / kTT));
+  adjoint_pair_f32x2<WALLS><<<grid, kAThr, kASmem, s>>>(*tmap_f, *tmap_l, *tmap_fn, *tmap_ln, f, lam_in, lam_out,
+                                                        ghost, gwall, gdir, a0, na, b0, p, d);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_adjoint_pairs_f32(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l, const CUtensorMap* tmap_fn,
                                      const CUtensorMap* tmap_ln, const float* f,
                                      const float* lam_in, float* lam_out, const EqParams<float>* ghost,
                                      const float* gwall, const float* gdir, int a0, int na, int b0, int nx,
-                                     const StepParams& p,
-                                     const DvmConst<float>& d, cudaStream_t s) {
-  static std::atomic<unsigned long long> configured{0};
-  {
-    const cudaError_t e = set_smem_once(adjoint_pair_f32x2, kASmem, configured);
-    if (e != cudaSuccess) return e;
-  }
-  const dim3 grid((unsigned)nx, (unsigned)((p.n_theta + kTT - 1) / kTT));
-  adjoint_pair_f32x2<<<grid, kAThr, kASmem, s>>>(*tmap_f, *tmap_l, *tmap_fn, *tmap_ln, f, lam_in, lam_out, ghost, gwall,
-                                                 gdir,
-                                                 a0, na, b0, p, d);
-  return cudaGetLastError();
+                                     bool walls, const StepParams& p, const DvmConst<float>& d, cudaStream_t s) {
+  return walls ? launch_pairs<true>(tmap_f, tmap_l, tmap_fn, tmap_ln, f, lam_in, lam_out, ghost, gwall, gdir, a0, na,
+                                    b0, nx, p, d, s)
+               : launch_pairs<false>(tmap_f, tmap_l, tmap_fn, tmap_ln, f, lam_in, lam_out, ghost, gwall, gdir, a0,
+                                     na, b0, nx, p, d, s);
 }
 
 }  // namespace pclb

@@ -677,12 +677,11 @@ cudaError_t launch_adjoint(const CUtensorMap* tmap_f, const CUtensorMap* tmap_l,
     e = cudaGetLastError();
     if (e == cudaSuccess)
       e = launch_adjoint_pairs_f32(tmap_f, tmap_l, tmap_fn, tmap_ln, f, lam_in, lam_out, ghost, gwall, gdir, 0, 1, b0,
-                                   1 + (nt - b0), p, d,
-                                   side);
+                                   1 + (nt - b0), true, p, d, side);
+    // tiles 1 .. t_hi - 1 have r0 > 0 and r0 < n_r - 33: no wall tile among them
     if (e == cudaSuccess && n_interior > 0)
       e = launch_adjoint_pairs_f32(tmap_f, tmap_l, tmap_fn, tmap_ln, f, lam_in, lam_out, ghost, gwall, gdir, 1, n_interior,
-                                   0, n_interior,
-                                   p, d, stream);
+                                   0, n_interior, false, p, d, stream);
   } else {
     static std::atomic<unsigned long long> configured{0};
     constexpr int smem = AdjSize<T>::smem;
