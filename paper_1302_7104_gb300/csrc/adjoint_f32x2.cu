@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(kAThr, 3)
 #pragma unroll
     for (int j = 0; j < 4; ++j) gs[j] = mul2(omd, g[j]);
     // the cotangent the ghost nodes return to the two nodes next to each wall
-    if (row_ok && (r < 2 || r + 3 >= p.n_r)) {
+    if (WALLS && row_ok && (r < 2 || r + 3 >= p.n_r)) {
       auto wall = [&](int rr) {
         float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
         auto add = [&](int side, int node) {
@@ -534,15 +534,19 @@ __global__ void __launch_bounds__(kAThr, 3)
   const int p_az = kAT + row * kTileR + j2;     // its azimuthal product slot
   const f2 my_invr = lds2(invr + j2);
   float* out_row = lam_out + (size_t)srow * p.pitch + r;
-  const bool lo_ghost = row_ok && t >= p.n_theta - 2;
-  const bool hi_ghost = row_ok && t < 2;
-  float* out_lo = lam_out + (size_t)max(t - (p.n_theta - 2), 0) * p.pitch + r;
-  float* out_hi = lam_out + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r;
   const bool plain_tile = r0 + kTileR <= p.n_r && t0 >= 2 && t0 + kTT <= p.n_theta - 2;
   auto store = [&](int q, f2 o) {
     if (plain_tile) {
       __stcs(reinterpret_cast<float2*>(out_row + (size_t)q * plane_out), o);
-    } else if (v1) {
+      return;
+    }
+    // seam and ragged tiles: the seam rows' ghost copies, formed here so
+    // that plain tiles keep no registers for them
+    const bool lo_ghost = row_ok && t >= p.n_theta - 2;
+    const bool hi_ghost = row_ok && t < 2;
+    float* out_lo = lam_out + (size_t)max(t - (p.n_theta - 2), 0) * p.pitch + r;
+    float* out_hi = lam_out + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r;
+    if (v1) {
       *reinterpret_cast<float2*>(out_row + (size_t)q * plane_out) = o;
       if (lo_ghost) *reinterpret_cast<float2*>(out_lo + (size_t)d.recv_lo[q] * plane_out) = o;
       if (hi_ghost) *reinterpret_cast<float2*>(out_hi + (size_t)d.recv_hi[q] * plane_out) = o;

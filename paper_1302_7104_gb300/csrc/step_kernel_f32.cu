@@ -296,17 +296,20 @@ __global__ void __launch_bounds__(kStepThreads32, kCtasPerSm32)
   const f2 decay = bc2((float)p.decay);
   const size_t plane_out = (size_t)p.rows * p.pitch;
   float* out_row = f_out + (size_t)(t + kGhostRows) * p.pitch + r;
-  const bool lo_ghost = row_ok && t >= p.n_theta - 2;
-  const bool hi_ghost = row_ok && t < 2;
-  float* out_lo = f_out + (size_t)max(t - (p.n_theta - 2), 0) * p.pitch + r;
-  float* out_hi = f_out + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r;
-
   // tiles away from the radial walls and the seam take the plain store
   const bool plain_tile = r0 + kTileR <= p.n_r && t0 >= 2 && t0 + kTileT32 <= p.n_theta - 2;
   auto store = [&](int q, f2 o) {
     if (plain_tile) {
       __stcs(reinterpret_cast<float2*>(out_row + (size_t)q * plane_out), o);   // not read again before the next step
-    } else if (v1) {
+      return;
+    }
+    // seam and ragged tiles: the seam rows' ghost copies, formed here so
+    // that plain tiles keep no registers for them
+    const bool lo_ghost = row_ok && t >= p.n_theta - 2;
+    const bool hi_ghost = row_ok && t < 2;
+    float* out_lo = f_out + (size_t)max(t - (p.n_theta - 2), 0) * p.pitch + r;
+    float* out_hi = f_out + (size_t)(p.n_theta + kGhostRows + t) * p.pitch + r;
+    if (v1) {
       *reinterpret_cast<float2*>(out_row + (size_t)q * plane_out) = o;
       if (lo_ghost) *reinterpret_cast<float2*>(out_lo + (size_t)d.recv_lo[q] * plane_out) = o;
       if (hi_ghost) *reinterpret_cast<float2*>(out_hi + (size_t)d.recv_hi[q] * plane_out) = o;
