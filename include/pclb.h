@@ -322,7 +322,11 @@ pclb_status pclb_lambda_get(pclb_ctx* ctx, void* lam);
 
 /* One adjoint step: lam <- J(f)^T lam, where f is the state the forward step
  * started from: f_state (device, a buffer filled by pclb_save_state) or, if
- * NULL, the context's current state.  One fused kernel launch. */
+ * NULL, the context's current state.  Asynchronous, three kernel launches:
+ * the wall feedback and the tiles next to the walls on a side stream of the
+ * context, forked from and joined back to the context's stream with events,
+ * and the interior tiles on the context's stream; to the caller it is one
+ * stream-ordered operation. */
 pclb_status pclb_adjoint_state(pclb_ctx* ctx, const void* f_state);
 
 /* Convenience form in the packed layout: lam_n = J(f_n)^T lam_np1, all three
