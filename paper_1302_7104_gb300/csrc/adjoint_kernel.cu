@@ -274,8 +274,11 @@ __global__ void __launch_bounds__(128)
   const EqParams<T> e1 = eq_params<T>(grho[1], gux[1], guy[1], gE[1], d);
   const bool neq = (p.bc_kind[side] & PCLB_BC_NEQ) != 0;
   // non-equilibrium ghosts also carry the wall node's departure f_q(a) -
-  // f^eq_q(a): its equilibrium parameters go to the third slot
-  const EqParams<T> ea = eq_params<T>(a.rho_d, a.ux, a.uy, a.E_d, d);
+  // f^eq_q(a): its equilibrium parameters go to the third slot (zero for
+  // other walls, whose pair kernels do not read it; neq is uniform across
+  // the warp, which serves one side)
+  EqParams<T> ea{};
+  if (neq) ea = eq_params<T>(a.rho_d, a.ux, a.uy, a.E_d, d);
   if (lane == 0) {
     if (!(grho[0] > 0.0 && grho[1] > 0.0 && gE[0] > 0.0 && gE[1] > 0.0)) atomicOr(p.status, PCLB_FLAG_NONPHYS);
     ghost[(size_t)(side * 3 + 0) * p.n_theta + t] = e0;
@@ -324,6 +327,7 @@ __global__ void __launch_bounds__(128)
     const T lneq[2] = {neq ? -(lg[0][0] + lg[0][1]) : T(0), neq ? -(lg[1][0] + lg[1][1]) : T(0)};
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
+      if (l == 2 && !neq) break;                      // the departure's terms: non-equilibrium ghosts only
       const T E = l < 2 ? (T)gE[l] : a.E, ux = l < 2 ? gux[l] : a.ux, uy = l < 2 ? guy[l] : a.uy;
       const T lp = l < 2 ? lg[0][l] : lneq[0], lm = l < 2 ? lg[1][l] : lneq[1];
       const T* cf = d.Fc[k];
@@ -339,17 +343,23 @@ __global__ void __launch_bounds__(128)
     }
   }
 #pragma unroll
-  for (int l = 0; l < 3; ++l)
+  for (int l = 0; l < 3; ++l) {
+    if (l == 2 && !neq) break;
 #pragma unroll
     for (int j = 0; j < 6; ++j)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) c[l][j] += __shfl_xor_sync(0xffffffffu, c[l][j], o);
+  }
   if (lane != 0) return;
   T Gl[3][4];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     // G of eq_cotangent at the ghost state, and at the wall node's state for
     // the departure (the rest velocity returns nothing)
+    if (l == 2 && !neq) {
+      Gl[2][0] = Gl[2][1] = Gl[2][2] = Gl[2][3] = T(0);
+      break;
+    }
     const T rho = l < 2 ? (T)grho[l] : a.rho, E = l < 2 ? (T)gE[l] : a.E;
     const T ux = l < 2 ? gux[l] : a.ux, uy = l < 2 ? guy[l] : a.uy;
     const T invE = recip1(E);
